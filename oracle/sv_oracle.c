@@ -1,0 +1,270 @@
+/*
+ * sv_oracle.c -- the correctness oracle for the state-vector hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference leg of bench.py may load this library.  The CUDA
+ * path never calls it, and it shares no code with the CUDA path.
+ *
+ * What it computes is the plain definition of exact state-vector simulation
+ * (§II: the full 2^n complex amplitude vector), written out in complex128:
+ *
+ *   psi_out = U_G ... U_2 U_1 psi_in,
+ *
+ * each U_g being gate g's 2^k x 2^k matrix acting on its k target qubits and
+ * the identity on every other qubit.  Gates are applied one at a time in
+ * program order -- no fusion, no blocking, no reordering.
+ *
+ * Conventions (the paper ingests Qiskit circuits and OpenQASM 2, §III-A, and
+ * is otherwise silent; these are the readings adopted):
+ *   - qubit q is bit q of the amplitude index (little-endian);
+ *   - for a gate on targets (t_0 .. t_{k-1}), bit m of the matrix row/column
+ *     index refers to qubit t_m (t_0 is the least significant matrix bit);
+ *     so for cx(c, t), c = t_0 and t = t_1;
+ *   - gate matrices follow the OpenQASM 2 definitions (u3, cx, cp, ...).
+ *
+ * Measurement (§III-B: sampling of end-of-circuit measurements from the final
+ * state; expectation values from the cached state):
+ *   - p_i = |psi_i|^2, CDF C_i = sum_{j<=i} p_j accumulated sequentially in
+ *     double precision;
+ *   - a draw with uniform u in [0,1) picks x = min{ i : C_i > u * C_{N-1} }
+ *     (strict), clamped to the last index with p_i > 0 if rounding leaves no
+ *     such i;
+ *   - <Z_mask> = sum_i p_i (-1)^popcount(i & mask) / C_{N-1}.
+ *
+ * Parity pinning: see tests/test_oracle_pins.py (closed forms for GHZ and QFT,
+ * an explicit DFT matrix, Kronecker-product brute force for n <= 8, textbook
+ * gate identities, norm preservation, circuit * inverse = |0...0>, sampler and
+ * expectation closed forms).
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double _Complex cplx;
+
+/* Gate kinds of the oracle's own IR (independent of the CUDA library's enum). */
+enum {
+  ORC_U3 = 1, ORC_H, ORC_X, ORC_Y, ORC_Z, ORC_S, ORC_SDG, ORC_T, ORC_TDG,
+  ORC_RX, ORC_RY, ORC_RZ, ORC_P, ORC_CX, ORC_CZ, ORC_CP, ORC_SWAP, ORC_UNITARY
+};
+
+typedef struct {
+  int32_t kind;
+  int32_t nq;
+  int32_t q[5];
+  int32_t _pad;
+  double p[3];
+  const cplx *mat; /* ORC_UNITARY only: 2^nq x 2^nq row-major */
+} orc_gate;
+
+void orc_set_threads(int t) {
+#ifdef _OPENMP
+  omp_set_num_threads(t > 0 ? t : 1);
+#else
+  (void)t;
+#endif
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/*
+ * Gate matrix, row-major 2^k x 2^k, from the OpenQASM 2 definitions:
+ *   u3(θ,φ,λ) = [[cos(θ/2), -e^{iλ} sin(θ/2)], [e^{iφ} sin(θ/2), e^{i(φ+λ)} cos(θ/2)]]
+ *   rx(θ) = u3(θ,-π/2,π/2), ry(θ) = u3(θ,0,0), rz(φ) = diag(e^{-iφ/2}, e^{iφ/2}),
+ *   p(λ) = diag(1, e^{iλ}), h = u3(π/2,0,π), x, y, z, s, sdg, t, tdg standard,
+ *   cx (control t_0, target t_1), cz, cp(λ) = diag(1,1,1,e^{iλ}), swap.
+ * Returns the number of qubits k, or -1 for an unknown kind.
+ */
+int orc_gate_matrix(const orc_gate *g, cplx *m) {
+  const double *p = g->p;
+  const double r2 = 1.0 / sqrt(2.0);
+  int k;
+  switch (g->kind) {
+  case ORC_UNITARY:
+    k = g->nq;
+    memcpy(m, g->mat, sizeof(cplx) * (size_t)(1u << k) * (size_t)(1u << k));
+    return k;
+  case ORC_U3: {
+    double c = cos(p[0] / 2.0), s = sin(p[0] / 2.0);
+    m[0] = c;
+    m[1] = -cexp(I * p[2]) * s;
+    m[2] = cexp(I * p[1]) * s;
+    m[3] = cexp(I * (p[1] + p[2])) * c;
+    return 1;
+  }
+  case ORC_H: m[0] = r2; m[1] = r2; m[2] = r2; m[3] = -r2; return 1;
+  case ORC_X: m[0] = 0; m[1] = 1; m[2] = 1; m[3] = 0; return 1;
+  case ORC_Y: m[0] = 0; m[1] = -I; m[2] = I; m[3] = 0; return 1;
+  case ORC_Z: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = -1; return 1;
+  case ORC_S: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = I; return 1;
+  case ORC_SDG: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = -I; return 1;
+  case ORC_T: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = cexp(I * M_PI / 4.0); return 1;
+  case ORC_TDG: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = cexp(-I * M_PI / 4.0); return 1;
+  case ORC_RX: {
+    double c = cos(p[0] / 2.0), s = sin(p[0] / 2.0);
+    m[0] = c; m[1] = -I * s; m[2] = -I * s; m[3] = c;
+    return 1;
+  }
+  case ORC_RY: {
+    double c = cos(p[0] / 2.0), s = sin(p[0] / 2.0);
+    m[0] = c; m[1] = -s; m[2] = s; m[3] = c;
+    return 1;
+  }
+  case ORC_RZ:
+    m[0] = cexp(-I * p[0] / 2.0); m[1] = 0; m[2] = 0; m[3] = cexp(I * p[0] / 2.0);
+    return 1;
+  case ORC_P: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = cexp(I * p[0]); return 1;
+  case ORC_CX:
+  case ORC_CZ:
+  case ORC_CP:
+  case ORC_SWAP:
+    for (int i = 0; i < 16; i++) m[i] = 0;
+    if (g->kind == ORC_CX) {
+      /* index bit 0 = control (t_0), bit 1 = target (t_1) */
+      m[0 * 4 + 0] = 1; m[2 * 4 + 2] = 1; m[1 * 4 + 3] = 1; m[3 * 4 + 1] = 1;
+    } else if (g->kind == ORC_SWAP) {
+      m[0 * 4 + 0] = 1; m[1 * 4 + 2] = 1; m[2 * 4 + 1] = 1; m[3 * 4 + 3] = 1;
+    } else {
+      m[0] = 1; m[5] = 1; m[10] = 1;
+      m[15] = (g->kind == ORC_CZ) ? -1.0 : cexp(I * p[0]);
+    }
+    return 2;
+  default:
+    return -1;
+  }
+}
+
+/*
+ * Apply a k-qubit matrix M (2^k x 2^k row-major) on targets t[0..k-1]:
+ * for every index i with all target bits clear, gather v_j = psi[i | bits(j)]
+ * (bit m of j placed at qubit t_m), then psi[i | bits(r)] = sum_j M[r][j] v_j.
+ */
+void orc_apply_matrix(cplx *psi, int n, int k, const int32_t *t, const cplx *M) {
+  const uint64_t N = 1ull << n;
+  const int K = 1 << k;
+  uint64_t tmask = 0;
+  for (int m = 0; m < k; m++) tmask |= 1ull << t[m];
+  uint64_t off[32];
+  for (int j = 0; j < K; j++) {
+    uint64_t o = 0;
+    for (int m = 0; m < k; m++)
+      if ((j >> m) & 1) o |= 1ull << t[m];
+    off[j] = o;
+  }
+#pragma omp parallel for schedule(static)
+  for (int64_t ii = 0; ii < (int64_t)N; ii++) {
+    uint64_t i = (uint64_t)ii;
+    if (i & tmask) continue;
+    cplx v[32], w[32];
+    for (int j = 0; j < K; j++) v[j] = psi[i | off[j]];
+    for (int r = 0; r < K; r++) {
+      cplx acc = 0;
+      for (int j = 0; j < K; j++) acc += M[r * K + j] * v[j];
+      w[r] = acc;
+    }
+    for (int r = 0; r < K; r++) psi[i | off[r]] = w[r];
+  }
+}
+
+/* Check the IR: kinds known, 1 <= nq <= 5, qubits in range and distinct. */
+int orc_validate(int n, const orc_gate *g, uint64_t ngates) {
+  for (uint64_t a = 0; a < ngates; a++) {
+    cplx m[1024];
+    if (g[a].kind == ORC_UNITARY && (g[a].nq < 1 || g[a].nq > 5 || !g[a].mat)) return -1;
+    int k = orc_gate_matrix(&g[a], m);
+    if (k < 0) return -1;
+    for (int x = 0; x < k; x++) {
+      if (g[a].q[x] < 0 || g[a].q[x] >= n) return -1;
+      for (int y = 0; y < x; y++)
+        if (g[a].q[x] == g[a].q[y]) return -1;
+    }
+    for (int x = 0; x < 3; x++)
+      if (!isfinite(g[a].p[x])) return -1;
+  }
+  return 0;
+}
+
+/* Run a circuit gate by gate, in order, on psi (2^n complex128). */
+int orc_run(cplx *psi, int n, const orc_gate *g, uint64_t ngates) {
+  if (orc_validate(n, g, ngates)) return -1;
+  cplx m[1024];
+  for (uint64_t a = 0; a < ngates; a++) {
+    int k = orc_gate_matrix(&g[a], m);
+    orc_apply_matrix(psi, n, k, g[a].q, m);
+  }
+  return 0;
+}
+
+/* ||psi||^2 summed sequentially in double precision. */
+double orc_norm2(const cplx *psi, uint64_t N) {
+  double s = 0.0;
+  for (uint64_t i = 0; i < N; i++) {
+    double re = creal(psi[i]), im = cimag(psi[i]);
+    s += re * re + im * im;
+  }
+  return s;
+}
+
+/* p_i = |psi_i|^2 and the sequential double-precision CDF C_i. */
+void orc_cdf(const cplx *psi, uint64_t N, double *C) {
+  double s = 0.0;
+  for (uint64_t i = 0; i < N; i++) {
+    double re = creal(psi[i]), im = cimag(psi[i]);
+    s += re * re + im * im;
+    C[i] = s;
+  }
+}
+
+/*
+ * Inverse-CDF sampling: shot s takes t = u_s * C_{N-1} and returns
+ * x = min{ i : C_i > t } (binary search over the non-decreasing C).  If no
+ * such i exists (t rounded up to the total), x is the last index with
+ * p_i > 0.  boundary[s] = 1 when t lies within eps of C_x or of C_{x-1}
+ * (C_{-1} = 0); returns the number of such boundary draws.
+ */
+uint64_t orc_sample(const double *C, uint64_t N, const double *u, uint64_t S, double eps,
+                    uint64_t *out, uint8_t *boundary) {
+  const double total = C[N - 1];
+  uint64_t last = N - 1;
+  while (last > 0 && C[last] <= C[last - 1]) last--;
+  uint64_t nb = 0;
+  for (uint64_t s = 0; s < S; s++) {
+    double t = u[s] * total;
+    uint64_t lo = 0, hi = N; /* first index in [lo, hi) with C > t */
+    while (lo < hi) {
+      uint64_t mid = lo + (hi - lo) / 2;
+      if (C[mid] > t) hi = mid; else lo = mid + 1;
+    }
+    uint64_t x = (lo < N) ? lo : last;
+    double below = x ? C[x - 1] : 0.0;
+    int b = (fabs(t - C[x]) < eps) || (fabs(t - below) < eps);
+    out[s] = x;
+    if (boundary) boundary[s] = (uint8_t)b;
+    nb += (uint64_t)b;
+  }
+  return nb;
+}
+
+/* <Z_mask> = sum_i p_i (-1)^popcount(i & mask) / sum_i p_i (sequential). */
+double orc_expect_z(const cplx *psi, uint64_t N, uint64_t zmask) {
+  double num = 0.0, den = 0.0;
+  for (uint64_t i = 0; i < N; i++) {
+    double re = creal(psi[i]), im = cimag(psi[i]);
+    double p = re * re + im * im;
+    num += (__builtin_popcountll(i & zmask) & 1) ? -p : p;
+    den += p;
+  }
+  return num / den;
+}

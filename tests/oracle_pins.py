@@ -1,0 +1,357 @@
+"""Pins for the oracle: checks against what the mathematics fixes, not against
+the oracle itself.  Each ``pin_*`` takes an ``oracle.Oracle`` and raises
+AssertionError on a mismatch, so the same pins run on the real oracle
+(test_oracle_pins.py) and on deliberately broken copies of it
+(test_oracle_mutants.py).
+
+Sources of truth used here:
+* textbook gate identities and special cases (OpenQASM 2 definitions; the paper
+  ingests OpenQASM 2 / Qiskit circuits, §III-A);
+* Kronecker-product brute force: every gate's full 2^n x 2^n unitary is built
+  from np.kron with identities and adjacent-qubit SWAP conjugations;
+* closed forms: GHZ state, QFT of a basis state (and the explicit DFT matrix /
+  numpy's inverse FFT for n <= 10);
+* invariants: norm preservation, circuit * inverse = |0...0> (the paper's
+  mirror-circuit check, §IV-A);
+* sampling (§III-B) and expectation values from the final state (§III-B):
+  a hand-worked fixture, basis states, GHZ, np.searchsorted(side="right") as
+  the library special case of "first index with C_i > t", exact ⟨Z⟩ closed forms.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+I2 = np.eye(2, dtype=np.complex128)
+X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+Y = np.array([[0, -1j], [1j, 0]], dtype=np.complex128)
+Z = np.array([[1, 0], [0, -1]], dtype=np.complex128)
+H = np.array([[1, 1], [1, -1]], dtype=np.complex128) / math.sqrt(2.0)
+S = np.array([[1, 0], [0, 1j]], dtype=np.complex128)
+T = np.array([[1, 0], [0, (1 + 1j) / math.sqrt(2.0)]], dtype=np.complex128)
+SWAP2 = np.array([[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, 1]], dtype=np.complex128)
+
+
+def _close(a, b, tol=1e-12, what=""):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    err = float(np.max(np.abs(a - b))) if a.size else 0.0
+    assert err <= tol, f"{what}: max abs err {err:.3e} > {tol:.1e}"
+
+
+# ---------------------------------------------------------------------------
+# Kronecker-product brute force (independent of the oracle's gather/scatter)
+# ---------------------------------------------------------------------------
+
+def _kron_all(mats):
+    out = np.ones((1, 1), dtype=np.complex128)
+    for m in mats:
+        out = np.kron(out, m)
+    return out
+
+
+def _adjacent_swap(n, q):
+    """Full unitary swapping qubits q and q+1 (qubit 0 = least significant)."""
+    # kron order lists the most significant qubit first.
+    mats = []
+    q_hi = n - 1
+    while q_hi >= 0:
+        if q_hi == q + 1:
+            mats.append(SWAP2)
+            q_hi -= 2
+        else:
+            mats.append(I2)
+            q_hi -= 1
+    return _kron_all(mats)
+
+
+def _low_embed(n, M):
+    """I ⊗ M with M acting on the k lowest qubits (matrix bit m = qubit m)."""
+    k = int(M.shape[0]).bit_length() - 1
+    return np.kron(np.eye(1 << (n - k), dtype=np.complex128), M)
+
+
+def kron_full(n, targets, M):
+    """Full 2^n unitary of M on `targets` (t_0 = least significant matrix bit).
+
+    Conjugate the low-embedded M by a product of adjacent swaps that carries
+    qubit t_m to position m for every m.
+    """
+    order = list(range(n))  # order[pos] = logical qubit currently at pos
+    P = np.eye(1 << n, dtype=np.complex128)
+    for m, t in enumerate(targets):
+        pos = order.index(t)
+        while pos > m:
+            P = _adjacent_swap(n, pos - 1) @ P
+            order[pos - 1], order[pos] = order[pos], order[pos - 1]
+            pos -= 1
+    return P.conj().T @ _low_embed(n, M) @ P
+
+
+def _textbook_matrix(name, params):
+    """Gate matrices from identities of the textbook gates, not from the u3 formula."""
+    if name == "h":
+        return H
+    if name == "x":
+        return X
+    if name == "y":
+        return Y
+    if name == "z":
+        return Z
+    if name == "s":
+        return S
+    if name == "sdg":
+        return S.conj().T
+    if name == "t":
+        return T
+    if name == "tdg":
+        return T.conj().T
+    if name == "rx":
+        return _expm_pauli(X, params[0])
+    if name == "ry":
+        return _expm_pauli(Y, params[0])
+    if name == "rz":
+        return _expm_pauli(Z, params[0])
+    if name == "p":
+        return np.diag([1.0, np.exp(1j * params[0])])
+    if name == "u3":
+        # U3(θ,φ,λ) = e^{i(φ+λ)/2} RZ(φ) RY(θ) RZ(λ)
+        th, ph, la = params
+        return np.exp(0.5j * (ph + la)) * (_expm_pauli(Z, ph) @ _expm_pauli(Y, th) @ _expm_pauli(Z, la))
+    if name == "cx":   # control = matrix bit 0, target = matrix bit 1
+        P0 = np.diag([1.0, 0.0]).astype(np.complex128)
+        P1 = np.diag([0.0, 1.0]).astype(np.complex128)
+        return np.kron(I2, P0) + np.kron(X, P1)
+    if name == "cz":
+        return np.diag([1, 1, 1, -1]).astype(np.complex128)
+    if name == "cp":
+        return np.diag([1, 1, 1, np.exp(1j * params[0])])
+    if name == "swap":
+        return SWAP2
+    if name == "unitary":
+        return params[0]
+    raise KeyError(name)
+
+
+def _expm_pauli(P, theta):
+    """exp(-i θ P / 2) for a Pauli P (P^2 = I)."""
+    return math.cos(theta / 2) * I2 - 1j * math.sin(theta / 2) * P
+
+
+def random_unitary(k, rng):
+    a = rng.standard_normal((1 << k, 1 << k)) + 1j * rng.standard_normal((1 << k, 1 << k))
+    q, r = np.linalg.qr(a)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+def random_state(n, rng):
+    v = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    return v / np.linalg.norm(v)
+
+
+# ---------------------------------------------------------------------------
+# pins
+# ---------------------------------------------------------------------------
+
+def pin_gate_identities(o):
+    """Every gate kind equals its textbook matrix; u3 special cases."""
+    rng = np.random.default_rng(11)
+    _close(o.gate_matrix("u3", (0,), (math.pi, 0.0, math.pi)), X, what="U3(π,0,π)=X")
+    _close(o.gate_matrix("u3", (0,), (math.pi / 2, 0.0, math.pi)), H, what="U3(π/2,0,π)=H")
+    for _ in range(5):
+        th, ph, la = rng.uniform(-math.pi, math.pi, 3)
+        _close(o.gate_matrix("u3", (0,), (th, ph, la)), _textbook_matrix("u3", (th, ph, la)),
+               what="U3 vs e^{i(φ+λ)/2} RZ RY RZ")
+        _close(o.gate_matrix("rx", (0,), (th,)), _expm_pauli(X, th), what="RX")
+        _close(o.gate_matrix("ry", (0,), (th,)), _expm_pauli(Y, th), what="RY")
+        _close(o.gate_matrix("rz", (0,), (th,)), _expm_pauli(Z, th), what="RZ")
+        _close(o.gate_matrix("p", (0,), (th,)), np.diag([1, np.exp(1j * th)]), what="P")
+        _close(o.gate_matrix("cp", (0, 1), (th,)), np.diag([1, 1, 1, np.exp(1j * th)]), what="CP")
+    for name, M in [("h", H), ("x", X), ("y", Y), ("z", Z), ("s", S), ("t", T),
+                    ("sdg", S.conj().T), ("tdg", T.conj().T), ("swap", SWAP2),
+                    ("cz", np.diag([1, 1, 1, -1]))]:
+        qs = (0, 1) if M.shape[0] == 4 else (0,)
+        _close(o.gate_matrix(name, qs), M, what=name)
+    _close(o.gate_matrix("h") @ o.gate_matrix("x") @ o.gate_matrix("h"), Z, what="HXH=Z")
+    _close(o.gate_matrix("s") @ o.gate_matrix("s"), Z, what="S^2=Z")
+    _close(o.gate_matrix("t") @ o.gate_matrix("t"), S, what="T^2=S")
+    cx = o.gate_matrix("cx", (0, 1))
+    _close(cx @ cx, np.eye(4), what="CX^2=I")
+    _close(cx, _textbook_matrix("cx", ()), what="CX = I⊗|0><0| + X⊗|1><1|")
+
+
+def pin_kron_bruteforce(o, n_max=7, gates_per=24):
+    """Oracle output equals the product of Kronecker-built full unitaries (n<=8)."""
+    rng = np.random.default_rng(5)
+    for n in range(1, n_max + 1):
+        circ = W.random_gate_soup(n, gates_per, seed=100 + n)
+        if n >= 3:
+            for _ in range(2):
+                qs = tuple(int(q) for q in rng.choice(n, size=3, replace=False))
+                circ.append(("unitary", qs, (random_unitary(3, rng),)))
+        U = np.eye(1 << n, dtype=np.complex128)
+        for name, qs, ps in circ:
+            U = kron_full(n, qs, _textbook_matrix(name, ps)) @ U
+        psi0 = random_state(n, rng)
+        _close(o.run(n, circ, psi0), U @ psi0, tol=1e-11, what=f"kron n={n}")
+        _close(o.run(n, circ), U[:, 0], tol=1e-11, what=f"kron |0> n={n}")
+
+
+def pin_apply_matrix_k5(o):
+    """A dense 5-qubit matrix on scattered targets matches the Kronecker build."""
+    rng = np.random.default_rng(7)
+    n = 7
+    for targets in [(0, 1, 2, 3, 4), (6, 2, 0, 5, 3), (1, 6, 4, 2, 5)]:
+        M = random_unitary(5, rng)
+        psi = random_state(n, rng)
+        _close(o.apply_matrix(psi, targets, M), kron_full(n, targets, M) @ psi, tol=1e-11,
+               what=f"k=5 {targets}")
+
+
+def pin_ghz(o):
+    for n in range(1, 13):
+        psi = o.run(n, W.ghz(n))
+        want = np.zeros(1 << n, dtype=np.complex128)
+        want[0] = want[-1] = 1 / math.sqrt(2.0)
+        _close(psi, want, tol=1e-13, what=f"GHZ n={n}")
+
+
+def pin_qft(o):
+    """QFT|x> = 2^{-n/2} Σ_y e^{+2πi x y / 2^n}|y>: explicit DFT matrix (n<=8),
+    numpy inverse FFT (n<=10), closed form (n<=14)."""
+    for n in range(1, 15):
+        N = 1 << n
+        x = W.basis_index(n, 40 + n)
+        psi = o.run(n, W.qft(n), _basis(n, x))
+        y = np.arange(N)
+        closed = np.exp(2j * math.pi * ((x * y) % N) / N) / math.sqrt(N)
+        _close(psi, closed, tol=1e-11, what=f"QFT closed form n={n}")
+        if n <= 10:
+            e = np.zeros(N, dtype=np.complex128)
+            e[x] = 1.0
+            _close(psi, np.fft.ifft(e) * math.sqrt(N), tol=1e-11, what=f"QFT ifft n={n}")
+        if n <= 8:
+            F = np.exp(2j * math.pi * np.outer(y, y) / N) / math.sqrt(N)
+            rng = np.random.default_rng(n)
+            v = random_state(n, rng)
+            _close(o.run(n, W.qft(n), v), F @ v, tol=1e-11, what=f"QFT DFT matrix n={n}")
+
+
+def _basis(n, x):
+    v = np.zeros(1 << n, dtype=np.complex128)
+    v[x] = 1.0
+    return v
+
+
+def pin_norm_and_mirror(o):
+    """Unitarity keeps ||psi|| = 1; C·C^-1|0> = |0> (mirror circuit, §IV-A)."""
+    for n, d, seed in [(12, 20, 1), (9, 30, 2), (13, 8, 3)]:
+        c = W.random_layered(n, d, seed)
+        psi = o.run(n, c)
+        assert abs(o.norm2(psi) - 1.0) < 1e-12, f"norm n={n}"
+        assert abs(np.vdot(psi, psi).real - 1.0) < 1e-12
+        back = o.run(n, W.inverse(c), psi)
+        assert abs(back[0]) ** 2 > 1 - 1e-12, f"mirror n={n}: {abs(back[0])**2}"
+        soup = W.random_gate_soup(n, 60, seed)
+        back2 = o.run(n, soup + W.inverse(soup))
+        assert abs(back2[0]) ** 2 > 1 - 1e-12, f"mirror soup n={n}"
+
+
+def pin_norm_sum(o):
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal(1000) + 1j * rng.standard_normal(1000)
+    assert abs(o.norm2(v) - float(np.sum(np.abs(v) ** 2))) < 1e-9
+    C = o.cdf(v)
+    _close(C, np.cumsum(np.abs(v) ** 2), tol=1e-9, what="cdf")
+
+
+def load_sampler_golden():
+    amps, rows = None, []
+    with open(os.path.join(GOLDEN, "sampler_cases.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            parts = line.split()
+            if parts[0] == "amplitudes":
+                amps = np.array([float(v) for v in parts[1:]], dtype=np.complex128)
+            else:
+                rows.append((float(parts[0]), int(parts[1]), int(parts[2])))
+    return amps, rows
+
+
+def pin_sampler(o):
+    amps, rows = load_sampler_golden()
+    u = np.array([r[0] for r in rows])
+    x, b, nb = o.sample(amps, u)
+    assert [int(v) for v in x] == [r[1] for r in rows], f"golden x {x}"
+    assert [int(v) for v in b] == [r[2] for r in rows], f"golden boundary {b}"
+    # basis states: every draw returns the basis index
+    for n, idx in [(3, 5), (6, 0), (6, 63), (8, 77)]:
+        x, _, _ = o.sample(_basis(n, idx), W.shot_uniforms(9, 500))
+        assert np.all(x == idx), f"basis {idx}"
+    # first index with C_i > t, against numpy's searchsorted(side="right")
+    rng = np.random.default_rng(21)
+    for n in (1, 3, 6, 10):
+        v = random_state(n, rng)
+        v[rng.random(1 << n) < 0.3] = 0.0
+        if not np.any(v):
+            v[0] = 1.0
+        u = W.shot_uniforms(31 + n, 3000)
+        x, _, _ = o.sample(v, u)
+        C = np.cumsum(np.abs(v) ** 2)
+        want = np.minimum(np.searchsorted(C, u * C[-1], side="right"), len(C) - 1)
+        assert np.array_equal(x.astype(np.int64), want), f"searchsorted n={n}"
+        assert np.all(np.abs(v[x.astype(np.int64)]) > 0), "zero-probability index drawn"
+    # GHZ: only 0 and 2^n-1, each near 1/2; Hellinger fidelity near 1 - N/(8S) (§IV-C)
+    n, Sh = 6, 20000
+    x, _, _ = o.sample(o.run(n, W.ghz(n)), W.shot_uniforms(77, Sh))
+    assert set(np.unique(x).tolist()) <= {0, (1 << n) - 1}
+    frac = float(np.mean(x == 0))
+    assert abs(frac - 0.5) < 5 * math.sqrt(0.25 / Sh), f"GHZ freq {frac}"
+    # chi-square against exact probabilities on a random 5-qubit state
+    v = random_state(5, rng)
+    p = np.abs(v) ** 2
+    Sh = 40000
+    x, _, _ = o.sample(v, W.shot_uniforms(5, Sh))
+    cnt = np.bincount(x.astype(np.int64), minlength=32)
+    chi2 = float(np.sum((cnt - Sh * p) ** 2 / (Sh * p)))
+    assert chi2 < 31 + 6 * math.sqrt(62), f"chi2 {chi2}"
+    hell = float(np.sum(np.sqrt(p * cnt / Sh))) ** 2
+    assert hell > 1 - 32 / (8 * Sh) * 4, f"hellinger {hell}"
+
+
+def pin_expectation(o):
+    rng = np.random.default_rng(8)
+    for _ in range(4):
+        th, ph, la = rng.uniform(-math.pi, math.pi, 3)
+        psi = o.run(1, [("u3", (0,), (th, ph, la))])
+        assert abs(o.expect_z(psi, 1) - math.cos(th)) < 1e-12, "<Z> = cos θ"
+    n = 7
+    g = o.run(n, W.ghz(n))
+    for m in range(1, 1 << n):
+        want = 1.0 if bin(m).count("1") % 2 == 0 else 0.0
+        assert abs(o.expect_z(g, m) - want) < 1e-12, f"GHZ <Z_{m}>"
+    v = random_state(n, rng) * 1.7
+    for m in (1, 5, 64, 127, 0):
+        diag = _kron_all([np.diag([1.0, -1.0]) if (m >> q) & 1 else np.eye(2)
+                          for q in range(n - 1, -1, -1)]).diagonal().real
+        want = float(np.sum(np.abs(v) ** 2 * diag) / np.sum(np.abs(v) ** 2))
+        assert abs(o.expect_z(v, m) - want) < 1e-12, f"kron <Z_{m}>"
+
+
+def pin_validate(o):
+    assert o.validate(3, [("cx", (0, 2), ())])
+    assert not o.validate(3, [("cx", (0, 3), ())]), "qubit out of range accepted"
+    assert not o.validate(3, [("cx", (1, 1), ())]), "repeated qubit accepted"
+    assert not o.validate(3, [("u3", (0,), (float("nan"), 0.0, 0.0))]), "NaN accepted"
+
+
+ALL_PINS = [pin_gate_identities, pin_kron_bruteforce, pin_apply_matrix_k5, pin_ghz, pin_qft,
+            pin_norm_and_mirror, pin_norm_sum, pin_sampler, pin_expectation, pin_validate]

@@ -1,0 +1,58 @@
+"""Plant plausible mistakes in a copy of the oracle (CPU only) and check that
+the pins catch every one of them: a pin set that a dropped term, a wrong sign,
+a swapped index or a transposed operand slips through would not pin anything.
+"""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+from oracle import build as obuild
+from tests import oracle_pins as P
+
+MUTANTS = {
+    "u3_sign": ("m[1] = -cexp(I * p[2]) * s;", "m[1] = cexp(I * p[2]) * s;"),
+    "u3_phase": ("m[3] = cexp(I * (p[1] + p[2])) * c;", "m[3] = cexp(I * (p[1] - p[2])) * c;"),
+    "u3_swap_phi_lambda": ("m[2] = cexp(I * p[1]) * s;", "m[2] = cexp(I * p[2]) * s;"),
+    "rz_sign": ("m[0] = cexp(-I * p[0] / 2.0); m[1] = 0;", "m[0] = cexp(I * p[0] / 2.0); m[1] = 0;"),
+    "y_sign": ("m[0] = 0; m[1] = -I; m[2] = I;", "m[0] = 0; m[1] = I; m[2] = -I;"),
+    "target_bit_order": ("if ((j >> m) & 1) o |= 1ull << t[m];", "if ((j >> m) & 1) o |= 1ull << t[k - 1 - m];"),
+    "cx_control_target": ("m[0 * 4 + 0] = 1; m[2 * 4 + 2] = 1; m[1 * 4 + 3] = 1; m[3 * 4 + 1] = 1;",
+                          "m[0 * 4 + 0] = 1; m[1 * 4 + 1] = 1; m[2 * 4 + 3] = 1; m[3 * 4 + 2] = 1;"),
+    "matrix_transposed": ("acc += M[r * K + j] * v[j];", "acc += M[j * K + r] * v[j];"),
+    "dropped_last_column": ("for (int j = 0; j < K; j++) acc += M", "for (int j = 0; j < K - 1; j++) acc += M"),
+    "sampler_not_strict": ("if (C[mid] > t) hi = mid;", "if (C[mid] >= t) hi = mid;"),
+    "sampler_unnormalised": ("double t = u[s] * total;", "double t = u[s];"),
+    "sampler_no_lower_boundary": ("int b = (fabs(t - C[x]) < eps) || (fabs(t - below) < eps);",
+                                  "int b = (fabs(t - C[x]) < eps);"),
+    "cdf_drops_imag": ("s += re * re + im * im;\n    C[i] = s;", "s += re * re;\n    C[i] = s;"),
+    "expect_sign": ("num += (__builtin_popcountll(i & zmask) & 1) ? -p : p;",
+                    "num += (__builtin_popcountll(i & zmask) & 1) ? p : -p;"),
+    "expect_unnormalised": ("return num / den;", "return num;"),
+    "validate_allows_duplicates": ("if (g[a].q[x] == g[a].q[y]) return -1;", "(void)y;"),
+}
+
+
+def _build_mutant(tmp_path, name):
+    old, new = MUTANTS[name]
+    src = open(obuild.SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique/not found"
+    path = os.path.join(str(tmp_path), f"{name}.c")
+    with open(path, "w") as f:
+        f.write(src.replace(old, new))
+    so = os.path.join(str(tmp_path), f"lib{name}.so")
+    subprocess.run(["gcc", "-O1", "-std=gnu99", "-fPIC", "-shared", "-o", so, path, "-lm"], check=True)
+    return oracle.Oracle(so)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(tmp_path, name):
+    o = _build_mutant(tmp_path, name)
+    caught = []
+    for pin in P.ALL_PINS:
+        try:
+            pin(o)
+        except AssertionError as e:
+            caught.append(f"{pin.__name__}: {str(e)[:60]}")
+    assert caught, f"mutant {name} passed every pin"
