@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Benchmark of the state-vector hot path on GB300.
+
+One step = the whole path on the 28-qubit workload: reset to |0..0>, apply a
+random layered circuit (n=28, depth 40, 1680 gates: fusion, pass planning and
+the pass kernels), FP64 CDF + 1e5 shots from pre-drawn uniforms, FP64 norm, a
+Z-string expectation, then reset to a seeded basis state and apply the 28-qubit
+QFT.  The complex64 state is 2 GiB, larger than the 129 MB L2, so every pass
+streams from HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  ``value`` is algorithmic HBM GB/s over the step (bytes
+the path must move: 16 B per amplitude per pass, 8 B per amplitude per reset,
+norm, CDF and expectation read) divided by device time.  ``roofline`` refers
+to the pass kernel, timed per launch with CUDA events on the state's stream.
+``--impl reference`` times the complex128 CPU oracle on a bounded sample of the
+same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+N_QUBITS = 28
+DEPTH = 40
+SEED = 2
+SHOTS = 100_000
+ZMASK = 0b1011  # <Z_0 Z_1 Z_3>
+OPTS = dict(k_max=2, tile_qubits=12, low_qubits=5, precision=0)
+METRIC = "state-vector apply HBM GB/s vs peak"
+WORKLOAD = (f"random layered n={N_QUBITS} depth={DEPTH} + QFT-{N_QUBITS} on a seeded basis state; "
+            f"FP64 norm, CDF and {SHOTS} shots; <Z> expectation")
+# DRAM bytes of one pass-kernel launch from ncu; None until captured for the
+# current kernel (see profiles/).
+PASS_TRAFFIC_BYTES = None
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.remove(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def step_bytes(plan_rand, plan_qft, n):
+    amps = float(1 << n)
+    return plan_rand["bytes"] + plan_qft["bytes"] + 5 * 8.0 * amps  # 2 resets + cdf + norm + expect
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2512_04216_gb300 import capi
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    n = N_QUBITS
+    circ = W.random_layered(n, DEPTH, SEED)
+    qft = W.qft(n)
+    x = W.basis_index(n, SEED)
+    opts = capi.make_opts(**OPTS)
+    ir_r, keep_r = capi.to_ir(circ)
+    ir_q, keep_q = capi.to_ir(qft)
+    plan_r = capi.sv_plan_stats(n, circ, opts)
+    plan_q = capi.sv_plan_stats(n, qft, opts)
+    bytes_step = step_bytes(plan_r, plan_q, n)
+
+    stream = torch.cuda.Stream(dev)
+    amps = torch.empty(1 << n, dtype=torch.complex64, device=dev)
+    h = capi.sv_wrap(amps, n, capi.SV_C64, stream)
+    u_host = W.shot_uniforms(SEED, SHOTS)
+    u_dev = torch.as_tensor(u_host, device=dev)
+    out_dev = torch.empty(SHOTS, dtype=torch.int64, device=dev)
+    L = capi._L
+    import ctypes
+
+    def step_device():
+        capi.sv_reset(h, 0)
+        capi.sv_apply_circuit(h, ir_r, len(circ), opts)
+        capi._check(L.sv_sample_uniforms(h, u_dev.data_ptr(), SHOTS, out_dev.data_ptr(), None, 1))
+        capi.sv_norm(h)
+        capi.sv_expect_pauli(h, 0, ZMASK)
+        capi.sv_reset(h, x)
+        capi.sv_apply_circuit(h, ir_q, len(qft), opts)
+
+    u_pin = torch.from_numpy(u_host).pin_memory()
+    out_host = np.empty(SHOTS, dtype=np.uint64)
+    nb = ctypes.c_uint64()
+
+    def step_e2e():
+        capi.sv_reset(h, 0)
+        capi.sv_apply_circuit(h, ir_r, len(circ), opts)
+        capi._check(L.sv_sample_uniforms(h, u_pin.data_ptr(), SHOTS, out_host.ctypes.data,
+                                         ctypes.byref(nb), 0))
+        capi.sv_norm(h)
+        capi.sv_expect_pauli(h, 0, ZMASK)
+        capi.sv_reset(h, x)
+        capi.sv_apply_circuit(h, ir_q, len(qft), opts)
+        capi.sv_synchronize(h)
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+
+    def barrier():
+        if dist:
+            td.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step_device()
+    barrier()
+
+    # ---- device-timed steps (inputs resident in HBM) ----
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    capi.sv_profile_enable(h, True)
+    capi.sv_profile_read(h)  # reset records
+    launches0 = capi.sv_launch_count()
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step_device()
+        ev1.record(stream)
+        barrier()
+    launches = capi.sv_launch_count() - launches0
+    prof = capi.sv_profile_read(h)
+    capi.sv_profile_enable(h, False)
+    dev_ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([dev_ms], device=dev)
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        dev_ms = float(t.item())
+    clocks = clk.summary()
+
+    # ---- end-to-end steps through the public API, host buffers ----
+    for _ in range(max(1, args.warmup // 2)):
+        step_e2e()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # parity spot check on the final state (QFT of |x>), outside the timed regions
+    idx = np.array([0, 1, 12345, (1 << n) - 1], dtype=np.int64)
+    got = np.array([capi_get(capi, h, int(i)) for i in idx])
+    want = np.exp(2j * np.pi * ((x * idx) % (1 << n)) / (1 << n)) / math.sqrt(1 << n)
+    spot_err = float(np.max(np.abs(got - want)))
+    capi.sv_destroy(h)
+
+    peak, peak_kind = peaks()
+    pk = prof.get("pass", {"launches": 0, "ms": float("nan"), "bytes": 0.0})
+    achieved = pk["bytes"] / (pk["ms"] * 1e-3) / 1e9 if pk["launches"] else float("nan")
+    value = world * bytes_step * args.steps / (dev_ms * 1e-3) / 1e9
+    e2e_val = world * bytes_step * args.steps / e2e_s / 1e9
+    h2d = plan_r["upload_bytes"] + plan_q["upload_bytes"] + SHOTS * 8
+    d2h = SHOTS * 8 + 8 + 3 * 8
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+        "data": "synthetic (seeded random layered circuit, QFT, SplitMix64 uniforms)",
+        "config": {"workload": WORKLOAD, "n_qubits": n, "depth": DEPTH, "gates": len(circ) + len(qft),
+                   "shots": SHOTS, "fusion_k_max": OPTS["k_max"], "tile_qubits": OPTS["tile_qubits"],
+                   "passes_per_step": plan_r["n_passes"] + plan_q["n_passes"],
+                   "l2": "inputs larger than L2 (2 GiB state vs 129 MB L2)",
+                   "parallelism": f"replicas{world}"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                     "kernel": "k_pass (one HBM pass)",
+                     "traffic": PASS_TRAFFIC_BYTES,
+                     "algorithmic_bytes_per_launch": 16 * (1 << n),
+                     "avg_launch_ms": round(pk["ms"] / max(pk["launches"], 1), 4)},
+        "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                        "GB/s": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 and v["bytes"] else None}
+                    for k, v in prof.items()},
+        "e2e": {"value": round(e2e_val, 1), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_s * 1e3 / args.steps, 3)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "spot_check_max_abs_err": spot_err,
+    }
+    return line
+
+
+def capi_get(capi, h, i):
+    out = np.empty(1, dtype=np.complex64)
+    capi.sv_get_amplitudes(h, out, i, 1, False)
+    return complex(out[0])
+
+
+def oracle_sample(gates_sample: int, measure: bool = True):
+    """Times the oracle on a bounded sample of the step at full size: the first
+    `gates_sample` gates of the random circuit on 2^28 complex128 amplitudes,
+    then (optionally) its CDF + 1e5 draws, norm and expectation.  Returns
+    (extrapolated seconds per step, threads, description)."""
+    import oracle
+    o = oracle.default()
+    o.set_threads(os.cpu_count() or 1)
+    threads = o.max_threads()
+    n = N_QUBITS
+    circ = W.random_layered(n, DEPTH, SEED)
+    total_gates = len(circ) + len(W.qft(n))
+    t0 = time.perf_counter()
+    psi = o.run(n, circ[:gates_sample])
+    t_g = (time.perf_counter() - t0) / gates_sample
+    t_m = 0.0
+    if measure:
+        t0 = time.perf_counter()
+        o.sample(psi, W.shot_uniforms(SEED, SHOTS))
+        o.norm2(psi)
+        o.expect_z(psi, ZMASK)
+        t_m = time.perf_counter() - t0
+    del psi
+    desc = (f"oracle (complex128, {threads} threads) on the first {gates_sample} of {total_gates} gates "
+            f"at n={n}{' + CDF/1e5 shots/norm/<Z>' if measure else ''}; per-gate time x {total_gates} gates"
+            f"{' + measured measurement time' if measure else ''}")
+    return t_g * total_gates + t_m, threads, desc
+
+
+def bytes_step_host():
+    from paper_2512_04216_gb300 import capi
+    n = N_QUBITS
+    opts = capi.make_opts(**OPTS)
+    return step_bytes(capi.sv_plan_stats(n, W.random_layered(n, DEPTH, SEED), opts),
+                      capi.sv_plan_stats(n, W.qft(n), opts), n)
+
+
+def run_reference(args):
+    bstep = bytes_step_host()
+    vals = []
+    desc = threads = None
+    for i in range(args.warmup + args.steps):
+        t_step, threads, desc = oracle_sample(gates_sample=4, measure=True)
+        if i >= args.warmup:
+            vals.append(t_step)
+    t = statistics.median(vals)
+    v = bstep / t / 1e9
+    return {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS},
+        "cpu_baseline": {"value": v, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": desc},
+        "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(local_rank)
+        td.init_process_group("nccl")
+    line = run_ours(args, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_step, threads, desc = oracle_sample(gates_sample=12, measure=True)
+        v = bytes_step_host() / t_step / 1e9
+        line["cpu_baseline"] = {"value": v, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": desc,
+                                "ms_per_step": t_step * 1e3}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as td
+        td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

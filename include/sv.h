@@ -1,0 +1,220 @@
+/*
+ * sv.h -- C-ABI of the GB300 state-vector library (libsvgb.so).
+ *
+ * The library keeps a 2^n complex amplitude vector resident in GPU memory,
+ * applies a circuit given as a flat gate IR, and returns amplitudes,
+ * probabilities, measurement samples or Z-string expectation values.  This is
+ * the "circuit IR in; samples, expectations or amplitudes out" interface of
+ * the paper's state-vector backend (§III-A common IR, §II state-vector method,
+ * §III-B end-of-circuit sampling and cached-state expectation values).
+ *
+ * Conventions (all functions):
+ *  - Every function returns SV_OK (0) or a negative sv_status and never aborts.
+ *    On failure sv_last_error() describes the cause.
+ *  - Qubit q is bit q of the amplitude index (little-endian).  Amplitudes are
+ *    complex64 stored interleaved (re, im) as two float32 -- 8 bytes each.
+ *  - Work is queued asynchronously on the state's CUDA stream.  Functions that
+ *    return host values (sv_norm, sv_expect_pauli, sv_sample* into host
+ *    buffers, sv_get_amplitudes/sv_probabilities into host buffers) synchronise
+ *    the stream before returning.
+ *  - Pointers passed in are owned by the caller and only read/written during
+ *    the call (device outputs: until the stream reaches that point).  A state
+ *    is owned by the library unless created with sv_wrap.
+ *  - A CUDA error marks the state as poisoned: later calls on it return
+ *    SV_ERR_STATE; only sv_destroy is allowed.
+ *  - No function is thread-safe on the same state; distinct states may be used
+ *    from distinct threads.  sv_last_error() is per thread.
+ */
+#ifndef SVGB_SV_H
+#define SVGB_SV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sv_state sv_state; /* opaque */
+
+enum sv_dtype { SV_C64 = 1, SV_C128 = 2 /* not supported: SV_ERR_UNSUPPORTED */ };
+
+enum sv_status {
+  SV_OK = 0,
+  SV_ERR_ARG = -1,         /* invalid argument or invalid IR */
+  SV_ERR_OOM = -2,         /* device or pinned-host allocation failed */
+  SV_ERR_CUDA = -3,        /* a CUDA call failed; the state is now poisoned */
+  SV_ERR_UNSUPPORTED = -4, /* valid request this build does not implement */
+  SV_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+  SV_ERR_STATE = -6        /* the state was poisoned by an earlier failure */
+};
+
+/*
+ * Gate kinds of the IR, with OpenQASM 2 semantics (the paper's front end takes
+ * Qiskit circuits and OpenQASM 2, §III-A):
+ *   U3(θ,φ,λ) = [[cos θ/2, -e^{iλ} sin θ/2], [e^{iφ} sin θ/2, e^{i(φ+λ)} cos θ/2]]
+ *   RX, RY, RZ(θ) = exp(-iθP/2); P(λ) = diag(1, e^{iλ}); H, X, Y, Z, S, SDG, T, TDG.
+ *   CX(c,t): q[0] = control, q[1] = target.  CZ, CP(λ) = diag(1,1,1,e^{iλ}), SWAP.
+ *   UNITARY: a dense 2^nq x 2^nq matrix (nq <= 5) given by `mat`.
+ * For a gate on q[0..nq-1], bit m of the matrix row/column index refers to
+ * qubit q[m] (q[0] is the least significant matrix bit).
+ */
+enum sv_gate_kind {
+  SV_GATE_U3 = 1, SV_GATE_H, SV_GATE_X, SV_GATE_Y, SV_GATE_Z, SV_GATE_S, SV_GATE_SDG,
+  SV_GATE_T, SV_GATE_TDG, SV_GATE_RX, SV_GATE_RY, SV_GATE_RZ, SV_GATE_P, SV_GATE_CX,
+  SV_GATE_CZ, SV_GATE_CP, SV_GATE_SWAP, SV_GATE_UNITARY
+};
+
+/* One IR gate (56 bytes; plain data). */
+typedef struct sv_gate {
+  uint8_t kind;       /* sv_gate_kind */
+  uint8_t nq;         /* number of qubits: 1 or 2 for named kinds, 1..5 for UNITARY */
+  uint16_t reserved;  /* must be 0 */
+  int32_t q[5];       /* target qubits, distinct, each in [0, n) */
+  double p[3];        /* angles (radians) for U3 (θ,φ,λ), RX/RY/RZ/P/CP (p[0]) */
+  const double *mat;  /* UNITARY only: host pointer to 2^nq x 2^nq complex128,
+                         row-major, interleaved (re, im); read during the call */
+} sv_gate;
+
+/* Options of sv_apply_circuit.  Zero fields take the library default. */
+typedef struct sv_opts {
+  int32_t k_max;       /* fusion width: gates are fused into dense blocks of at most
+                          k_max qubits (1..5; default 2) */
+  int32_t tile_qubits; /* T: qubits held by one CTA tile in shared memory per HBM
+                          pass (5..13; default 12; clamped to n) */
+  int32_t low_qubits;  /* c: low qubits every tile contains, so each global access
+                          is a run of 2^c contiguous amplitudes (1..T; default 5) */
+  int32_t precision;   /* 0 = FP32 CUDA cores for every block;
+                          1 = 3xTF32 tensor cores (tcgen05) for 4-5 qubit blocks */
+} sv_opts;
+
+/* Statistics of the fusion + pass plan of a circuit (host-side only). */
+typedef struct sv_plan_info {
+  uint64_t n_gates;    /* IR gates */
+  uint64_t n_blocks;   /* dense fused blocks after fusion */
+  uint64_t n_phase;    /* diagonal phase ops (gates whose qubits leave the tile) */
+  uint64_t n_passes;   /* HBM passes (one read + one write of the state each) */
+  uint64_t hist_k[6];  /* hist_k[k] = dense blocks with k qubits */
+  uint64_t flops;      /* useful real flops of the dense blocks over the whole state */
+  uint64_t bytes;      /* algorithmic HBM bytes: n_passes * 2 * 2^n * 8 */
+  uint64_t upload_bytes; /* size of the packed plan copied host -> device per apply */
+} sv_plan_info;
+
+/* ---- lifetime ------------------------------------------------------------ */
+
+/* Allocate a 2^n_qubits complex64 state on the current CUDA device (cudaMalloc;
+ * 8 * 2^n bytes) and set it to |0...0>.  n_qubits in [1, 36].  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  *out receives the handle. */
+int sv_create(int n_qubits, int dtype, void *cuda_stream, sv_state **out);
+
+/* Wrap a caller-owned device buffer of 2^n_qubits complex64 amplitudes (e.g. a
+ * torch tensor's storage, 16-byte aligned).  The contents are used as-is; the
+ * buffer must outlive the handle and is never freed by the library. */
+int sv_wrap(void *dev_ptr, int n_qubits, int dtype, void *cuda_stream, sv_state **out);
+
+/* Free the handle, its scratch buffers and (if owned) the amplitudes.  Waits
+ * for the state's stream.  NULL is accepted. */
+int sv_destroy(sv_state *s);
+
+/* Change the stream later work is queued on. */
+int sv_set_stream(sv_state *s, void *cuda_stream);
+
+/* Wait for all queued work on the state's stream. */
+int sv_synchronize(sv_state *s);
+
+/* Set the state to the basis vector |basis_index> (< 2^n). */
+int sv_reset(sv_state *s, uint64_t basis_index);
+
+/* Number of qubits of the state (or SV_ERR_ARG). */
+int sv_num_qubits(const sv_state *s);
+
+/* Device pointer of the amplitudes (2^n complex64). */
+void *sv_device_ptr(sv_state *s);
+
+/* ---- apply --------------------------------------------------------------- */
+
+/*
+ * Apply gates ir[0..n_gates-1] in order:  psi <- U_{G-1} ... U_0 psi.
+ * The host validates the IR (kinds, qubits distinct and < n, finite angles),
+ * fuses gates into dense blocks of at most k_max qubits, groups blocks into
+ * HBM passes whose qubits fit one shared-memory tile, and launches one kernel
+ * per pass on the state's stream.  opts may be NULL.  Returns SV_ERR_ARG for
+ * an invalid IR (nothing is applied).  Asynchronous.
+ */
+int sv_apply_circuit(sv_state *s, const sv_gate *ir, size_t n_gates, const sv_opts *opts);
+
+/* Fusion + pass-plan statistics for a circuit on n qubits (no GPU work). */
+int sv_plan_stats(int n_qubits, const sv_gate *ir, size_t n_gates, const sv_opts *opts,
+                  sv_plan_info *out);
+
+/* ---- readout ------------------------------------------------------------- */
+
+/* ||psi||^2: |a_i|^2 formed exactly from the float32 parts, accumulated with
+ * compensated float32 sums per 64 amplitudes and double precision above. */
+int sv_norm(sv_state *s, double *out_norm2);
+
+/* out[j] = |a_{offset+j}|^2 in double precision, j < count.  out is a device
+ * pointer if out_on_device, else host memory. */
+int sv_probabilities(sv_state *s, double *out, uint64_t offset, uint64_t count, int out_on_device);
+
+/* Copy amplitudes [offset, offset+count) (complex64, interleaved) to out. */
+int sv_get_amplitudes(sv_state *s, void *out, uint64_t offset, uint64_t count, int out_on_device);
+
+/* Overwrite amplitudes [offset, offset+count) from in (complex64). */
+int sv_set_amplitudes(sv_state *s, const void *in, uint64_t offset, uint64_t count, int in_on_device);
+
+/*
+ * Measure all qubits `shots` times from the current state (end-of-circuit
+ * sampling, §III-B).  With the CDF C_i = sum_{j<=i} |a_j|^2 (double precision)
+ * and uniform u in [0,1), a draw returns x = min{ i : C_i > u * C_{N-1} }.
+ * sv_sample draws u_s (s = 0..shots-1) on the device from `seed` with
+ * counter-based SplitMix64: u_s = (mix64(seed + (s+1)*0x9E3779B97F4A7C15) >> 11) * 2^-53.
+ * sv_sample_uniforms takes the uniforms from the caller.  out_bitstrings[s]
+ * receives x for draw s, in draw order.  out_n_boundary (may be NULL) receives
+ * how many draws fell within 1e-9 of a CDF boundary of this state.
+ * Buffers are device pointers if on_device, else host memory.
+ */
+int sv_sample(sv_state *s, uint64_t shots, uint64_t seed, uint64_t *out_bitstrings,
+              int on_device);
+int sv_sample_uniforms(sv_state *s, const double *uniforms, uint64_t shots,
+                       uint64_t *out_bitstrings, uint64_t *out_n_boundary, int on_device);
+
+/*
+ * Expectation of the Pauli string X^x_mask Z^z_mask (cached-state expectation
+ * values, §III-B): <Z_mask> = sum_i |a_i|^2 (-1)^popcount(i & z_mask) / ||psi||^2.
+ * x_mask != 0 returns SV_ERR_UNSUPPORTED.
+ */
+int sv_expect_pauli(sv_state *s, uint64_t x_mask, uint64_t z_mask, double *out);
+
+/* ---- profiling ----------------------------------------------------------- */
+
+/* Per-kernel-kind launch records.  When enabled, the library brackets every
+ * launch with CUDA events on the state's stream. */
+typedef struct sv_kernel_stat {
+  char name[32];       /* kernel kind */
+  uint64_t launches;
+  double ms;           /* summed event time */
+  double bytes;        /* summed algorithmic HBM bytes */
+} sv_kernel_stat;
+
+int sv_profile_enable(sv_state *s, int on);
+/* Synchronises; writes up to cap records; *n_out = number of kinds. Resets. */
+int sv_profile_read(sv_state *s, sv_kernel_stat *out, int cap, int *n_out);
+
+/* ---- errors ---------------------------------------------------------------*/
+
+/* Message of the last failure on this thread ("" if none). */
+const char *sv_last_error(void);
+
+/* Library version string. */
+const char *sv_version(void);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all states, all devices); a memset is not counted. */
+uint64_t sv_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SVGB_SV_H */

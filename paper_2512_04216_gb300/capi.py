@@ -1,0 +1,268 @@
+"""ctypes binding of libsvgb.so (include/sv.h): same names, argument marshalling only.
+
+Every function here calls straight into the C-ABI; no step of the hot path runs
+in Python.  A non-zero status raises ``SvError`` carrying the library's
+``sv_last_error()`` message.  If the library has not been built this module
+raises ImportError -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsvgb.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build the CUDA library first "
+        "(python -m paper_2512_04216_gb300.build, or __graft_entry__.build())")
+
+_L = ctypes.CDLL(LIB_PATH)
+
+SV_OK, SV_ERR_ARG, SV_ERR_OOM, SV_ERR_CUDA, SV_ERR_UNSUPPORTED, SV_ERR_TIMEOUT, SV_ERR_STATE = (
+    0, -1, -2, -3, -4, -5, -6)
+SV_C64, SV_C128 = 1, 2
+
+GATE_KIND = {
+    "u3": 1, "h": 2, "x": 3, "y": 4, "z": 5, "s": 6, "sdg": 7, "t": 8, "tdg": 9, "rx": 10,
+    "ry": 11, "rz": 12, "p": 13, "cx": 14, "cz": 15, "cp": 16, "swap": 17, "unitary": 18,
+}
+
+GATE_DTYPE = np.dtype([("kind", "u1"), ("nq", "u1"), ("reserved", "<u2"), ("q", "<i4", (5,)),
+                       ("p", "<f8", (3,)), ("mat", "<u8")], align=True)
+assert GATE_DTYPE.itemsize == 56
+
+
+class SvError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class sv_opts(ctypes.Structure):
+    _fields_ = [("k_max", ctypes.c_int32), ("tile_qubits", ctypes.c_int32),
+                ("low_qubits", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+class sv_plan_info(ctypes.Structure):
+    _fields_ = [("n_gates", ctypes.c_uint64), ("n_blocks", ctypes.c_uint64),
+                ("n_phase", ctypes.c_uint64), ("n_passes", ctypes.c_uint64),
+                ("hist_k", ctypes.c_uint64 * 6), ("flops", ctypes.c_uint64),
+                ("bytes", ctypes.c_uint64), ("upload_bytes", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {"n_gates": self.n_gates, "n_blocks": self.n_blocks, "n_phase": self.n_phase,
+                "n_passes": self.n_passes, "hist_k": list(self.hist_k), "flops": self.flops,
+                "bytes": self.bytes, "upload_bytes": self.upload_bytes}
+
+
+class sv_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64),
+                ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_u64 = ctypes.c_uint64
+_i = ctypes.c_int
+_SIGS = {
+    "sv_create": ([_i, _i, _P, ctypes.POINTER(_P)], _i),
+    "sv_wrap": ([_P, _i, _i, _P, ctypes.POINTER(_P)], _i),
+    "sv_destroy": ([_P], _i),
+    "sv_set_stream": ([_P, _P], _i),
+    "sv_synchronize": ([_P], _i),
+    "sv_reset": ([_P, _u64], _i),
+    "sv_num_qubits": ([_P], _i),
+    "sv_device_ptr": ([_P], _P),
+    "sv_apply_circuit": ([_P, _P, ctypes.c_size_t, _P], _i),
+    "sv_plan_stats": ([_i, _P, ctypes.c_size_t, _P, _P], _i),
+    "sv_norm": ([_P, _P], _i),
+    "sv_probabilities": ([_P, _P, _u64, _u64, _i], _i),
+    "sv_get_amplitudes": ([_P, _P, _u64, _u64, _i], _i),
+    "sv_set_amplitudes": ([_P, _P, _u64, _u64, _i], _i),
+    "sv_sample": ([_P, _u64, _u64, _P, _i], _i),
+    "sv_sample_uniforms": ([_P, _P, _u64, _P, _P, _i], _i),
+    "sv_expect_pauli": ([_P, _u64, _u64, _P], _i),
+    "sv_profile_enable": ([_P, _i], _i),
+    "sv_profile_read": ([_P, _P, _i, _P], _i),
+    "sv_last_error": ([], ctypes.c_char_p),
+    "sv_version": ([], ctypes.c_char_p),
+    "sv_launch_count": ([], ctypes.c_uint64),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_L, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+EXPORTED = tuple(_SIGS)
+
+
+def _check(rc: int):
+    if rc != SV_OK:
+        raise SvError(rc, _L.sv_last_error().decode())
+
+
+def _ptr(x) -> int:
+    """Address of a numpy array or torch tensor (device or host)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return int(x.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# IR marshalling
+# ---------------------------------------------------------------------------
+
+def to_ir(circuit):
+    """(name, qubits, params) tuples -> (sv_gate array, keep-alive list)."""
+    ir = np.zeros(max(len(circuit), 1), dtype=GATE_DTYPE)
+    keep = []
+    for a, (name, qs, ps) in enumerate(circuit):
+        ir["kind"][a] = GATE_KIND[name]
+        ir["nq"][a] = len(qs)
+        ir["q"][a, : len(qs)] = qs
+        if name == "unitary":
+            m = np.ascontiguousarray(np.asarray(ps[0], dtype=np.complex128))
+            keep.append(m)
+            ir["mat"][a] = m.ctypes.data
+        else:
+            ir["p"][a, : len(ps)] = ps
+    return ir, keep
+
+
+def make_opts(k_max=0, tile_qubits=0, low_qubits=0, precision=0):
+    return sv_opts(int(k_max), int(tile_qubits), int(low_qubits), int(precision))
+
+
+# ---------------------------------------------------------------------------
+# the C-ABI, one wrapper per entry point
+# ---------------------------------------------------------------------------
+
+def sv_version() -> str:
+    return _L.sv_version().decode()
+
+
+def sv_launch_count() -> int:
+    return int(_L.sv_launch_count())
+
+
+def sv_last_error() -> str:
+    return _L.sv_last_error().decode()
+
+
+def sv_create(n_qubits: int, dtype: int = SV_C64, stream=None):
+    h = _P()
+    _check(_L.sv_create(n_qubits, dtype, _stream_ptr(stream), ctypes.byref(h)))
+    return h
+
+
+def sv_wrap(dev_tensor, n_qubits: int, dtype: int = SV_C64, stream=None):
+    h = _P()
+    _check(_L.sv_wrap(_ptr(dev_tensor), n_qubits, dtype, _stream_ptr(stream), ctypes.byref(h)))
+    return h
+
+
+def sv_destroy(h):
+    _check(_L.sv_destroy(h))
+
+
+def sv_set_stream(h, stream):
+    _check(_L.sv_set_stream(h, _stream_ptr(stream)))
+
+
+def sv_synchronize(h):
+    _check(_L.sv_synchronize(h))
+
+
+def sv_reset(h, basis_index: int = 0):
+    _check(_L.sv_reset(h, int(basis_index)))
+
+
+def sv_num_qubits(h) -> int:
+    return int(_L.sv_num_qubits(h))
+
+
+def sv_device_ptr(h) -> int:
+    return int(_L.sv_device_ptr(h) or 0)
+
+
+def sv_apply_circuit(h, ir, n_gates=None, opts=None):
+    """ir: an sv_gate ndarray (see to_ir) with n_gates rows, or a circuit list."""
+    keep = None
+    if not isinstance(ir, np.ndarray):
+        n_gates = len(ir)
+        ir, keep = to_ir(ir)
+    elif n_gates is None:
+        n_gates = ir.shape[0]
+    _check(_L.sv_apply_circuit(h, ir.ctypes.data, int(n_gates),
+                               ctypes.byref(opts) if opts is not None else None))
+    return keep
+
+
+def sv_plan_stats(n_qubits, circuit, opts=None) -> dict:
+    ir, keep = to_ir(circuit)
+    info = sv_plan_info()
+    _check(_L.sv_plan_stats(n_qubits, ir.ctypes.data, len(circuit),
+                            ctypes.byref(opts) if opts is not None else None, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def sv_norm(h) -> float:
+    out = ctypes.c_double()
+    _check(_L.sv_norm(h, ctypes.byref(out)))
+    return out.value
+
+
+def sv_probabilities(h, out, offset: int, count: int, out_on_device: bool):
+    _check(_L.sv_probabilities(h, _ptr(out), int(offset), int(count), int(bool(out_on_device))))
+
+
+def sv_get_amplitudes(h, out, offset: int, count: int, out_on_device: bool):
+    _check(_L.sv_get_amplitudes(h, _ptr(out), int(offset), int(count), int(bool(out_on_device))))
+
+
+def sv_set_amplitudes(h, src, offset: int, count: int, in_on_device: bool):
+    _check(_L.sv_set_amplitudes(h, _ptr(src), int(offset), int(count), int(bool(in_on_device))))
+
+
+def sv_sample(h, shots: int, seed: int, out, on_device: bool):
+    _check(_L.sv_sample(h, int(shots), int(seed) & (2**64 - 1), _ptr(out), int(bool(on_device))))
+
+
+def sv_sample_uniforms(h, uniforms, shots: int, out, on_device: bool) -> int:
+    nb = ctypes.c_uint64()
+    _check(_L.sv_sample_uniforms(h, _ptr(uniforms), int(shots), _ptr(out), ctypes.byref(nb),
+                                 int(bool(on_device))))
+    return int(nb.value)
+
+
+def sv_expect_pauli(h, x_mask: int, z_mask: int) -> float:
+    out = ctypes.c_double()
+    _check(_L.sv_expect_pauli(h, int(x_mask), int(z_mask), ctypes.byref(out)))
+    return out.value
+
+
+def sv_profile_enable(h, on: bool = True):
+    _check(_L.sv_profile_enable(h, int(bool(on))))
+
+
+def sv_profile_read(h) -> dict:
+    cap = 32
+    arr = (sv_kernel_stat * cap)()
+    n = ctypes.c_int()
+    _check(_L.sv_profile_read(h, ctypes.cast(arr, _P), cap, ctypes.byref(n)))
+    return {arr[i].name.decode(): {"launches": int(arr[i].launches), "ms": float(arr[i].ms),
+                                   "bytes": float(arr[i].bytes)} for i in range(min(n.value, cap))}

@@ -1,0 +1,545 @@
+// sv_capi.cu -- the extern "C" entry points declared in include/sv.h.
+//
+// State handles own (or wrap) the amplitude buffer, a device copy of the
+// current plan, and scratch buffers for the measurement kernels.  Every entry
+// point validates its arguments, switches to the state's device for the
+// duration of the call, and maps CUDA failures to status codes.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/sv.h"
+#include "sv_internal.h"
+#include "sv_plan.h"
+
+using namespace svgb;
+
+std::atomic<uint64_t> svgb::g_launches{0};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+struct ProfRec {
+  const char *name;
+  cudaEvent_t a, b;
+  double bytes;
+};
+
+}  // namespace
+
+struct sv_state {
+  int n = 0;
+  int device = 0;
+  float2 *amp = nullptr;
+  bool owned = false;
+  bool poisoned = false;
+  cudaStream_t stream = nullptr;
+  // plan staging
+  uint8_t *plan_dev = nullptr;
+  size_t plan_cap = 0;
+  uint8_t *plan_host = nullptr;
+  size_t plan_host_cap = 0;
+  cudaEvent_t plan_evt = nullptr;
+  bool plan_evt_live = false;
+  // measurement scratch
+  MeasureScratch ms;
+  double *dscal = nullptr;       // device scalars: [0] sum p, [1] sum pz, [2] total
+  uint64_t *dcount = nullptr;    // boundary counter
+  double *hscal = nullptr;       // pinned host scalars
+  void *stage = nullptr;         // device staging for host in/out buffers
+  size_t stage_cap = 0;
+  // profiling
+  bool prof = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> evpool;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int cuda_fail(sv_state *s, cudaError_t e, const char *what) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();  // allocation failures do not poison the context
+    return fail(SV_ERR_OOM, "%s: out of memory", what);
+  }
+  if (s) s->poisoned = true;
+  return fail(SV_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(s, expr)                                         \
+  do {                                                      \
+    cudaError_t _e = (expr);                                \
+    if (_e != cudaSuccess) return cuda_fail((s), _e, #expr); \
+  } while (0)
+
+#define CHECK_STATE(s)                                                                     \
+  do {                                                                                     \
+    if (!(s)) return fail(SV_ERR_ARG, "null state");                                       \
+    if ((s)->poisoned) return fail(SV_ERR_STATE, "state poisoned by an earlier CUDA error"); \
+  } while (0)
+
+cudaEvent_t take_event(sv_state *s) {
+  if (!s->evpool.empty()) {
+    cudaEvent_t e = s->evpool.back();
+    s->evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Runs `launch` bracketed by profiling events when profiling is on.
+template <class F>
+cudaError_t timed(sv_state *s, const char *name, double bytes, F &&launch) {
+  if (!s->prof) return launch();
+  ProfRec r{name, take_event(s), take_event(s), bytes};
+  if (!r.a || !r.b) return launch();
+  cudaEventRecord(r.a, s->stream);
+  cudaError_t e = launch();
+  cudaEventRecord(r.b, s->stream);
+  s->recs.push_back(r);
+  return e;
+}
+
+int ensure_dev(sv_state *s, void **p, size_t *cap, size_t need, const char *what) {
+  if (*cap >= need) return SV_OK;
+  if (*p) {
+    CK(s, cudaStreamSynchronize(s->stream));
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+  }
+  size_t bytes = need < 256 ? 256 : need;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) return cuda_fail(s, e, what);
+  *cap = bytes;
+  return SV_OK;
+}
+
+int ensure_scalars(sv_state *s) {
+  if (!s->dscal) {
+    CK(s, cudaMalloc(&s->dscal, 8 * sizeof(double)));
+  }
+  if (!s->dcount) {
+    CK(s, cudaMalloc(&s->dcount, 8 * sizeof(uint64_t)));
+  }
+  if (!s->hscal) {
+    CK(s, cudaMallocHost(&s->hscal, 8 * sizeof(double)));
+  }
+  return SV_OK;
+}
+
+int ensure_reduce(sv_state *s) {
+  int rc = ensure_scalars(s);
+  if (rc) return rc;
+  const size_t parts = reduce_parts(s->n);
+  if (s->ms.n_part * 1 < parts) {
+    if (s->ms.part) {
+      CK(s, cudaStreamSynchronize(s->stream));
+      cudaFree(s->ms.part);
+      s->ms.part = nullptr;
+    }
+    CK(s, cudaMalloc(&s->ms.part, 2 * parts * sizeof(double)));
+    s->ms.n_part = parts;
+  }
+  return SV_OK;
+}
+
+int ensure_cdf(sv_state *s) {
+  int rc = ensure_reduce(s);
+  if (rc) return rc;
+  const uint64_t N = uint64_t(1) << s->n;
+  const size_t nchunk = size_t((N + 63) >> kChunkBits);
+  const size_t nblock = size_t((N + 4095) >> kBlockBits);
+  if (s->ms.n_chunk < nchunk) {
+    if (s->ms.chunk) {
+      CK(s, cudaStreamSynchronize(s->stream));
+      cudaFree(s->ms.chunk);
+      s->ms.chunk = nullptr;
+    }
+    CK(s, cudaMalloc(&s->ms.chunk, nchunk * sizeof(double)));
+    s->ms.n_chunk = nchunk;
+  }
+  if (s->ms.n_block < nblock) {
+    if (s->ms.block) {
+      CK(s, cudaStreamSynchronize(s->stream));
+      cudaFree(s->ms.block);
+      s->ms.block = nullptr;
+    }
+    CK(s, cudaMalloc(&s->ms.block, nblock * sizeof(double)));
+    s->ms.n_block = nblock;
+  }
+  return SV_OK;
+}
+
+int new_state(int n, int dtype, void *stream, sv_state **out) {
+  if (!out) return fail(SV_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (dtype == SV_C128) return fail(SV_ERR_UNSUPPORTED, "complex128 states are not supported");
+  if (dtype != SV_C64) return fail(SV_ERR_ARG, "unknown dtype %d", dtype);
+  if (n < 1 || n > 36) return fail(SV_ERR_ARG, "n_qubits must be in [1,36], got %d", n);
+  sv_state *s = new sv_state();
+  s->n = n;
+  s->stream = static_cast<cudaStream_t>(stream);
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    delete s;
+    return fail(SV_ERR_CUDA, "no CUDA device");
+  }
+  *out = s;
+  return SV_OK;
+}
+
+void free_state(sv_state *s) {
+  if (!s) return;
+  DeviceGuard g(s->device);
+  cudaStreamSynchronize(s->stream);
+  if (s->owned && s->amp) cudaFree(s->amp);
+  if (s->plan_dev) cudaFree(s->plan_dev);
+  if (s->plan_host) cudaFreeHost(s->plan_host);
+  if (s->plan_evt) cudaEventDestroy(s->plan_evt);
+  if (s->ms.chunk) cudaFree(s->ms.chunk);
+  if (s->ms.block) cudaFree(s->ms.block);
+  if (s->ms.part) cudaFree(s->ms.part);
+  if (s->dscal) cudaFree(s->dscal);
+  if (s->dcount) cudaFree(s->dcount);
+  if (s->hscal) cudaFreeHost(s->hscal);
+  if (s->stage) cudaFree(s->stage);
+  for (auto &r : s->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : s->evpool) cudaEventDestroy(e);
+  delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sv_last_error(void) { return g_err.c_str(); }
+
+const char *sv_version(void) { return "svgb 0.1 (sm_103a)"; }
+
+uint64_t sv_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int sv_create(int n_qubits, int dtype, void *cuda_stream, sv_state **out) {
+  int rc = new_state(n_qubits, dtype, cuda_stream, out);
+  if (rc) return rc;
+  sv_state *s = *out;
+  const size_t bytes = (size_t(1) << n_qubits) * sizeof(float2);
+  cudaError_t e = cudaMalloc(&s->amp, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    *out = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? SV_ERR_OOM : SV_ERR_CUDA,
+                "cudaMalloc of %zu bytes for a %d-qubit state: %s", bytes, n_qubits,
+                cudaGetErrorString(e));
+  }
+  s->owned = true;
+  e = launch_reset(s->amp, n_qubits, 0, s->stream);
+  if (e != cudaSuccess) {
+    free_state(s);
+    *out = nullptr;
+    return fail(SV_ERR_CUDA, "reset: %s", cudaGetErrorString(e));
+  }
+  return SV_OK;
+}
+
+int sv_wrap(void *dev_ptr, int n_qubits, int dtype, void *cuda_stream, sv_state **out) {
+  if (!dev_ptr) return fail(SV_ERR_ARG, "dev_ptr is null");
+  if (reinterpret_cast<uintptr_t>(dev_ptr) % 16) return fail(SV_ERR_ARG, "dev_ptr must be 16-byte aligned");
+  int rc = new_state(n_qubits, dtype, cuda_stream, out);
+  if (rc) return rc;
+  (*out)->amp = static_cast<float2 *>(dev_ptr);
+  (*out)->owned = false;
+  return SV_OK;
+}
+
+int sv_destroy(sv_state *s) {
+  free_state(s);
+  return SV_OK;
+}
+
+int sv_set_stream(sv_state *s, void *cuda_stream) {
+  if (!s) return fail(SV_ERR_ARG, "null state");
+  s->stream = static_cast<cudaStream_t>(cuda_stream);
+  return SV_OK;
+}
+
+int sv_synchronize(sv_state *s) {
+  CHECK_STATE(s);
+  DeviceGuard g(s->device);
+  CK(s, cudaStreamSynchronize(s->stream));
+  return SV_OK;
+}
+
+int sv_num_qubits(const sv_state *s) { return s ? s->n : SV_ERR_ARG; }
+
+void *sv_device_ptr(sv_state *s) { return s ? s->amp : nullptr; }
+
+int sv_reset(sv_state *s, uint64_t basis_index) {
+  CHECK_STATE(s);
+  if (basis_index >> s->n) return fail(SV_ERR_ARG, "basis index out of range");
+  DeviceGuard g(s->device);
+  CK(s, timed(s, "reset", double(size_t(8) << s->n),
+              [&] { return launch_reset(s->amp, s->n, basis_index, s->stream); }));
+  return SV_OK;
+}
+
+int sv_plan_stats(int n_qubits, const sv_gate *ir, size_t n_gates, const sv_opts *opts,
+                  sv_plan_info *out) {
+  if (!out) return fail(SV_ERR_ARG, "out is null");
+  if (n_qubits < 1 || n_qubits > 36) return fail(SV_ERR_ARG, "n_qubits must be in [1,36]");
+  if (n_gates && !ir) return fail(SV_ERR_ARG, "ir is null");
+  Plan plan;
+  std::string err;
+  if (!build_plan(n_qubits, ir, n_gates, opts, plan, err)) return fail(SV_ERR_ARG, "%s", err.c_str());
+  *out = plan.info;
+  return SV_OK;
+}
+
+int sv_apply_circuit(sv_state *s, const sv_gate *ir, size_t n_gates, const sv_opts *opts) {
+  CHECK_STATE(s);
+  if (n_gates == 0) return SV_OK;
+  if (!ir) return fail(SV_ERR_ARG, "ir is null");
+  if (opts && opts->precision == 1)
+    return fail(SV_ERR_UNSUPPORTED, "precision=1 (3xTF32 tensor cores) is not built in this library");
+  Plan plan;
+  std::string err;
+  if (!build_plan(s->n, ir, n_gates, opts, plan, err)) return fail(SV_ERR_ARG, "%s", err.c_str());
+  DeviceGuard g(s->device);
+  const size_t bytes = plan.bytes.size();
+  // host staging: wait until the previous upload has left the pinned buffer
+  if (s->plan_evt_live) {
+    CK(s, cudaEventSynchronize(s->plan_evt));
+    s->plan_evt_live = false;
+  }
+  if (s->plan_host_cap < bytes) {
+    if (s->plan_host) cudaFreeHost(s->plan_host);
+    s->plan_host = nullptr;
+    s->plan_host_cap = 0;
+    CK(s, cudaMallocHost(&s->plan_host, bytes * 2));
+    s->plan_host_cap = bytes * 2;
+  }
+  {
+    void *p = s->plan_dev;
+    int rc = ensure_dev(s, &p, &s->plan_cap, bytes * 2, "plan buffer");
+    s->plan_dev = static_cast<uint8_t *>(p);
+    if (rc) return rc;
+  }
+  if (!s->plan_evt) CK(s, cudaEventCreateWithFlags(&s->plan_evt, cudaEventDisableTiming));
+  std::memcpy(s->plan_host, plan.bytes.data(), bytes);
+  CK(s, cudaMemcpyAsync(s->plan_dev, s->plan_host, bytes, cudaMemcpyHostToDevice, s->stream));
+  CK(s, cudaEventRecord(s->plan_evt, s->stream));
+  s->plan_evt_live = true;
+  const double pass_bytes = 16.0 * double(uint64_t(1) << s->n);
+  for (size_t p = 0; p < plan.passes.size(); p++) {
+    CK(s, timed(s, "pass", pass_bytes, [&] {
+         return launch_pass(s->amp, s->plan_dev, plan.pass_offs[p], plan.passes[p], s->stream);
+       }));
+  }
+  return SV_OK;
+}
+
+int sv_norm(sv_state *s, double *out_norm2) {
+  CHECK_STATE(s);
+  if (!out_norm2) return fail(SV_ERR_ARG, "out is null");
+  DeviceGuard g(s->device);
+  int rc = ensure_reduce(s);
+  if (rc) return rc;
+  CK(s, timed(s, "reduce", double(size_t(8) << s->n), [&] {
+       return launch_reduce_pz(s->amp, s->n, 0, s->ms.part, s->ms.n_part, s->dscal, s->stream);
+     }));
+  CK(s, cudaMemcpyAsync(s->hscal, s->dscal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  *out_norm2 = s->hscal[0];
+  return SV_OK;
+}
+
+int sv_expect_pauli(sv_state *s, uint64_t x_mask, uint64_t z_mask, double *out) {
+  CHECK_STATE(s);
+  if (!out) return fail(SV_ERR_ARG, "out is null");
+  if ((x_mask | z_mask) >> s->n) return fail(SV_ERR_ARG, "mask has bits beyond n_qubits");
+  if (x_mask) return fail(SV_ERR_UNSUPPORTED, "X/Y Pauli components are not supported");
+  DeviceGuard g(s->device);
+  int rc = ensure_reduce(s);
+  if (rc) return rc;
+  CK(s, timed(s, "reduce", double(size_t(8) << s->n), [&] {
+       return launch_reduce_pz(s->amp, s->n, z_mask, s->ms.part, s->ms.n_part, s->dscal, s->stream);
+     }));
+  CK(s, cudaMemcpyAsync(s->hscal, s->dscal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  if (!(s->hscal[0] > 0.0)) return fail(SV_ERR_ARG, "state has zero norm");
+  *out = s->hscal[1] / s->hscal[0];
+  return SV_OK;
+}
+
+int sv_probabilities(sv_state *s, double *out, uint64_t offset, uint64_t count, int out_on_device) {
+  CHECK_STATE(s);
+  const uint64_t N = uint64_t(1) << s->n;
+  if (offset > N || count > N - offset) return fail(SV_ERR_ARG, "range beyond the state");
+  if (count == 0) return SV_OK;
+  if (!out) return fail(SV_ERR_ARG, "out is null");
+  DeviceGuard g(s->device);
+  if (out_on_device) {
+    CK(s, timed(s, "probabilities", 16.0 * double(count),
+                [&] { return launch_probabilities(s->amp, offset, count, out, s->stream); }));
+    return SV_OK;
+  }
+  const uint64_t step = uint64_t(1) << 22;
+  int rc = ensure_dev(s, &s->stage, &s->stage_cap, step * sizeof(double), "staging buffer");
+  if (rc) return rc;
+  for (uint64_t o = 0; o < count; o += step) {
+    const uint64_t c = (count - o < step) ? count - o : step;
+    CK(s, launch_probabilities(s->amp, offset + o, c, static_cast<double *>(s->stage), s->stream));
+    CK(s, cudaMemcpyAsync(out + o, s->stage, c * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+  }
+  return SV_OK;
+}
+
+int sv_get_amplitudes(sv_state *s, void *out, uint64_t offset, uint64_t count, int out_on_device) {
+  CHECK_STATE(s);
+  const uint64_t N = uint64_t(1) << s->n;
+  if (offset > N || count > N - offset) return fail(SV_ERR_ARG, "range beyond the state");
+  if (count == 0) return SV_OK;
+  if (!out) return fail(SV_ERR_ARG, "out is null");
+  DeviceGuard g(s->device);
+  CK(s, cudaMemcpyAsync(out, s->amp + offset, count * sizeof(float2),
+                        out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
+  if (!out_on_device) CK(s, cudaStreamSynchronize(s->stream));
+  return SV_OK;
+}
+
+int sv_set_amplitudes(sv_state *s, const void *in, uint64_t offset, uint64_t count, int in_on_device) {
+  CHECK_STATE(s);
+  const uint64_t N = uint64_t(1) << s->n;
+  if (offset > N || count > N - offset) return fail(SV_ERR_ARG, "range beyond the state");
+  if (count == 0) return SV_OK;
+  if (!in) return fail(SV_ERR_ARG, "in is null");
+  DeviceGuard g(s->device);
+  CK(s, cudaMemcpyAsync(s->amp + offset, in, count * sizeof(float2),
+                        in_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream));
+  if (!in_on_device) CK(s, cudaStreamSynchronize(s->stream));
+  return SV_OK;
+}
+
+static int sample_impl(sv_state *s, const double *u, uint64_t seed, int use_seed, uint64_t shots,
+                       uint64_t *out, uint64_t *out_nb, int on_device) {
+  CHECK_STATE(s);
+  if (shots == 0) {
+    if (out_nb) *out_nb = 0;
+    return SV_OK;
+  }
+  if (!out) return fail(SV_ERR_ARG, "out is null");
+  if (!use_seed && !u) return fail(SV_ERR_ARG, "uniforms is null");
+  DeviceGuard g(s->device);
+  int rc = ensure_cdf(s);
+  if (rc) return rc;
+  const double nbytes = double(size_t(8) << s->n);
+  CK(s, timed(s, "cdf", nbytes, [&] { return launch_build_cdf(s->amp, s->n, s->ms, s->dscal + 2, s->stream); }));
+  const double *u_dev = u;
+  uint64_t *out_dev = out;
+  if (!on_device) {
+    const size_t need = shots * (sizeof(uint64_t) + (use_seed ? 0 : sizeof(double)));
+    rc = ensure_dev(s, &s->stage, &s->stage_cap, need, "staging buffer");
+    if (rc) return rc;
+    out_dev = static_cast<uint64_t *>(s->stage);
+    if (!use_seed) {
+      double *ud = reinterpret_cast<double *>(out_dev + shots);
+      CK(s, cudaMemcpyAsync(ud, u, shots * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+      u_dev = ud;
+    }
+  }
+  CK(s, cudaMemsetAsync(s->dcount, 0, sizeof(uint64_t), s->stream));
+  CK(s, timed(s, "sample", 0.0, [&] {
+       return launch_sample(s->amp, s->n, s->ms, s->dscal + 2, u_dev, seed, use_seed, shots, out_dev,
+                            s->dcount, s->stream);
+     }));
+  if (!on_device)
+    CK(s, cudaMemcpyAsync(out, out_dev, shots * sizeof(uint64_t), cudaMemcpyDeviceToHost, s->stream));
+  if (out_nb || !on_device) {
+    CK(s, cudaMemcpyAsync(s->hscal, s->dcount, sizeof(uint64_t), cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    uint64_t nb;
+    std::memcpy(&nb, s->hscal, sizeof(nb));
+    if (out_nb) *out_nb = nb;
+  }
+  return SV_OK;
+}
+
+int sv_sample(sv_state *s, uint64_t shots, uint64_t seed, uint64_t *out_bitstrings, int on_device) {
+  return sample_impl(s, nullptr, seed, 1, shots, out_bitstrings, nullptr, on_device);
+}
+
+int sv_sample_uniforms(sv_state *s, const double *uniforms, uint64_t shots, uint64_t *out_bitstrings,
+                       uint64_t *out_n_boundary, int on_device) {
+  return sample_impl(s, uniforms, 0, 0, shots, out_bitstrings, out_n_boundary, on_device);
+}
+
+int sv_profile_enable(sv_state *s, int on) {
+  if (!s) return fail(SV_ERR_ARG, "null state");
+  s->prof = on != 0;
+  return SV_OK;
+}
+
+int sv_profile_read(sv_state *s, sv_kernel_stat *out, int cap, int *n_out) {
+  CHECK_STATE(s);
+  DeviceGuard g(s->device);
+  CK(s, cudaStreamSynchronize(s->stream));
+  std::map<std::string, sv_kernel_stat> agg;
+  std::vector<std::string> order;
+  for (auto &r : s->recs) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    auto it = agg.find(r.name);
+    if (it == agg.end()) {
+      sv_kernel_stat st{};
+      std::snprintf(st.name, sizeof(st.name), "%s", r.name);
+      it = agg.emplace(r.name, st).first;
+      order.push_back(r.name);
+    }
+    it->second.launches++;
+    it->second.ms += ms;
+    it->second.bytes += r.bytes;
+    s->evpool.push_back(r.a);
+    s->evpool.push_back(r.b);
+  }
+  s->recs.clear();
+  int k = 0;
+  for (auto &nm : order) {
+    if (k < cap && out) out[k] = agg[nm];
+    k++;
+  }
+  if (n_out) *n_out = k;
+  return SV_OK;
+}
+
+}  // extern "C"

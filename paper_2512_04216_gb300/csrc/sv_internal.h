@@ -1,0 +1,94 @@
+// sv_internal.h -- plan format shared by the host planner and the kernels.
+//
+// A circuit becomes a list of passes.  A pass is one HBM sweep of the state:
+// every CTA owns a tile of 2^T amplitudes whose indices agree on all qubits
+// outside the pass's tile set Q (|Q| = T, Q always holds the c lowest qubits so
+// each global access is a run of 2^c contiguous amplitudes).  The CTA loads its
+// tile into shared memory, applies the pass's ops in order, and stores it back.
+//
+// Ops act on tile-local bit positions (local bit j <-> physical qubit lq[j]):
+//   OP_DENSE  a fused k-qubit block (k <= 5), complex64 2^k x 2^k matrix,
+//             matrix bit m <-> local bit lb[m];
+//   OP_PHASE  a product of diagonal gates whose terms each touch at most one
+//             tile qubit (the others are fixed per CTA); phases are stored as
+//             32-bit fractions of a turn so sums wrap exactly modulo 2*pi.
+#pragma once
+
+#include <atomic>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace svgb {
+
+// Kernels launched by this library in this process (all devices).
+extern std::atomic<uint64_t> g_launches;
+inline void count_launch(uint64_t k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+enum : uint8_t { OP_DENSE = 1, OP_PHASE = 2 };
+
+constexpr int kMaxTile = 13;   // largest T (64 KiB of complex64 in shared memory)
+constexpr int kMaxK = 5;       // largest fused block
+
+struct alignas(16) PlanPass {
+  uint64_t outer_mask;  // physical qubits outside the tile (within n)
+  uint64_t high_mask;   // tile qubits >= c (their ascending order = local bits c..T-1)
+  uint64_t n_tiles;     // 2^(n-T)
+  uint32_t T;           // tile qubits
+  uint32_t c;           // low qubits (0..c-1) in every tile
+  uint32_t n_ops;
+  uint32_t ops_off;     // byte offset of OpRec[n_ops] from the plan base
+  uint32_t kmax;        // largest dense k in this pass
+  uint32_t n_phase_terms;
+  int8_t lq[32];        // local bit -> physical qubit
+};
+
+struct alignas(16) OpRec {
+  uint8_t type;
+  uint8_t k;
+  uint8_t lb[5];        // DENSE: local bits, matrix bit m <-> lb[m]
+  uint8_t pad;
+  uint32_t data_off;    // DENSE: byte offset of float2[4^k] (row-major); PHASE: of PhaseTerm[]
+  uint32_t count;       // PHASE: number of terms
+};
+
+struct alignas(16) PhaseTerm {
+  uint64_t outer_mask;  // outer qubits that must all be 1 for the term to apply
+  int32_t la;           // local bit that must be 1 (-1: none)
+  uint32_t turn;        // phase as a fraction of 2*pi, scaled by 2^32
+};
+
+static_assert(sizeof(PlanPass) == 80, "PlanPass layout");
+static_assert(sizeof(OpRec) == 16, "OpRec layout");
+static_assert(sizeof(PhaseTerm) == 16, "PhaseTerm layout");
+
+// Launch one pass kernel (sv_apply.cu).  plan_dev/pass_off locate the PlanPass;
+// host_pass is the same record on the host (for grid size and template choice).
+cudaError_t launch_pass(float2 *amp, const uint8_t *plan_dev, uint32_t pass_off,
+                        const PlanPass &host_pass, cudaStream_t stream);
+
+// Measurement kernels (sv_measure.cu).
+struct MeasureScratch {
+  double *chunk = nullptr;   // 2^(n-6) sums of 64 amplitudes
+  double *block = nullptr;   // 2^(n-12) inclusive prefix of 4096-amplitude block sums
+  double *part = nullptr;    // per-CTA partials for reductions / scan carries
+  uint64_t *counter = nullptr;
+  size_t n_chunk = 0, n_block = 0, n_part = 0;
+};
+
+constexpr int kChunkBits = 6;   // 64 amplitudes
+constexpr int kBlockBits = 12;  // 4096 amplitudes = 64 chunks
+
+cudaError_t launch_reduce_pz(const float2 *amp, int n, uint64_t zmask, double *part,
+                             size_t n_part, double *out2, cudaStream_t st);
+cudaError_t launch_build_cdf(const float2 *amp, int n, MeasureScratch &ms, double *total_dev,
+                             cudaStream_t st);
+cudaError_t launch_sample(const float2 *amp, int n, const MeasureScratch &ms,
+                          const double *total_dev, const double *u, uint64_t seed, int use_seed,
+                          uint64_t shots, uint64_t *out, uint64_t *n_boundary, cudaStream_t st);
+cudaError_t launch_probabilities(const float2 *amp, uint64_t offset, uint64_t count, double *out,
+                                 cudaStream_t st);
+cudaError_t launch_reset(float2 *amp, int n, uint64_t basis, cudaStream_t st);
+
+size_t reduce_parts(int n);
+
+}  // namespace svgb

@@ -1,0 +1,568 @@
+// sv_plan.cpp -- host side of sv_apply_circuit: IR validation, gate matrices,
+// pass planning and gate fusion.
+//
+// The method applies a circuit's gates one after another to the 2^n amplitude
+// vector (§II, exact state-vector simulation).  Here the gate list is
+// re-grouped, without changing the product it computes:
+//
+//  1. Pass planning.  Scan the unapplied gates in program order and accept a
+//     gate into the current pass when (a) no earlier unaccepted gate shares a
+//     qubit with it, and (b) its qubits fit the pass's tile set Q (at most T
+//     qubits, always including the c lowest).  Diagonal gates need not fit Q:
+//     their effect on a tile depends on outer qubits only through a per-tile
+//     constant.  A rejected gate blocks its qubits for the rest of the scan, so
+//     every accepted gate commutes with every rejected gate before it.
+//  2. Fusion.  Within a pass, gates are merged into dense blocks of at most
+//     k_max qubits (open blocks on disjoint qubit sets; a gate merges the open
+//     blocks it touches when the union fits, else those blocks are emitted and
+//     the gate opens a new one).  Block matrices are built in complex128 and
+//     stored as complex64.  Diagonal gates with at most one tile qubit become
+//     phase terms instead.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sv.h"
+#include "sv_internal.h"
+#include "sv_plan.h"
+
+namespace svgb {
+
+using cd = std::complex<double>;
+
+static inline int popc(uint64_t x) { return __builtin_popcountll(x); }
+
+// ---------------------------------------------------------------------------
+// gate matrices (OpenQASM 2 definitions, see include/sv.h)
+// ---------------------------------------------------------------------------
+
+static bool gate_matrix(const sv_gate &g, GateM &out, std::string &err) {
+  const double *p = g.p;
+  const cd I(0.0, 1.0);
+  out.diag = false;
+  auto one = [&](cd a, cd b, cd c, cd d) {
+    out.k = 1;
+    out.m = {a, b, c, d};
+  };
+  switch (g.kind) {
+    case SV_GATE_U3: {
+      double ct = std::cos(0.5 * p[0]), st = std::sin(0.5 * p[0]);
+      one(ct, -std::exp(I * p[2]) * st, std::exp(I * p[1]) * st, std::exp(I * (p[1] + p[2])) * ct);
+      break;
+    }
+    case SV_GATE_H: {
+      double r = std::sqrt(0.5);
+      one(r, r, r, -r);
+      break;
+    }
+    case SV_GATE_X: one(0.0, 1.0, 1.0, 0.0); break;
+    case SV_GATE_Y: one(0.0, -I, I, 0.0); break;
+    case SV_GATE_Z: one(1.0, 0.0, 0.0, -1.0); out.diag = true; break;
+    case SV_GATE_S: one(1.0, 0.0, 0.0, I); out.diag = true; break;
+    case SV_GATE_SDG: one(1.0, 0.0, 0.0, -I); out.diag = true; break;
+    case SV_GATE_T: one(1.0, 0.0, 0.0, std::polar(1.0, M_PI / 4)); out.diag = true; break;
+    case SV_GATE_TDG: one(1.0, 0.0, 0.0, std::polar(1.0, -M_PI / 4)); out.diag = true; break;
+    case SV_GATE_RX: {
+      double ct = std::cos(0.5 * p[0]), st = std::sin(0.5 * p[0]);
+      one(ct, -I * st, -I * st, ct);
+      break;
+    }
+    case SV_GATE_RY: {
+      double ct = std::cos(0.5 * p[0]), st = std::sin(0.5 * p[0]);
+      one(ct, -st, st, ct);
+      break;
+    }
+    case SV_GATE_RZ:
+      one(std::polar(1.0, -0.5 * p[0]), 0.0, 0.0, std::polar(1.0, 0.5 * p[0]));
+      out.diag = true;
+      break;
+    case SV_GATE_P: one(1.0, 0.0, 0.0, std::polar(1.0, p[0])); out.diag = true; break;
+    case SV_GATE_CX:
+    case SV_GATE_CZ:
+    case SV_GATE_CP:
+    case SV_GATE_SWAP: {
+      out.k = 2;
+      out.m.assign(16, 0.0);
+      auto at = [&](int r, int c) -> cd & { return out.m[r * 4 + c]; };
+      if (g.kind == SV_GATE_CX) {
+        // index bit 0 = control q[0], bit 1 = target q[1]
+        at(0, 0) = 1.0; at(2, 2) = 1.0; at(1, 3) = 1.0; at(3, 1) = 1.0;
+      } else if (g.kind == SV_GATE_SWAP) {
+        at(0, 0) = 1.0; at(1, 2) = 1.0; at(2, 1) = 1.0; at(3, 3) = 1.0;
+      } else {
+        at(0, 0) = 1.0; at(1, 1) = 1.0; at(2, 2) = 1.0;
+        at(3, 3) = (g.kind == SV_GATE_CZ) ? cd(-1.0) : std::polar(1.0, p[0]);
+        out.diag = true;
+      }
+      break;
+    }
+    case SV_GATE_UNITARY: {
+      if (g.nq < 1 || g.nq > 5 || g.mat == nullptr) {
+        err = "UNITARY gate needs 1 <= nq <= 5 and a matrix";
+        return false;
+      }
+      out.k = g.nq;
+      size_t K = size_t(1) << g.nq;
+      out.m.resize(K * K);
+      for (size_t i = 0; i < K * K; i++) {
+        out.m[i] = cd(g.mat[2 * i], g.mat[2 * i + 1]);
+        if (!std::isfinite(g.mat[2 * i]) || !std::isfinite(g.mat[2 * i + 1])) {
+          err = "UNITARY matrix has a non-finite entry";
+          return false;
+        }
+      }
+      break;
+    }
+    default:
+      err = "unknown gate kind " + std::to_string(int(g.kind));
+      return false;
+  }
+  if (g.kind != SV_GATE_UNITARY && g.nq != out.k) {
+    err = "gate kind " + std::to_string(int(g.kind)) + " takes " + std::to_string(out.k) +
+          " qubit(s), nq = " + std::to_string(int(g.nq));
+    return false;
+  }
+  for (int x = 0; x < out.k; x++) out.q[x] = g.q[x];
+  return true;
+}
+
+bool convert_ir(int n, const sv_gate *ir, size_t ng, std::vector<GateM> &gates, std::string &err) {
+  gates.resize(ng);
+  for (size_t a = 0; a < ng; a++) {
+    const sv_gate &g = ir[a];
+    if (g.reserved != 0) {
+      err = "gate " + std::to_string(a) + ": reserved field must be 0";
+      return false;
+    }
+    for (int x = 0; x < 3; x++)
+      if (!std::isfinite(g.p[x])) {
+        err = "gate " + std::to_string(a) + ": non-finite parameter";
+        return false;
+      }
+    if (!gate_matrix(g, gates[a], err)) {
+      err = "gate " + std::to_string(a) + ": " + err;
+      return false;
+    }
+    uint64_t mask = 0;
+    for (int x = 0; x < gates[a].k; x++) {
+      int q = gates[a].q[x];
+      if (q < 0 || q >= n) {
+        err = "gate " + std::to_string(a) + ": qubit " + std::to_string(q) + " out of range [0," +
+              std::to_string(n) + ")";
+        return false;
+      }
+      if (mask >> q & 1) {
+        err = "gate " + std::to_string(a) + ": repeated qubit " + std::to_string(q);
+        return false;
+      }
+      mask |= uint64_t(1) << q;
+    }
+    gates[a].mask = mask;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// fusion helpers
+// ---------------------------------------------------------------------------
+
+struct Block {
+  uint64_t mask = 0;
+  std::vector<int> qs;   // matrix bit m <-> physical qubit qs[m]
+  std::vector<cd> M;     // 2^k x 2^k row-major
+  int k() const { return int(qs.size()); }
+};
+
+// M <- G (on block bits pos[0..kg-1]) * M, column by column.
+static void apply_to_block(Block &b, const GateM &g) {
+  const int k = b.k();
+  const int K = 1 << k, KG = 1 << g.k;
+  int pos[5];
+  for (int x = 0; x < g.k; x++) {
+    auto it = std::find(b.qs.begin(), b.qs.end(), g.q[x]);
+    pos[x] = int(it - b.qs.begin());
+  }
+  int gmask = 0;
+  for (int x = 0; x < g.k; x++) gmask |= 1 << pos[x];
+  int off[32];
+  for (int j = 0; j < KG; j++) {
+    int o = 0;
+    for (int x = 0; x < g.k; x++)
+      if (j >> x & 1) o |= 1 << pos[x];
+    off[j] = o;
+  }
+  cd v[32], w[32];
+  for (int col = 0; col < K; col++) {
+    for (int r0 = 0; r0 < K; r0++) {
+      if (r0 & gmask) continue;
+      for (int j = 0; j < KG; j++) v[j] = b.M[(r0 | off[j]) * K + col];
+      for (int r = 0; r < KG; r++) {
+        cd acc = 0.0;
+        for (int j = 0; j < KG; j++) acc += g.m[r * KG + j] * v[j];
+        w[r] = acc;
+      }
+      for (int r = 0; r < KG; r++) b.M[(r0 | off[r]) * K + col] = w[r];
+    }
+  }
+}
+
+// Tensor product of disjoint blocks: qs = a.qs ++ b.qs (a on the low matrix bits).
+static Block kron_blocks(const Block &a, const Block &b) {
+  Block c;
+  c.mask = a.mask | b.mask;
+  c.qs = a.qs;
+  c.qs.insert(c.qs.end(), b.qs.begin(), b.qs.end());
+  const int KA = 1 << a.k(), KB = 1 << b.k(), K = KA * KB;
+  c.M.assign(size_t(K) * K, 0.0);
+  for (int rb = 0; rb < KB; rb++)
+    for (int ra = 0; ra < KA; ra++)
+      for (int jb = 0; jb < KB; jb++)
+        for (int ja = 0; ja < KA; ja++)
+          c.M[(rb * KA + ra) * K + (jb * KA + ja)] = a.M[ra * KA + ja] * b.M[rb * KB + jb];
+  return c;
+}
+
+static Block identity_block() {
+  Block b;
+  b.M = {cd(1.0)};
+  return b;
+}
+
+static uint32_t to_turn(double phi) {
+  double f = phi / (2.0 * M_PI);
+  f -= std::floor(f);
+  double s = std::nearbyint(f * 4294967296.0);
+  return uint32_t(uint64_t(s) & 0xffffffffu);
+}
+
+struct HostTerm {
+  uint64_t outer;  // outer qubits required to be 1
+  int la;          // local bit required to be 1 (-1 none)
+  uint32_t turn;
+};
+
+struct HostOp {
+  uint8_t type;
+  Block blk;                   // DENSE
+  std::vector<HostTerm> terms; // PHASE
+};
+
+// Decompose a diagonal 1- or 2-qubit gate into phase terms (constant, per-qubit,
+// pair) and append them.  lpos[q] = local bit of q or -1.
+static void diag_terms(const GateM &g, const int *lpos, std::vector<HostTerm> &out) {
+  double ph[4];
+  const int K = 1 << g.k;
+  for (int j = 0; j < K; j++) ph[j] = std::arg(g.m[j * K + j]);
+  // coefficient of the product of the index bits in subset S (Mobius inversion)
+  for (int S = 0; S < K; S++) {
+    double a = 0.0;
+    for (int T = 0; T < K; T++)
+      if ((T & S) == T) a += ((popc(uint64_t(S ^ T)) & 1) ? -1.0 : 1.0) * ph[T];
+    uint32_t turn = to_turn(a);
+    if (turn == 0) continue;
+    HostTerm t{0, -1, turn};
+    for (int x = 0; x < g.k; x++)
+      if (S >> x & 1) {
+        int q = g.q[x];
+        if (lpos[q] >= 0) t.la = lpos[q];
+        else t.outer |= uint64_t(1) << q;
+      }
+    out.push_back(t);
+  }
+}
+
+static void merge_terms(std::vector<HostTerm> &terms) {
+  std::sort(terms.begin(), terms.end(), [](const HostTerm &a, const HostTerm &b) {
+    return a.la != b.la ? a.la < b.la : a.outer < b.outer;
+  });
+  std::vector<HostTerm> out;
+  for (auto &t : terms) {
+    if (!out.empty() && out.back().la == t.la && out.back().outer == t.outer)
+      out.back().turn += t.turn;
+    else
+      out.push_back(t);
+  }
+  out.erase(std::remove_if(out.begin(), out.end(), [](const HostTerm &t) { return t.turn == 0; }),
+            out.end());
+  terms.swap(out);
+}
+
+// ---------------------------------------------------------------------------
+// planning
+// ---------------------------------------------------------------------------
+
+static void fuse_pass(const std::vector<GateM> &gates, const std::vector<uint32_t> &acc,
+                      uint64_t Q, const int *lpos, int kmax, std::vector<HostOp> &ops) {
+  std::vector<Block> open;
+  std::vector<HostTerm> pending;
+  uint64_t pending_local = 0;
+
+  auto emit_block = [&](Block &&b) {
+    HostOp op;
+    op.type = OP_DENSE;
+    op.blk = std::move(b);
+    ops.push_back(std::move(op));
+  };
+  auto flush_phase = [&]() {
+    if (pending.empty()) {
+      pending_local = 0;
+      return;
+    }
+    merge_terms(pending);
+    if (!pending.empty()) {
+      HostOp op;
+      op.type = OP_PHASE;
+      op.terms.swap(pending);
+      ops.push_back(std::move(op));
+    }
+    pending.clear();
+    pending_local = 0;
+  };
+  auto close_touching = [&](uint64_t m) {
+    for (size_t i = 0; i < open.size();) {
+      if (open[i].mask & m) {
+        emit_block(std::move(open[i]));
+        open.erase(open.begin() + i);
+      } else {
+        i++;
+      }
+    }
+  };
+
+  for (uint32_t gi : acc) {
+    const GateM &g = gates[gi];
+    const uint64_t local = g.mask & Q;
+    const bool outer = (g.mask & ~Q) != 0;
+    bool to_phase = false;
+    if (g.diag && popc(local) <= 1) {
+      if (outer) {
+        to_phase = true;
+      } else {
+        // a local one-qubit diagonal gate: absorb it into an open block that has
+        // room, else keep it with the phase terms
+        to_phase = true;
+        for (auto &b : open)
+          if ((b.mask & local) && popc(b.mask | g.mask) <= kmax) to_phase = false;
+      }
+    }
+    if (to_phase) {
+      close_touching(local);
+      diag_terms(g, lpos, pending);
+      pending_local |= local;
+      continue;
+    }
+    if (pending_local & g.mask) flush_phase();
+    uint64_t U = g.mask;
+    for (auto &b : open)
+      if (b.mask & g.mask) U |= b.mask;
+    Block nb;
+    if (popc(U) <= kmax) {
+      nb = identity_block();
+      for (size_t i = 0; i < open.size();) {
+        if (open[i].mask & g.mask) {
+          nb = kron_blocks(nb, open[i]);
+          open.erase(open.begin() + i);
+        } else {
+          i++;
+        }
+      }
+    } else {
+      close_touching(g.mask);
+      nb = identity_block();
+    }
+    // append the gate's new qubits, then multiply the gate in
+    for (int x = 0; x < g.k; x++) {
+      if (!(nb.mask >> g.q[x] & 1)) {
+        Block one;
+        one.mask = uint64_t(1) << g.q[x];
+        one.qs = {g.q[x]};
+        one.M = {cd(1.0), cd(0.0), cd(0.0), cd(1.0)};
+        nb = kron_blocks(nb, one);
+      }
+    }
+    apply_to_block(nb, g);
+    open.push_back(std::move(nb));
+  }
+  for (auto &b : open) emit_block(std::move(b));
+  flush_phase();
+}
+
+static void put_bytes(std::vector<uint8_t> &buf, const void *p, size_t n) {
+  const uint8_t *b = static_cast<const uint8_t *>(p);
+  buf.insert(buf.end(), b, b + n);
+}
+static void align16(std::vector<uint8_t> &buf) {
+  while (buf.size() % 16) buf.push_back(0);
+}
+
+bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Plan &plan,
+                std::string &err) {
+  sv_opts o{};
+  if (opts_in) o = *opts_in;
+  int kmax = o.k_max ? o.k_max : 2;
+  int T = o.tile_qubits ? o.tile_qubits : 12;
+  int c = o.low_qubits ? o.low_qubits : 5;
+  if (kmax < 1 || kmax > kMaxK) {
+    err = "k_max must be in [1,5]";
+    return false;
+  }
+  if (T < 1 || T > kMaxTile) {
+    err = "tile_qubits must be in [1," + std::to_string(kMaxTile) + "]";
+    return false;
+  }
+  if (o.precision != 0 && o.precision != 1) {
+    err = "precision must be 0 or 1";
+    return false;
+  }
+  if (T > n) T = n;
+  if (c > T) c = T;
+  // a pass must be able to take any single gate (up to 5 qubits) next to the c low qubits
+  int widest = 1;
+  std::vector<GateM> gates;
+  if (!convert_ir(n, ir, ng, gates, err)) return false;
+  for (auto &g : gates) widest = std::max(widest, g.k);
+  if (T < n && T - c < widest) c = std::max(1, T - widest);
+  if (T < n && T - c < widest) {
+    err = "tile_qubits too small for a " + std::to_string(widest) + "-qubit gate";
+    return false;
+  }
+  kmax = std::min(kmax, T);  // a wider UNITARY still gets a block of its own
+
+  plan = Plan();
+  plan.n = n;
+  plan.info.n_gates = ng;
+  const uint64_t nmask = (n >= 64) ? ~uint64_t(0) : ((uint64_t(1) << n) - 1);
+  const uint64_t lowmask = (uint64_t(1) << c) - 1;
+
+  std::vector<uint32_t> remaining(ng);
+  for (size_t i = 0; i < ng; i++) remaining[i] = uint32_t(i);
+
+  struct PassH {
+    uint64_t Q;
+    std::vector<HostOp> ops;
+    int lq[32];
+  };
+  std::vector<PassH> passes;
+
+  while (!remaining.empty()) {
+    uint64_t Q = lowmask, blocked = 0;
+    std::vector<uint32_t> acc, rest;
+    acc.reserve(remaining.size());
+    for (uint32_t gi : remaining) {
+      const GateM &g = gates[gi];
+      if (g.mask & blocked) {
+        blocked |= g.mask;
+        rest.push_back(gi);
+        continue;
+      }
+      if (g.diag || (g.mask & ~Q) == 0) {
+        acc.push_back(gi);
+      } else if (popc(Q | g.mask) <= T) {
+        Q |= g.mask;
+        acc.push_back(gi);
+      } else {
+        blocked |= g.mask;
+        rest.push_back(gi);
+      }
+    }
+    if (acc.empty()) {
+      err = "internal: pass planner made no progress";
+      return false;
+    }
+    // fill the tile set up to T qubits with the lowest unused qubits
+    for (int q = 0; q < n && popc(Q) < T; q++) Q |= uint64_t(1) << q;
+    PassH ph;
+    ph.Q = Q;
+    int lpos[64];
+    for (int q = 0; q < 64; q++) lpos[q] = -1;
+    int j = 0;
+    for (int q = 0; q < n; q++)
+      if (Q >> q & 1) {
+        lpos[q] = j;
+        ph.lq[j] = q;
+        j++;
+      }
+    fuse_pass(gates, acc, Q, lpos, kmax, ph.ops);
+    passes.push_back(std::move(ph));
+    remaining.swap(rest);
+  }
+
+  // ---- pack -----------------------------------------------------------------
+  std::vector<uint8_t> &buf = plan.bytes;
+  const size_t P = passes.size();
+  buf.resize(P * sizeof(PlanPass), 0);
+  plan.passes.resize(P);
+  plan.pass_offs.resize(P);
+  const double amps = std::ldexp(1.0, n);
+  for (size_t p = 0; p < P; p++) {
+    PassH &ph = passes[p];
+    PlanPass hp{};
+    hp.outer_mask = nmask & ~ph.Q;
+    hp.high_mask = ph.Q & ~lowmask;
+    hp.T = uint32_t(popc(ph.Q));
+    hp.c = uint32_t(c);
+    hp.n_tiles = uint64_t(1) << (n - int(hp.T));
+    hp.n_ops = uint32_t(ph.ops.size());
+    for (int x = 0; x < 32; x++) hp.lq[x] = int8_t(x < int(hp.T) ? ph.lq[x] : -1);
+    int lpos[64];
+    for (int q = 0; q < 64; q++) lpos[q] = -1;
+    for (int x = 0; x < int(hp.T); x++) lpos[ph.lq[x]] = x;
+
+    align16(buf);
+    hp.ops_off = uint32_t(buf.size());
+    const size_t ops_at = buf.size();
+    buf.resize(buf.size() + ph.ops.size() * sizeof(OpRec), 0);
+    std::vector<OpRec> recs(ph.ops.size());
+    uint32_t kmx = 0, nterms = 0;
+    for (size_t i = 0; i < ph.ops.size(); i++) {
+      HostOp &op = ph.ops[i];
+      OpRec r{};
+      r.type = op.type;
+      align16(buf);
+      r.data_off = uint32_t(buf.size());
+      if (op.type == OP_DENSE) {
+        const int k = op.blk.k();
+        r.k = uint8_t(k);
+        for (int m = 0; m < k; m++) r.lb[m] = uint8_t(lpos[op.blk.qs[m]]);
+        const int K = 1 << k;
+        for (int e = 0; e < K * K; e++) {
+          float f[2] = {float(op.blk.M[e].real()), float(op.blk.M[e].imag())};
+          put_bytes(buf, f, sizeof(f));
+        }
+        kmx = std::max<uint32_t>(kmx, uint32_t(k));
+        plan.info.n_blocks++;
+        plan.info.hist_k[k]++;
+        plan.info.flops += uint64_t(amps * 8.0 * K);
+      } else {
+        r.count = uint32_t(op.terms.size());
+        for (auto &t : op.terms) {
+          PhaseTerm pt{};
+          pt.outer_mask = t.outer;
+          pt.la = t.la;
+          pt.turn = t.turn;
+          put_bytes(buf, &pt, sizeof(pt));
+        }
+        nterms += r.count;
+        plan.info.n_phase++;
+      }
+      recs[i] = r;
+    }
+    std::memcpy(buf.data() + ops_at, recs.data(), recs.size() * sizeof(OpRec));
+    hp.kmax = kmx;
+    hp.n_phase_terms = nterms;
+    std::memcpy(buf.data() + p * sizeof(PlanPass), &hp, sizeof(hp));
+    plan.passes[p] = hp;
+    plan.pass_offs[p] = uint32_t(p * sizeof(PlanPass));
+  }
+  align16(buf);
+  plan.info.n_passes = P;
+  plan.info.bytes = uint64_t(double(P) * 16.0 * amps);
+  plan.info.upload_bytes = buf.size();
+  plan.precision = o.precision;
+  return true;
+}
+
+}  // namespace svgb

@@ -1,0 +1,107 @@
+"""StateVector: a resident 2^n complex64 state in a torch CUDA tensor, driven
+through the C-ABI (every operation is one library call)."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import capi
+
+
+class StateVector:
+    """Owns a torch complex64 tensor of 2^n amplitudes wrapped by sv_wrap.
+
+    ``stream``: a torch.cuda.Stream (default: the current stream at creation).
+    """
+
+    def __init__(self, n: int, stream: torch.cuda.Stream | None = None, device=None,
+                 basis_index: int = 0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("StateVector needs a CUDA device")
+        self.n = int(n)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        with torch.cuda.device(self.device):
+            self.amps = torch.empty(1 << self.n, dtype=torch.complex64, device=self.device)
+            self.h = capi.sv_wrap(self.amps, self.n, capi.SV_C64, self.stream)
+            capi.sv_reset(self.h, basis_index)
+
+    # -- lifetime -------------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            capi.sv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- operations -------------------------------------------------------------
+    def reset(self, basis_index: int = 0):
+        capi.sv_reset(self.h, basis_index)
+
+    def apply(self, circuit, k_max=0, tile_qubits=0, low_qubits=0, precision=0):
+        ir, keep = capi.to_ir(circuit)
+        opts = capi.make_opts(k_max, tile_qubits, low_qubits, precision)
+        capi.sv_apply_circuit(self.h, ir, len(circuit), opts)
+        del keep
+
+    def synchronize(self):
+        capi.sv_synchronize(self.h)
+
+    def norm2(self) -> float:
+        return capi.sv_norm(self.h)
+
+    def expect_z(self, zmask: int) -> float:
+        return capi.sv_expect_pauli(self.h, 0, zmask)
+
+    def sample(self, shots: int, seed: int, on_device: bool = False):
+        if on_device:
+            out = torch.empty(shots, dtype=torch.int64, device=self.device)
+        else:
+            out = np.empty(shots, dtype=np.uint64)
+        capi.sv_sample(self.h, shots, seed, out, on_device)
+        return out
+
+    def sample_uniforms(self, uniforms, on_device: bool = False):
+        if on_device:
+            u = uniforms if torch.is_tensor(uniforms) else torch.as_tensor(uniforms, device=self.device)
+            out = torch.empty(u.shape[0], dtype=torch.int64, device=self.device)
+        else:
+            u = np.ascontiguousarray(uniforms, dtype=np.float64)
+            out = np.empty(u.shape[0], dtype=np.uint64)
+        nb = capi.sv_sample_uniforms(self.h, u, u.shape[0], out, on_device)
+        return out, nb
+
+    def probabilities(self, offset: int = 0, count: int | None = None, on_device: bool = False):
+        count = (1 << self.n) - offset if count is None else count
+        if on_device:
+            out = torch.empty(count, dtype=torch.float64, device=self.device)
+        else:
+            out = np.empty(count, dtype=np.float64)
+        capi.sv_probabilities(self.h, out, offset, count, on_device)
+        return out
+
+    def amplitudes(self, offset: int = 0, count: int | None = None) -> np.ndarray:
+        count = (1 << self.n) - offset if count is None else count
+        out = np.empty(count, dtype=np.complex64)
+        capi.sv_get_amplitudes(self.h, out, offset, count, False)
+        return out
+
+    def set_amplitudes(self, values, offset: int = 0):
+        v = np.ascontiguousarray(values, dtype=np.complex64)
+        capi.sv_set_amplitudes(self.h, v, offset, v.shape[0], False)
+
+    def profile(self, on: bool = True):
+        capi.sv_profile_enable(self.h, on)
+
+    def profile_read(self) -> dict:
+        return capi.sv_profile_read(self.h)

@@ -1,0 +1,107 @@
+"""Host-side checks of the C-ABI library (no GPU): it loads, exports every
+function include/sv.h declares, and its planner accepts/rejects IR correctly."""
+import os
+import re
+
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    from paper_2512_04216_gb300 import build
+    build.build()
+    from paper_2512_04216_gb300 import capi
+    return capi
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(sv_[a-z_0-9]+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["sv_create", "sv_apply_circuit", "sv_probabilities", "sv_sample",
+                     "sv_expect_pauli", "sv_norm", "sv_sample_uniforms", "sv_destroy"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    capi = _lib()
+    import ctypes
+    lib = ctypes.CDLL(capi.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert capi.sv_version().startswith("svgb")
+
+
+def test_plan_stats_counts():
+    capi = _lib()
+    c = W.random_layered(12, 20, 1)
+    info = capi.sv_plan_stats(12, c, capi.make_opts(2, 12, 5))
+    assert info["n_gates"] == len(c)
+    assert info["n_passes"] == 1  # the whole 12-qubit state is one tile
+    assert info["bytes"] == 16 * (1 << 12)
+    assert sum(info["hist_k"]) == info["n_blocks"]
+    assert max(k for k in range(6) if info["hist_k"][k]) <= 2
+    info5 = capi.sv_plan_stats(12, c, capi.make_opts(5, 12, 5))
+    assert info5["n_blocks"] < info["n_blocks"]
+
+
+def test_plan_passes_shrink_with_tile():
+    capi = _lib()
+    c = W.random_layered(28, 10, 2)
+    p = [capi.sv_plan_stats(28, c, capi.make_opts(2, T, 5))["n_passes"] for T in (8, 10, 12, 13)]
+    assert p == sorted(p, reverse=True) and p[0] > p[-1]
+    # every qubit is touched in every layer and no pass holds all 28 qubits
+    assert p[-1] >= 3
+
+
+def test_qft_diagonal_gates_ride_along():
+    capi = _lib()
+    info = capi.sv_plan_stats(28, W.qft(28), capi.make_opts(2, 12, 5))
+    # the controlled phases need not share a tile with both of their qubits
+    assert info["n_passes"] <= 8
+    assert info["n_phase"] >= 1
+
+
+@pytest.mark.parametrize("bad,msg", [
+    ([("cx", (0, 12), ())], "out of range"),
+    ([("cx", (3, 3), ())], "repeated"),
+    ([("u3", (0,), (float("nan"), 0, 0))], "non-finite"),
+])
+def test_plan_rejects_invalid_ir(bad, msg):
+    capi = _lib()
+    with pytest.raises(capi.SvError) as e:
+        capi.sv_plan_stats(12, bad)
+    assert e.value.code == capi.SV_ERR_ARG
+    assert msg in str(e.value)
+
+
+def test_plan_rejects_bad_options():
+    capi = _lib()
+    with pytest.raises(capi.SvError):
+        capi.sv_plan_stats(12, W.ghz(12), capi.make_opts(k_max=6))
+    with pytest.raises(capi.SvError):
+        capi.sv_plan_stats(12, W.ghz(12), capi.make_opts(tile_qubits=14))
+
+
+def test_unknown_gate_kind_rejected():
+    capi = _lib()
+    import numpy as np
+    ir, keep = capi.to_ir(W.ghz(3))
+    ir["kind"][1] = 99
+    info = capi.sv_plan_info()
+    import ctypes
+    rc = capi._L.sv_plan_stats(3, ir.ctypes.data, 3, None, ctypes.byref(info))
+    assert rc == capi.SV_ERR_ARG
+    assert "unknown gate kind" in capi.sv_last_error()
