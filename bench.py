@@ -42,9 +42,10 @@ DEPTH = 40
 SEED = 2
 SHOTS = 100_000
 ZMASK = 0b1011  # <Z_0 Z_1 Z_3>
-OPTS = dict(k_max=2, tile_qubits=12, low_qubits=5, precision=0)
+OPTS = dict(k_max=2, tile_qubits=12, low_qubits=5, precision=0, kernel_variant=0)
 METRIC = "state-vector apply HBM GB/s vs peak"
-WORKLOAD = (f"random layered n={N_QUBITS} depth={DEPTH} + QFT-{N_QUBITS} on a seeded basis state; "
+def workload_name():
+    return (f"random layered n={N_QUBITS} depth={DEPTH} + QFT-{N_QUBITS} on a seeded basis state; "
             f"FP64 norm, CDF and {SHOTS} shots; <Z> expectation")
 # DRAM bytes of one pass-kernel launch from ncu; None until captured for the
 # current kernel (see profiles/).
@@ -228,7 +229,7 @@ def run_ours(args, rank, world, local_rank):
     capi.sv_destroy(h)
 
     peak, peak_kind = peaks()
-    pk = prof.get("pass", {"launches": 0, "ms": float("nan"), "bytes": 0.0})
+    pk = prof.get("pass_tc") or prof.get("pass") or {"launches": 0, "ms": float("nan"), "bytes": 0.0}
     achieved = pk["bytes"] / (pk["ms"] * 1e-3) / 1e9 if pk["launches"] else float("nan")
     value = world * bytes_step * args.steps / (dev_ms * 1e-3) / 1e9
     e2e_val = world * bytes_step * args.steps / e2e_s / 1e9
@@ -239,10 +240,11 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
         "data": "synthetic (seeded random layered circuit, QFT, SplitMix64 uniforms)",
-        "config": {"workload": WORKLOAD, "n_qubits": n, "depth": DEPTH, "gates": len(circ) + len(qft),
+        "config": {"workload": workload_name(), "n_qubits": n, "depth": DEPTH, "gates": len(circ) + len(qft),
                    "shots": SHOTS, "fusion_k_max": OPTS["k_max"], "tile_qubits": OPTS["tile_qubits"],
+                   "kernel_variant": OPTS.get("kernel_variant", 0), "precision": OPTS["precision"],
                    "passes_per_step": plan_r["n_passes"] + plan_q["n_passes"],
-                   "l2": "inputs larger than L2 (2 GiB state vs 129 MB L2)",
+                   "l2": f"inputs larger than L2 ({(8 << n) / 2**30:.3g} GiB state vs 129 MB L2)",
                    "parallelism": f"replicas{world}"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "peak_source": peak_kind,
@@ -319,20 +321,32 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS},
+        "config": {"workload": workload_name(), "n_qubits": N_QUBITS},
         "cpu_baseline": {"value": v, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": desc},
         "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
 
 def main():
+    global N_QUBITS, DEPTH
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-qubits", type=int, default=N_QUBITS,
+                    help="smaller states for profiling captures (the bench line uses 28)")
+    ap.add_argument("--depth", type=int, default=DEPTH)
+    ap.add_argument("--tile-qubits", type=int, default=OPTS["tile_qubits"])
+    ap.add_argument("--k-max", type=int, default=OPTS["k_max"])
+    ap.add_argument("--kernel-variant", type=int, default=0)
+    ap.add_argument("--precision", type=int, default=OPTS["precision"],
+                    help="0: FP32 CUDA cores; 1: 3xTF32 tensor-core stage products")
     args = ap.parse_args()
+    N_QUBITS, DEPTH = args.n_qubits, args.depth
+    OPTS.update(tile_qubits=args.tile_qubits, k_max=args.k_max, kernel_variant=args.kernel_variant,
+                precision=args.precision)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -86,6 +86,9 @@ typedef struct sv_opts {
                           is a run of 2^c contiguous amplitudes (1..T; default 5) */
   int32_t precision;   /* 0 = FP32 CUDA cores for every block;
                           1 = 3xTF32 tensor cores (tcgen05) for 4-5 qubit blocks */
+  int32_t kernel_variant; /* 0 = amplitudes stay in registers across the ops of a
+                          stage, shared memory only between stages (default);
+                          1 = every op sweeps the shared-memory tile */
 } sv_opts;
 
 /* Statistics of the fusion + pass plan of a circuit (host-side only). */
@@ -98,6 +101,8 @@ typedef struct sv_plan_info {
   uint64_t flops;      /* useful real flops of the dense blocks over the whole state */
   uint64_t bytes;      /* algorithmic HBM bytes: n_passes * 2 * 2^n * 8 */
   uint64_t upload_bytes; /* size of the packed plan copied host -> device per apply */
+  uint64_t n_stages;   /* register stages over all register-stage passes */
+  uint64_t tc_stages;  /* stages applied as one 3xTF32 tensor-core product (precision 1) */
 } sv_plan_info;
 
 /* ---- lifetime ------------------------------------------------------------ */

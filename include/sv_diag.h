@@ -1,0 +1,28 @@
+/*
+ * sv_diag.h -- diagnostics of libsvgb.so (not part of the simulation API).
+ */
+#ifndef SVGB_SV_DIAG_H
+#define SVGB_SV_DIAG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * One product on the tensor-core path used by sv_apply_circuit with
+ * precision = 1: d[m][n] = sum_k a[m][k] * b[n][k] for m < 128, n, k < 32,
+ * with a (float32, row-major 128 x 32) split into TF32 hi/lo parts on the
+ * device, b (double, row-major 32 x 32) split on the host, and the three
+ * products a_hi*b_hi + a_hi*b_lo + a_lo*b_hi accumulated in float32 by
+ * tcgen05.mma (kind::tf32, A in tensor memory, B in shared memory).  All
+ * pointers are host memory owned by the caller; d receives 128 x 32 floats.
+ * Runs on the current device; synchronous.  Returns SV_OK, SV_ERR_TIMEOUT if
+ * the bounded wait for MMA completion gave up, or SV_ERR_CUDA.
+ */
+int sv_tc_selftest(const float *a, const double *b, float *d);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SVGB_SV_DIAG_H */

@@ -45,19 +45,22 @@ class SvError(RuntimeError):
 
 class sv_opts(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int32), ("tile_qubits", ctypes.c_int32),
-                ("low_qubits", ctypes.c_int32), ("precision", ctypes.c_int32)]
+                ("low_qubits", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("kernel_variant", ctypes.c_int32)]
 
 
 class sv_plan_info(ctypes.Structure):
     _fields_ = [("n_gates", ctypes.c_uint64), ("n_blocks", ctypes.c_uint64),
                 ("n_phase", ctypes.c_uint64), ("n_passes", ctypes.c_uint64),
                 ("hist_k", ctypes.c_uint64 * 6), ("flops", ctypes.c_uint64),
-                ("bytes", ctypes.c_uint64), ("upload_bytes", ctypes.c_uint64)]
+                ("bytes", ctypes.c_uint64), ("upload_bytes", ctypes.c_uint64),
+                ("n_stages", ctypes.c_uint64), ("tc_stages", ctypes.c_uint64)]
 
     def as_dict(self):
         return {"n_gates": self.n_gates, "n_blocks": self.n_blocks, "n_phase": self.n_phase,
                 "n_passes": self.n_passes, "hist_k": list(self.hist_k), "flops": self.flops,
-                "bytes": self.bytes, "upload_bytes": self.upload_bytes}
+                "bytes": self.bytes, "upload_bytes": self.upload_bytes,
+                "n_stages": self.n_stages, "tc_stages": self.tc_stages}
 
 
 class sv_kernel_stat(ctypes.Structure):
@@ -91,6 +94,7 @@ _SIGS = {
     "sv_last_error": ([], ctypes.c_char_p),
     "sv_version": ([], ctypes.c_char_p),
     "sv_launch_count": ([], ctypes.c_uint64),
+    "sv_tc_selftest": ([_P, _P, _P], _i),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_L, _name)
@@ -143,8 +147,9 @@ def to_ir(circuit):
     return ir, keep
 
 
-def make_opts(k_max=0, tile_qubits=0, low_qubits=0, precision=0):
-    return sv_opts(int(k_max), int(tile_qubits), int(low_qubits), int(precision))
+def make_opts(k_max=0, tile_qubits=0, low_qubits=0, precision=0, kernel_variant=0):
+    return sv_opts(int(k_max), int(tile_qubits), int(low_qubits), int(precision),
+                   int(kernel_variant))
 
 
 # ---------------------------------------------------------------------------
@@ -253,6 +258,16 @@ def sv_expect_pauli(h, x_mask: int, z_mask: int) -> float:
     out = ctypes.c_double()
     _check(_L.sv_expect_pauli(h, int(x_mask), int(z_mask), ctypes.byref(out)))
     return out.value
+
+
+def sv_tc_selftest(a, b):
+    """Tensor-core product check (include/sv_diag.h): a 128x32 float32, b 32x32 float64."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    assert a.shape == (128, 32) and b.shape == (32, 32)
+    d = np.empty((128, 32), dtype=np.float32)
+    _check(_L.sv_tc_selftest(a.ctypes.data, b.ctypes.data, d.ctypes.data))
+    return d
 
 
 def sv_profile_enable(h, on: bool = True):

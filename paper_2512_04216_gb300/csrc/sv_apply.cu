@@ -1,18 +1,28 @@
-// sv_apply.cu -- the HBM pass kernel of sv_apply_circuit.
+// sv_apply.cu -- the HBM pass kernels of sv_apply_circuit.
 //
 // One launch applies one pass of the plan (see sv_internal.h): every CTA owns
 // the 2^T amplitudes whose indices share the values of the qubits outside the
 // pass's tile set.  Those amplitudes sit in 2^(T-c) runs of 2^c contiguous
-// amplitudes (the c lowest qubits are always in the tile).  The CTA
-//   1. gathers its runs into shared memory with 16-byte cp.async copies,
-//   2. applies the pass's ops in order -- dense fused blocks (each thread owns
-//      one group of 2^k amplitudes at a time) and diagonal phase ops (a
-//      per-tile table of phases, exact modulo 2*pi in 32-bit turn arithmetic),
-//   3. writes the tile back in place.
-// The state is read once and written once per pass: 16 bytes per amplitude.
+// amplitudes (the c lowest qubits are always in the tile).  The state is read
+// once and written once per pass: 16 bytes per amplitude.
+//
+// k_pass_reg (register stages, the default): each thread holds 2^R amplitudes
+// in registers.  The first stage loads them straight from HBM (lanes on the
+// low tile bits, so a warp reads contiguous runs), every op of a stage is
+// applied in registers with compile-time register indices, the tile is
+// re-distributed between stages through XOR-swizzled shared memory, and the
+// last stage stores straight to HBM.
+//
+// k_pass (shared-memory sweeps): gathers the tile into shared memory with
+// cp.async and applies each op as a sweep over the tile (one thread per group
+// of 2^k amplitudes).  Used for tiles too small for register stages.
+//
+// Diagonal phase ops tabulate a per-tile phase table from 32-bit turn
+// fractions (exact modulo 2*pi) over the low and high halves of the tile index.
 #include <cstdint>
 
 #include "sv_internal.h"
+#include "sv_tc_ptx.cuh"
 
 namespace svgb {
 
@@ -192,6 +202,527 @@ __global__ void __launch_bounds__(kNT) k_pass(float2 *__restrict__ amp, const ui
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// register stages
+// ---------------------------------------------------------------------------
+
+__host__ __device__ constexpr int popc_c(int m) { return m ? (m & 1) + popc_c(m >> 1) : 0; }
+
+// deposit the bits of j into the set bits of mask (ascending)
+__host__ __device__ constexpr int dep_c(int j, int mask) {
+  int out = 0, bit = 0;
+  for (int p = 0; p < 8; p++)
+    if ((mask >> p) & 1) {
+      if ((j >> bit) & 1) out |= 1 << p;
+      bit++;
+    }
+  return out;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Dense block on the register positions in MASK (matrix bit i <-> i-th set bit).
+template <int R, int MASK>
+__device__ __forceinline__ void reg_dense(float2 (&v)[1 << R], const float2 *__restrict__ m) {
+  constexpr int K = popc_c(MASK);
+  constexpr int KK = 1 << K;
+  constexpr bool kInRegs = K <= 2;
+  float2 mm[kInRegs ? KK * KK : 1];
+  if constexpr (kInRegs) {
+#pragma unroll
+    for (int e = 0; e < KK * KK; e++) mm[e] = m[e];
+  }
+#pragma unroll
+  for (int g = 0; g < (1 << R); g++) {
+    if (g & MASK) continue;
+    float2 x[KK];
+#pragma unroll
+    for (int j = 0; j < KK; j++) x[j] = v[g | dep_c(j, MASK)];
+#pragma unroll
+    for (int r = 0; r < KK; r++) {
+      float re = 0.f, im = 0.f;
+#pragma unroll
+      for (int j = 0; j < KK; j++) {
+        float2 e;
+        if constexpr (kInRegs) e = mm[r * KK + j];
+        else e = m[r * KK + j];
+        re = fmaf(e.x, x[j].x, re);
+        re = fmaf(-e.y, x[j].y, re);
+        im = fmaf(e.x, x[j].y, im);
+        im = fmaf(e.y, x[j].x, im);
+      }
+      v[g | dep_c(r, MASK)] = make_float2(re, im);
+    }
+  }
+}
+
+#define SV_CASE(M) \
+  case M: if constexpr ((M) < (1 << R)) reg_dense<R, (M)>(v, m); break;
+
+template <int R>
+__device__ __forceinline__ void reg_dense_dispatch(float2 (&v)[1 << R], uint32_t mask,
+                                                   const float2 *__restrict__ m) {
+  switch (mask) {
+    SV_CASE(1) SV_CASE(2) SV_CASE(3) SV_CASE(4) SV_CASE(5) SV_CASE(6) SV_CASE(7)
+    SV_CASE(8) SV_CASE(9) SV_CASE(10) SV_CASE(11) SV_CASE(12) SV_CASE(13) SV_CASE(14) SV_CASE(15)
+    SV_CASE(16) SV_CASE(17) SV_CASE(18) SV_CASE(19) SV_CASE(20) SV_CASE(21) SV_CASE(22) SV_CASE(23)
+    SV_CASE(24) SV_CASE(25) SV_CASE(26) SV_CASE(27) SV_CASE(28) SV_CASE(29) SV_CASE(30) SV_CASE(31)
+    default: break;
+  }
+}
+#undef SV_CASE
+
+// Phase tables for the current tile (see apply_phase); then every register
+// amplitude is multiplied by the phase of its local index la[j] | LB.
+template <int R>
+__device__ __forceinline__ void reg_phase(float2 (&v)[1 << R], const PhaseTerm *__restrict__ terms,
+                                          uint32_t count, uint64_t base, uint32_t T,
+                                          const uint16_t *__restrict__ la, uint32_t LB, uint32_t *acc,
+                                          float2 *tab) {
+  __syncthreads();  // a previous phase op may still read the tables
+  if (threadIdx.x <= T) acc[threadIdx.x] = 0u;
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) {
+    const PhaseTerm pt = terms[i];
+    if ((base & pt.outer_mask) == pt.outer_mask) atomicAdd(&acc[pt.la + 1], pt.turn);
+  }
+  __syncthreads();
+  const uint32_t h = T >> 1;
+  const uint32_t nlo = 1u << h, nhi = 1u << (T - h);
+  for (uint32_t e = threadIdx.x; e < nlo + nhi; e += blockDim.x) {
+    uint32_t turn;
+    if (e < nlo) {
+      turn = acc[0];
+      for (uint32_t j = 0; j < h; j++)
+        if ((e >> j) & 1u) turn += acc[1 + j];
+    } else {
+      const uint32_t e2 = e - nlo;
+      turn = 0u;
+      for (uint32_t j = 0; j < T - h; j++)
+        if ((e2 >> j) & 1u) turn += acc[1 + h + j];
+    }
+    float sn, cs;
+    sincospif(static_cast<float>(static_cast<int32_t>(turn)) * 4.656612873077393e-10f, &sn, &cs);
+    tab[e] = make_float2(cs, sn);
+  }
+  __syncthreads();
+  const uint32_t lmask = nlo - 1u;
+#pragma unroll
+  for (int j = 0; j < (1 << R); j++) {
+    const uint32_t l = uint32_t(la[j]) | LB;
+    v[j] = cmul(v[j], cmul(tab[l & lmask], tab[nlo + (l >> h)]));
+  }
+}
+
+// Persistent register-stage kernel.  Every CTA copies its pass's records
+// (ops, matrices, phase terms, stages) into shared memory once, builds the
+// per-thread stage index tables once, then walks tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...  While a tile is computed, the next tile's
+// amplitudes stream into `buf_in` with cp.async; stage 0 reads `buf_in`
+// (natural order: its lanes are the low tile bits), later stages exchange
+// through the swizzled `buf_x`, and the last stage stores straight to HBM.
+constexpr int kMaxStages = 24;     // stage tables kept in shared memory
+constexpr uint32_t kMaxPassData = 24 * 1024;
+
+struct RegLayout {
+  uint32_t L, nseg, NT, ns;
+  size_t off_in, off_x, off_seg, off_tab, off_acc, off_tt, off_data, total;
+};
+
+__host__ __device__ inline RegLayout reg_layout(uint32_t T, uint32_t c, uint32_t ns, uint32_t data_bytes) {
+  RegLayout r;
+  r.L = 1u << T;
+  r.nseg = 1u << (T - c);
+  r.NT = 1u << (T - 4);
+  r.ns = ns;
+  size_t o = 0;
+  r.off_in = o; o += size_t(r.L) * 8;
+  r.off_x = o; o += size_t(r.L) * 8;
+  r.off_seg = o; o += size_t(r.nseg) * 8;
+  r.off_tab = o; o += 256 * 8;
+  r.off_acc = o; o += 64 * 4;
+  r.off_tt = o; o += size_t(ns) * r.NT * 4;
+  o = (o + 15) & ~size_t(15);
+  r.off_data = o; o += data_bytes;
+  r.total = (o + 15) & ~size_t(15);
+  return r;
+}
+
+template <int R, int NTMAX>
+__global__ void __launch_bounds__(NTMAX, NTMAX <= 256 ? 3 : 1) k_pass_reg(float2 *__restrict__ amp,
+                                                                 const uint8_t *__restrict__ plan,
+                                                                 uint32_t pass_off) {
+  constexpr int NR = 1 << R;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const PlanPass *P = reinterpret_cast<const PlanPass *>(plan + pass_off);
+  const uint32_t T = P->T, c = P->c;
+  const uint32_t ns = P->n_stages;
+  const uint32_t data_off = P->ops_off, data_bytes = P->data_bytes;
+  const uint64_t outer_mask = P->outer_mask, n_tiles = P->n_tiles;
+  const RegLayout lay = reg_layout(T, c, ns, data_bytes);
+  float2 *buf_in = reinterpret_cast<float2 *>(smem + lay.off_in);
+  float2 *buf_x = reinterpret_cast<float2 *>(smem + lay.off_x);
+  uint64_t *segoff = reinterpret_cast<uint64_t *>(smem + lay.off_seg);
+  float2 *tab = reinterpret_cast<float2 *>(smem + lay.off_tab);
+  uint32_t *acc = reinterpret_cast<uint32_t *>(smem + lay.off_acc);
+  uint32_t *tt = reinterpret_cast<uint32_t *>(smem + lay.off_tt);
+  uint8_t *data = smem + lay.off_data;
+  const uint32_t tid = threadIdx.x, NT = blockDim.x;
+
+  // pass records -> shared memory (offsets below are relative to ops_off)
+  {
+    const uint4 *src = reinterpret_cast<const uint4 *>(plan + data_off);
+    uint4 *dst = reinterpret_cast<uint4 *>(data);
+    for (uint32_t i = tid; i < data_bytes / 16; i += NT) dst[i] = src[i];
+  }
+  const uint64_t hm = P->high_mask;
+  for (uint32_t s = tid; s < lay.nseg; s += NT) segoff[s] = pdep_u64(s, hm);
+  __syncthreads();
+  const StageRec *stages = reinterpret_cast<const StageRec *>(data + (P->stages_off - data_off));
+  const OpRec *ops = reinterpret_cast<const OpRec *>(data);
+  // per-thread stage tables: low 16 bits = local index part, high 16 = swizzled
+  for (uint32_t s = 0; s < ns; s++) {
+    uint32_t LB = 0;
+    for (uint32_t i = 0; i < T - R; i++)
+      if ((tid >> i) & 1u) LB |= 1u << stages[s].tb[i];
+    tt[s * NT + tid] = LB | (swz(LB) << 16);
+  }
+  const uint32_t lowmask = (1u << c) - 1u;
+  const uint32_t cs = c - 1u, cmask = (1u << cs) - 1u;
+  const uint32_t nchunk = lay.L >> 1;
+
+  uint64_t tile = blockIdx.x;
+  uint64_t base = tile < n_tiles ? pdep_u64(tile, outer_mask) : 0;
+  if (tile < n_tiles) {
+    for (uint32_t i = tid; i < nchunk; i += NT)
+      cp_async16(buf_in + 2 * i, amp + base + segoff[i >> cs] + (uint64_t(i & cmask) << 1));
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  __syncthreads();
+
+  float2 v[NR];
+  while (tile < n_tiles) {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    {
+      const StageRec &st = stages[0];
+      const uint32_t LB = tt[tid] & 0xffffu;
+#pragma unroll
+      for (int j = 0; j < NR; j++) v[j] = buf_in[uint32_t(st.la[j]) | LB];
+    }
+    __syncthreads();  // buf_in is free: prefetch the next tile
+    const uint64_t next = tile + gridDim.x;
+    const uint64_t base_next = next < n_tiles ? pdep_u64(next, outer_mask) : 0;
+    if (next < n_tiles) {
+      for (uint32_t i = tid; i < nchunk; i += NT)
+        cp_async16(buf_in + 2 * i, amp + base_next + segoff[i >> cs] + (uint64_t(i & cmask) << 1));
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    for (uint32_t s = 0; s < ns; s++) {
+      const StageRec &st = stages[s];
+      const uint32_t w = tt[s * NT + tid];
+      const uint32_t LB = w & 0xffffu, PB = w >> 16;
+      if (s > 0) {
+        const StageRec &pv = stages[s - 1];
+        const uint32_t PBp = tt[(s - 1) * NT + tid] >> 16;
+        __syncthreads();  // previous readers of buf_x are done
+#pragma unroll
+        for (int j = 0; j < NR; j++) buf_x[uint32_t(pv.pa[j]) ^ PBp] = v[j];
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NR; j++) v[j] = buf_x[uint32_t(st.pa[j]) ^ PB];
+      }
+      const uint32_t oe = st.op_end;
+      for (uint32_t o = st.op_begin; o < oe; o++) {
+        const OpRec op = ops[o];
+        if (op.type == OP_DENSE) {
+          reg_dense_dispatch<R>(v, op.rmask, reinterpret_cast<const float2 *>(data + (op.data_off - data_off)));
+        } else {
+          reg_phase<R>(v, reinterpret_cast<const PhaseTerm *>(data + (op.data_off - data_off)), op.count,
+                       base, T, st.la, LB, acc, tab);
+        }
+      }
+    }
+    {
+      const StageRec &st = stages[ns - 1];
+      const uint32_t LB = tt[(ns - 1) * NT + tid] & 0xffffu;
+#pragma unroll
+      for (int j = 0; j < NR; j++) {
+        const uint32_t l = uint32_t(st.la[j]) | LB;
+        __stcs(amp + base + segoff[l >> c] + (l & lowmask), v[j]);
+      }
+    }
+    tile = next;
+    base = base_next;
+  }
+}
+
+constexpr size_t kSmemOptIn = 232448;  // 227 KiB per CTA on sm_100-class parts
+
+template <int R, int NTMAX>
+static cudaError_t launch_reg(float2 *amp, const uint8_t *plan, uint32_t off, const PlanPass &hp,
+                              cudaStream_t st) {
+  const RegLayout lay = reg_layout(hp.T, hp.c, hp.n_stages, hp.data_bytes);
+  static unsigned long long configured = 0;
+  static int sms[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && !((configured >> dev) & 1ull)) {
+    e = cudaFuncSetAttribute(k_pass_reg<R, NTMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(kSmemOptIn));
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    configured |= 1ull << dev;
+  }
+  const unsigned nt = 1u << (hp.T - R);
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass_reg<R, NTMAX>, int(nt), lay.total);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const uint64_t want = uint64_t(sms[dev < 64 ? dev : 0] > 0 ? sms[dev < 64 ? dev : 0] : 1) * per_sm;
+  const unsigned grid = unsigned(hp.n_tiles < want ? hp.n_tiles : want);
+  k_pass_reg<R, NTMAX><<<grid, nt, lay.total, st>>>(amp, plan, off);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Whether a KIND_REG pass fits the persistent kernel's shared-memory tables.
+bool reg_pass_fits(uint32_t T, uint32_t c, uint32_t n_stages, uint32_t data_bytes) {
+  return T <= uint32_t(kMaxTile) && T >= 9 && n_stages <= uint32_t(kMaxStages) &&
+         data_bytes <= kMaxPassData && reg_layout(T, c, n_stages, data_bytes).total <= kSmemOptIn;
+}
+
+
+// ---------------------------------------------------------------------------
+// tensor-core stages (KIND_TC): the persistent register-stage skeleton, with
+// each stage's dense blocks applied as one 3xTF32 tcgen05 GEMM (sv_tc.cu).
+// ---------------------------------------------------------------------------
+
+constexpr int kTcErrTimeout = 1;
+constexpr size_t kTcStaticSmem = 1024;  // bar, tbase, abort flag (aligned with the dynamic region)
+
+template <int NTMAX>
+__global__ void __launch_bounds__(NTMAX, 1) k_pass_tc(float2 *__restrict__ amp, const uint8_t *__restrict__ plan,
+                                                      uint32_t pass_off, int *__restrict__ err) {
+  constexpr int NR = 16;  // R = 4 register qubits
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tbase_s;
+  __shared__ int abort_s;
+  const PlanPass *P = reinterpret_cast<const PlanPass *>(plan + pass_off);
+  const uint32_t T = P->T, c = P->c;
+  const uint32_t ns = P->n_stages;
+  const uint32_t data_off = P->ops_off, data_bytes = P->data_bytes;
+  const uint64_t outer_mask = P->outer_mask, n_tiles = P->n_tiles;
+  const RegLayout lay = reg_layout(T, c, ns, data_bytes);
+  float2 *buf_in = reinterpret_cast<float2 *>(smem + lay.off_in);
+  float2 *buf_x = reinterpret_cast<float2 *>(smem + lay.off_x);
+  uint64_t *segoff = reinterpret_cast<uint64_t *>(smem + lay.off_seg);
+  float2 *tab = reinterpret_cast<float2 *>(smem + lay.off_tab);
+  uint32_t *acc = reinterpret_cast<uint32_t *>(smem + lay.off_acc);
+  uint32_t *tt = reinterpret_cast<uint32_t *>(smem + lay.off_tt);
+  uint8_t *data = smem + lay.off_data;
+  const uint32_t tid = threadIdx.x, NT = blockDim.x, warp = tid >> 5;
+  const uint32_t groups = NT >> 7;
+  const uint32_t ncols = groups <= 1 ? 128u : (groups == 2 ? 256u : 512u);
+
+  {
+    const uint4 *src = reinterpret_cast<const uint4 *>(plan + data_off);
+    uint4 *dst = reinterpret_cast<uint4 *>(data);
+    for (uint32_t i = tid; i < data_bytes / 16; i += NT) dst[i] = src[i];
+  }
+  const uint64_t hm = P->high_mask;
+  for (uint32_t s = tid; s < lay.nseg; s += NT) segoff[s] = pdep_u64(s, hm);
+  fence_proxy_async_smem();  // stage matrices are read by the tensor cores
+  if (warp == 0) {
+    tmem_alloc(&tbase_s, ncols);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    abort_s = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const StageRec *stages = reinterpret_cast<const StageRec *>(data + (P->stages_off - data_off));
+  const OpRec *ops = reinterpret_cast<const OpRec *>(data);
+  for (uint32_t s = 0; s < ns; s++) {
+    uint32_t LB = 0;
+    for (uint32_t i = 0; i < T - 4; i++)
+      if ((tid >> i) & 1u) LB |= 1u << stages[s].tb[i];
+    tt[s * NT + tid] = LB | (swz(LB) << 16);
+  }
+  const uint32_t tbase = tbase_s;
+  const uint32_t tq = tbase + (((warp & 3u) * 32u) << 16) + (tid >> 7) * kTcColsPerGroup;
+  const uint32_t lowmask = (1u << c) - 1u;
+  const uint32_t cs = c - 1u, cmask = (1u << cs) - 1u;
+  const uint32_t nchunk = lay.L >> 1;
+  uint32_t parity = 0;
+
+  uint64_t tile = blockIdx.x;
+  uint64_t base = tile < n_tiles ? pdep_u64(tile, outer_mask) : 0;
+  if (tile < n_tiles) {
+    for (uint32_t i = tid; i < nchunk; i += NT)
+      cp_async16(buf_in + 2 * i, amp + base + segoff[i >> cs] + (uint64_t(i & cmask) << 1));
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  __syncthreads();
+
+  float2 v[NR];
+  bool aborted = false;
+  while (tile < n_tiles && !aborted) {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    {
+      const StageRec &st = stages[0];
+      const uint32_t LB = tt[tid] & 0xffffu;
+#pragma unroll
+      for (int j = 0; j < NR; j++) v[j] = buf_in[uint32_t(st.la[j]) | LB];
+    }
+    __syncthreads();
+    const uint64_t next = tile + gridDim.x;
+    const uint64_t base_next = next < n_tiles ? pdep_u64(next, outer_mask) : 0;
+    if (next < n_tiles) {
+      for (uint32_t i = tid; i < nchunk; i += NT)
+        cp_async16(buf_in + 2 * i, amp + base_next + segoff[i >> cs] + (uint64_t(i & cmask) << 1));
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    for (uint32_t s = 0; s < ns; s++) {
+      const StageRec &st = stages[s];
+      const uint32_t w = tt[s * NT + tid];
+      const uint32_t LB = w & 0xffffu, PB = w >> 16;
+      if (s > 0) {
+        const StageRec &pv = stages[s - 1];
+        const uint32_t PBp = tt[(s - 1) * NT + tid] >> 16;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NR; j++) buf_x[uint32_t(pv.pa[j]) ^ PBp] = v[j];
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NR; j++) v[j] = buf_x[uint32_t(st.pa[j]) ^ PB];
+      }
+      if (st.flags & 4u) {
+        uint32_t r[32];
+#pragma unroll
+        for (int j = 0; j < NR; j++) {
+          r[2 * j] = tf32_hi_bits(v[j].x);
+          r[2 * j + 1] = tf32_hi_bits(v[j].y);
+        }
+        tmem_st32(tq, r);
+#pragma unroll
+        for (int j = 0; j < NR; j++) {
+          r[2 * j] = __float_as_uint(__fsub_rn(v[j].x, __uint_as_float(tf32_hi_bits(v[j].x))));
+          r[2 * j + 1] = __float_as_uint(__fsub_rn(v[j].y, __uint_as_float(tf32_hi_bits(v[j].y))));
+        }
+        tmem_st32(tq + 32, r);
+        tmem_wait_st();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+          tc_fence_after();
+          const uint32_t bsa = smem_u32(data + (st.b_off - data_off));
+          for (uint32_t g = 0; g < groups; g++) issue_stage_mma(tbase, g, bsa);
+          mma_commit(&bar);
+        }
+        if (!mbar_wait_bounded(&bar, parity)) abort_s = 1;
+        parity ^= 1u;
+        __syncthreads();
+        if (abort_s) {
+          aborted = true;
+          break;
+        }
+        tc_fence_after();
+        tmem_ld32(tq + 64, r);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < NR; j++) v[j] = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+      }
+      const uint32_t oe = st.op_end;
+      for (uint32_t o = st.op_begin; o < oe; o++) {
+        const OpRec op = ops[o];
+        reg_phase<4>(v, reinterpret_cast<const PhaseTerm *>(data + (op.data_off - data_off)), op.count, base, T,
+                     st.la, LB, acc, tab);
+      }
+    }
+    if (aborted) break;
+    {
+      const StageRec &st = stages[ns - 1];
+      const uint32_t LB = tt[(ns - 1) * NT + tid] & 0xffffu;
+#pragma unroll
+      for (int j = 0; j < NR; j++) {
+        const uint32_t l = uint32_t(st.la[j]) | LB;
+        __stcs(amp + base + segoff[l >> c] + (l & lowmask), v[j]);
+      }
+    }
+    tile = next;
+    base = base_next;
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tbase, ncols);
+  if (tid == 0 && abort_s) atomicExch(err, kTcErrTimeout);
+}
+
+// Smallest dynamic shared memory that keeps (512 / TMEM columns) CTAs per SM at
+// most, so tcgen05.alloc never waits for a CTA that only finishes at the end.
+static size_t tc_smem_floor(uint32_t groups) {
+  const size_t per_sm = 233472;  // 228 KiB of shared memory per SM
+  const uint32_t ctas = groups <= 1 ? 4u : (groups == 2 ? 2u : 1u);
+  return per_sm / (ctas + 1) + 1024;
+}
+
+template <int NTMAX>
+static cudaError_t launch_tc(float2 *amp, const uint8_t *plan, uint32_t off, const PlanPass &hp, int *err,
+                             cudaStream_t st) {
+  const RegLayout lay = reg_layout(hp.T, hp.c, hp.n_stages, hp.data_bytes);
+  const uint32_t nt = 1u << (hp.T - 4);
+  size_t smem = lay.total;
+  const size_t floor_ = tc_smem_floor(nt >> 7);
+  if (smem < floor_) smem = floor_;
+  if (smem + kTcStaticSmem > kSmemOptIn) return cudaErrorInvalidValue;
+  static unsigned long long configured = 0;
+  static int sms[64] = {0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 64 && !((configured >> dev) & 1ull)) {
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, k_pass_tc<NTMAX>);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_pass_tc<NTMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(kSmemOptIn - kTcStaticSmem));
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    configured |= 1ull << dev;
+  }
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass_tc<NTMAX>, int(nt), smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  const int nsm = (dev < 64 && sms[dev] > 0) ? sms[dev] : 1;
+  const uint64_t want = uint64_t(nsm) * per_sm;
+  const unsigned grid = unsigned(hp.n_tiles < want ? hp.n_tiles : want);
+  k_pass_tc<NTMAX><<<grid, nt, smem, st>>>(amp, plan, off, err);
+  count_launch();
+  return cudaGetLastError();
+}
+
+bool tc_pass_fits(uint32_t T, uint32_t c, uint32_t n_stages, uint32_t data_bytes) {
+  if (T < 11 || T > 13 || T - c < 4) return false;
+  size_t total = reg_layout(T, c, n_stages, data_bytes).total;
+  const size_t floor_ = tc_smem_floor((1u << (T - 4)) >> 7);
+  if (total < floor_) total = floor_;
+  return total + kTcStaticSmem <= kSmemOptIn;
+}
+
 static size_t pass_smem(uint32_t T, uint32_t c, int kmax) {
   return (size_t(1) << T) * sizeof(float2) + (size_t(1) << (T - c)) * sizeof(uint64_t) +
          (size_t(1) << (2 * kmax)) * sizeof(float2) + 256 * sizeof(float2) + 64 * sizeof(uint32_t);
@@ -224,7 +755,17 @@ static cudaError_t launch_k(float2 *amp, const uint8_t *plan, uint32_t off, cons
 }
 
 cudaError_t launch_pass(float2 *amp, const uint8_t *plan_dev, uint32_t pass_off,
-                        const PlanPass &hp, cudaStream_t stream) {
+                        const PlanPass &hp, int *err, cudaStream_t stream) {
+  if (hp.kind == KIND_TC) {
+    if (hp.T <= 11) return launch_tc<128>(amp, plan_dev, pass_off, hp, err, stream);
+    if (hp.T == 12) return launch_tc<256>(amp, plan_dev, pass_off, hp, err, stream);
+    return launch_tc<512>(amp, plan_dev, pass_off, hp, err, stream);
+  }
+  if (hp.kind == KIND_REG) {
+    if (hp.R != 4) return cudaErrorInvalidValue;
+    if (hp.T <= 12) return launch_reg<4, 256>(amp, plan_dev, pass_off, hp, stream);
+    return launch_reg<4, 512>(amp, plan_dev, pass_off, hp, stream);
+  }
   switch (hp.kmax) {
     case 0:
     case 1: return launch_k<1>(amp, plan_dev, pass_off, hp, stream);

@@ -14,6 +14,8 @@
 #include "../../include/sv.h"
 #include "sv_internal.h"
 #include "sv_plan.h"
+#include "sv_tc.h"
+#include "../../include/sv_diag.h"
 
 using namespace svgb;
 
@@ -59,6 +61,7 @@ struct sv_state {
   MeasureScratch ms;
   double *dscal = nullptr;       // device scalars: [0] sum p, [1] sum pz, [2] total
   uint64_t *dcount = nullptr;    // boundary counter
+  int *derr = nullptr;           // device error word written by bounded waits
   double *hscal = nullptr;       // pinned host scalars
   void *stage = nullptr;         // device staging for host in/out buffers
   size_t stage_cap = 0;
@@ -152,6 +155,22 @@ int ensure_scalars(sv_state *s) {
   if (!s->hscal) {
     CK(s, cudaMallocHost(&s->hscal, 8 * sizeof(double)));
   }
+  if (!s->derr) {
+    CK(s, cudaMalloc(&s->derr, sizeof(int)));
+    CK(s, cudaMemsetAsync(s->derr, 0, sizeof(int), s->stream));
+  }
+  return SV_OK;
+}
+
+// After a stream synchronisation: report (and clear) a device-side timeout.
+int check_device_error(sv_state *s) {
+  if (!s->derr) return SV_OK;
+  int e = 0;
+  CK(s, cudaMemcpy(&e, s->derr, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    CK(s, cudaMemset(s->derr, 0, sizeof(int)));
+    return fail(SV_ERR_TIMEOUT, "a bounded device-side wait gave up (tensor-core pass)");
+  }
   return SV_OK;
 }
 
@@ -228,6 +247,7 @@ void free_state(sv_state *s) {
   if (s->ms.part) cudaFree(s->ms.part);
   if (s->dscal) cudaFree(s->dscal);
   if (s->dcount) cudaFree(s->dcount);
+  if (s->derr) cudaFree(s->derr);
   if (s->hscal) cudaFreeHost(s->hscal);
   if (s->stage) cudaFree(s->stage);
   for (auto &r : s->recs) {
@@ -297,7 +317,7 @@ int sv_synchronize(sv_state *s) {
   CHECK_STATE(s);
   DeviceGuard g(s->device);
   CK(s, cudaStreamSynchronize(s->stream));
-  return SV_OK;
+  return check_device_error(s);
 }
 
 int sv_num_qubits(const sv_state *s) { return s ? s->n : SV_ERR_ARG; }
@@ -329,12 +349,14 @@ int sv_apply_circuit(sv_state *s, const sv_gate *ir, size_t n_gates, const sv_op
   CHECK_STATE(s);
   if (n_gates == 0) return SV_OK;
   if (!ir) return fail(SV_ERR_ARG, "ir is null");
-  if (opts && opts->precision == 1)
-    return fail(SV_ERR_UNSUPPORTED, "precision=1 (3xTF32 tensor cores) is not built in this library");
   Plan plan;
   std::string err;
   if (!build_plan(s->n, ir, n_gates, opts, plan, err)) return fail(SV_ERR_ARG, "%s", err.c_str());
   DeviceGuard g(s->device);
+  {
+    int rc = ensure_scalars(s);
+    if (rc) return rc;
+  }
   const size_t bytes = plan.bytes.size();
   // host staging: wait until the previous upload has left the pinned buffer
   if (s->plan_evt_live) {
@@ -361,8 +383,9 @@ int sv_apply_circuit(sv_state *s, const sv_gate *ir, size_t n_gates, const sv_op
   s->plan_evt_live = true;
   const double pass_bytes = 16.0 * double(uint64_t(1) << s->n);
   for (size_t p = 0; p < plan.passes.size(); p++) {
-    CK(s, timed(s, "pass", pass_bytes, [&] {
-         return launch_pass(s->amp, s->plan_dev, plan.pass_offs[p], plan.passes[p], s->stream);
+    const char *kname = plan.passes[p].kind == KIND_TC ? "pass_tc" : "pass";
+    CK(s, timed(s, kname, pass_bytes, [&] {
+         return launch_pass(s->amp, s->plan_dev, plan.pass_offs[p], plan.passes[p], s->derr, s->stream);
        }));
   }
   return SV_OK;
@@ -379,6 +402,8 @@ int sv_norm(sv_state *s, double *out_norm2) {
      }));
   CK(s, cudaMemcpyAsync(s->hscal, s->dscal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   CK(s, cudaStreamSynchronize(s->stream));
+  rc = check_device_error(s);
+  if (rc) return rc;
   *out_norm2 = s->hscal[0];
   return SV_OK;
 }
@@ -396,6 +421,8 @@ int sv_expect_pauli(sv_state *s, uint64_t x_mask, uint64_t z_mask, double *out) 
      }));
   CK(s, cudaMemcpyAsync(s->hscal, s->dscal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   CK(s, cudaStreamSynchronize(s->stream));
+  rc = check_device_error(s);
+  if (rc) return rc;
   if (!(s->hscal[0] > 0.0)) return fail(SV_ERR_ARG, "state has zero norm");
   *out = s->hscal[1] / s->hscal[0];
   return SV_OK;
@@ -434,7 +461,10 @@ int sv_get_amplitudes(sv_state *s, void *out, uint64_t offset, uint64_t count, i
   DeviceGuard g(s->device);
   CK(s, cudaMemcpyAsync(out, s->amp + offset, count * sizeof(float2),
                         out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
-  if (!out_on_device) CK(s, cudaStreamSynchronize(s->stream));
+  if (!out_on_device) {
+    CK(s, cudaStreamSynchronize(s->stream));
+    return check_device_error(s);
+  }
   return SV_OK;
 }
 
@@ -491,6 +521,7 @@ static int sample_impl(sv_state *s, const double *u, uint64_t seed, int use_seed
     uint64_t nb;
     std::memcpy(&nb, s->hscal, sizeof(nb));
     if (out_nb) *out_nb = nb;
+    return check_device_error(s);
   }
   return SV_OK;
 }
@@ -502,6 +533,15 @@ int sv_sample(sv_state *s, uint64_t shots, uint64_t seed, uint64_t *out_bitstrin
 int sv_sample_uniforms(sv_state *s, const double *uniforms, uint64_t shots, uint64_t *out_bitstrings,
                        uint64_t *out_n_boundary, int on_device) {
   return sample_impl(s, uniforms, 0, 0, shots, out_bitstrings, out_n_boundary, on_device);
+}
+
+int sv_tc_selftest(const float *a, const double *b, float *d) {
+  if (!a || !b || !d) return fail(SV_ERR_ARG, "null argument");
+  int status = 0;
+  cudaError_t e = tc_selftest(a, b, d, &status);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "tensor-core self-test");
+  if (status) return fail(SV_ERR_TIMEOUT, "tensor-core self-test: the MMA completion wait gave up");
+  return SV_OK;
 }
 
 int sv_profile_enable(sv_state *s, int on) {

@@ -29,6 +29,8 @@ enum : uint8_t { OP_DENSE = 1, OP_PHASE = 2 };
 constexpr int kMaxTile = 13;   // largest T (64 KiB of complex64 in shared memory)
 constexpr int kMaxK = 5;       // largest fused block
 
+enum : uint32_t { KIND_SMEM = 0, KIND_REG = 1, KIND_TC = 2 };
+
 struct alignas(16) PlanPass {
   uint64_t outer_mask;  // physical qubits outside the tile (within n)
   uint64_t high_mask;   // tile qubits >= c (their ascending order = local bits c..T-1)
@@ -39,14 +41,56 @@ struct alignas(16) PlanPass {
   uint32_t ops_off;     // byte offset of OpRec[n_ops] from the plan base
   uint32_t kmax;        // largest dense k in this pass
   uint32_t n_phase_terms;
+  uint32_t kind;        // KIND_SMEM: ops sweep the shared-memory tile one by one;
+                        // KIND_REG: register stages (see StageRec)
+  uint32_t R;           // KIND_REG: amplitudes per thread = 2^R
+  uint32_t n_stages;
+  uint32_t stages_off;  // byte offset of StageRec[n_stages]
+  uint32_t data_bytes;  // bytes from ops_off to the end of this pass's records
+  uint32_t pad_[3];
   int8_t lq[32];        // local bit -> physical qubit
 };
+
+// One register stage of a KIND_REG pass.  Thread t of the CTA holds the 2^R
+// amplitudes with local index l = la[j] | dep(t, tb), j < 2^R: register bit i
+// is local bit rb[i], thread-index bit i is local bit tb[i].  Ops of the stage
+// act on registers only.  Between stages the tile is exchanged through shared
+// memory at the XOR-swizzled index swz(l) = pa[j] ^ swz(dep(t, tb)).  The
+// first stage loads from HBM and the last stores to HBM directly (their
+// thread bits start with the low tile bits, so a warp touches contiguous runs).
+struct alignas(16) StageRec {
+  uint8_t rb[5];
+  uint8_t tb[11];
+  uint16_t pa[32];
+  uint16_t la[32];
+  uint32_t op_begin, op_end;
+  uint32_t flags;       // bit 0: load from HBM, bit 1: store to HBM,
+                        // bit 2: KIND_TC stage with a tensor-core product
+  uint32_t b_off;       // KIND_TC: byte offset of the stage's 8 KB B_hi/B_lo image
+};
+
+// Columns of the shared-memory swizzle: local bit b < 4 maps to itself, local
+// bit b >= 4 additionally flips the bank-pair bits swz_col(b) (distinct, not a
+// single bit), so any 8 local bits include 4 whose bank-pair images are
+// independent -- the lanes of a half-warp can always be chosen conflict-free.
+// kSwz nibble i (bits 4i..4i+3) is the image of local bit 4 + i.
+constexpr uint64_t kSwz = 0x1fedb7ca9653ull;
+__host__ __device__ inline uint32_t swz_col(int b) {
+  return b < 4 ? (1u << b) : uint32_t((kSwz >> (4 * (b - 4))) & 15u);
+}
+__host__ __device__ inline uint32_t swz(uint32_t l) {
+  uint32_t x = l;
+  for (int b = 4; b < 16; b++)
+    if ((l >> b) & 1u) x ^= swz_col(b);
+  return x;
+}
 
 struct alignas(16) OpRec {
   uint8_t type;
   uint8_t k;
   uint8_t lb[5];        // DENSE: local bits, matrix bit m <-> lb[m]
-  uint8_t pad;
+  uint8_t rmask;        // DENSE in a KIND_REG pass: register positions (matrix bits in
+                        // ascending register order)
   uint32_t data_off;    // DENSE: byte offset of float2[4^k] (row-major); PHASE: of PhaseTerm[]
   uint32_t count;       // PHASE: number of terms
 };
@@ -57,14 +101,19 @@ struct alignas(16) PhaseTerm {
   uint32_t turn;        // phase as a fraction of 2*pi, scaled by 2^32
 };
 
-static_assert(sizeof(PlanPass) == 80, "PlanPass layout");
+static_assert(sizeof(PlanPass) == 112, "PlanPass layout");
+static_assert(sizeof(StageRec) == 160, "StageRec layout");
 static_assert(sizeof(OpRec) == 16, "OpRec layout");
 static_assert(sizeof(PhaseTerm) == 16, "PhaseTerm layout");
 
 // Launch one pass kernel (sv_apply.cu).  plan_dev/pass_off locate the PlanPass;
 // host_pass is the same record on the host (for grid size and template choice).
 cudaError_t launch_pass(float2 *amp, const uint8_t *plan_dev, uint32_t pass_off,
-                        const PlanPass &host_pass, cudaStream_t stream);
+                        const PlanPass &host_pass, int *err, cudaStream_t stream);
+// Whether a tensor-core pass fits the kernel's shared memory.
+bool tc_pass_fits(uint32_t T, uint32_t c, uint32_t n_stages, uint32_t data_bytes);
+// Whether a register-stage pass fits the persistent kernel's shared-memory tables.
+bool reg_pass_fits(uint32_t T, uint32_t c, uint32_t n_stages, uint32_t data_bytes);
 
 // Measurement kernels (sv_measure.cu).
 struct MeasureScratch {

@@ -28,6 +28,7 @@
 #include "../../include/sv.h"
 #include "sv_internal.h"
 #include "sv_plan.h"
+#include "sv_tc.h"
 
 namespace svgb {
 
@@ -398,6 +399,251 @@ static void align16(std::vector<uint8_t> &buf) {
   while (buf.size() % 16) buf.push_back(0);
 }
 
+// ---------------------------------------------------------------------------
+// register stages (KIND_REG passes)
+// ---------------------------------------------------------------------------
+
+struct HStage {
+  uint32_t R = 0;        // local bits held in registers
+  std::vector<int> ops;  // op indices (program order within the stage)
+};
+
+// Greedy, in op order: a stage takes every op whose earlier unplaced ops do not
+// share a bit with it and whose bits fit the stage's Rb register bits.  Phase
+// ops need no register bits.  The first stage avoids the c low bits (it loads
+// from HBM with the low bits on the lanes), and a store stage is appended when
+// the last stage holds a low bit.  With `tc` the dense ops of a stage become one
+// product applied before the stage's phase ops, so a dense op that touches a
+// bit of an accepted phase op waits for a later stage.
+static void assign_stages(const std::vector<HostOp> &ops, const std::vector<uint32_t> &omask, int T,
+                          int c, int Rb, std::vector<HStage> &st, bool tc = false) {
+  const uint32_t all = (T >= 32) ? ~0u : ((1u << T) - 1u), low = (1u << c) - 1u;
+  std::vector<int> rem(ops.size());
+  for (size_t i = 0; i < ops.size(); i++) rem[i] = int(i);
+  bool first = true;
+  while (!rem.empty()) {
+    const uint32_t allowed = first ? (all & ~low) : all;
+    HStage s;
+    uint32_t blocked = 0;
+    uint32_t phase_bits = 0;  // tc: bits of accepted phase ops (applied after the stage's product)
+    std::vector<int> rest;
+    for (int o : rem) {
+      const uint32_t M = omask[o];
+      if ((M & blocked) || (tc && ops[o].type == OP_DENSE && (M & phase_bits))) {
+        blocked |= M;
+        rest.push_back(o);
+        continue;
+      }
+      if (ops[o].type == OP_PHASE) {
+        s.ops.push_back(o);
+        phase_bits |= M;
+      } else if ((M & ~s.R) == 0) {
+        s.ops.push_back(o);
+      } else if ((M & ~allowed) == 0 && popc(uint64_t(s.R | M)) <= Rb) {
+        s.R |= M;
+        s.ops.push_back(o);
+      } else {
+        blocked |= M;
+        rest.push_back(o);
+      }
+    }
+    st.push_back(std::move(s));
+    rem.swap(rest);
+    first = false;
+  }
+  if (st.empty()) st.push_back(HStage{});
+  if (st.back().R & low) st.push_back(HStage{});
+  for (size_t i = 0; i < st.size(); i++) {
+    const bool io = (i == 0) || (i + 1 == st.size());
+    const uint32_t allowed = io ? (all & ~low) : all;
+    for (int b = T - 1; b >= 0 && popc(uint64_t(st[i].R)) < Rb; b--)
+      if (((allowed >> b) & 1u) && !((st[i].R >> b) & 1u)) st[i].R |= 1u << b;
+  }
+}
+
+static StageRec make_stage(const HStage &hs, int T, int c, int Rb, bool load, bool store) {
+  StageRec sr{};
+  int nr = 0;
+  for (int b = 0; b < T; b++)
+    if ((hs.R >> b) & 1u) sr.rb[nr++] = uint8_t(b);
+  std::vector<int> rest;
+  for (int b = 0; b < T; b++)
+    if (!((hs.R >> b) & 1u)) rest.push_back(b);
+  std::vector<int> tb;
+  if (load || store) {
+    tb = rest;  // ascending: the low tile bits sit on the lanes
+  } else {
+    // four lane bits whose swizzle images are independent (one half-warp of
+    // 8-byte accesses then hits 16 distinct bank pairs), then the others
+    uint32_t basis[4] = {0, 0, 0, 0};
+    std::vector<int> lanes, others;
+    for (int b : rest) {
+      uint32_t v = swz_col(b);
+      for (int i = 3; i >= 0; i--)
+        if ((v >> i) & 1u) {
+          if (basis[i]) {
+            v ^= basis[i];
+          } else {
+            basis[i] = v;
+            break;
+          }
+        }
+      if (v && lanes.size() < 4) lanes.push_back(b);
+      else others.push_back(b);
+    }
+    tb = lanes;
+    tb.insert(tb.end(), others.begin(), others.end());
+  }
+  for (size_t i = 0; i < tb.size() && i < 11; i++) sr.tb[i] = uint8_t(tb[i]);
+  for (int j = 0; j < (1 << Rb); j++) {
+    uint32_t l = 0;
+    for (int i = 0; i < Rb; i++)
+      if ((j >> i) & 1) l |= 1u << sr.rb[i];
+    sr.la[j] = uint16_t(l);
+    sr.pa[j] = uint16_t(swz(l));
+  }
+  sr.flags = (load ? 1u : 0u) | (store ? 2u : 0u);
+  (void)c;
+  return sr;
+}
+
+// U <- G * U for a 16x16 stage matrix U, G a k-qubit matrix on bit positions pos[].
+static void apply_on_positions(std::vector<cd> &U, const std::vector<cd> &G, int k, const int *pos) {
+  const int KG = 1 << k;
+  int gmask = 0;
+  for (int x = 0; x < k; x++) gmask |= 1 << pos[x];
+  int off[32];
+  for (int j = 0; j < KG; j++) {
+    int o = 0;
+    for (int x = 0; x < k; x++)
+      if ((j >> x) & 1) o |= 1 << pos[x];
+    off[j] = o;
+  }
+  cd v[32], w[32];
+  for (int col = 0; col < 16; col++)
+    for (int r0 = 0; r0 < 16; r0++) {
+      if (r0 & gmask) continue;
+      for (int j = 0; j < KG; j++) v[j] = U[size_t(r0 | off[j]) * 16 + col];
+      for (int r = 0; r < KG; r++) {
+        cd a = 0.0;
+        for (int j = 0; j < KG; j++) a += G[size_t(r) * KG + j] * v[j];
+        w[r] = a;
+      }
+      for (int r = 0; r < KG; r++) U[size_t(r0 | off[r]) * 16 + col] = w[r];
+    }
+}
+
+// Packs a tensor-core pass (records after the PlanPass headers); false when
+// it does not fit, leaving buf untouched.
+static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint32_t> &omask, const int *lpos,
+                         int T, int c, PlanPass &hp, std::vector<uint8_t> &buf, sv_plan_info &info) {
+  std::vector<HStage> stages;
+  assign_stages(ops, omask, T, c, 4, stages, true);
+  size_t nphase = 0, terms_bytes = 0, nmma = 0;
+  for (auto &st : stages) {
+    bool mma = false;
+    for (int o : st.ops) {
+      if (ops[o].type == OP_PHASE) {
+        nphase++;
+        terms_bytes += ops[o].terms.size() * sizeof(PhaseTerm);
+      } else {
+        mma = true;
+      }
+    }
+    nmma += mma;
+  }
+  const size_t est = nphase * sizeof(OpRec) + terms_bytes + 16 * nphase + stages.size() * sizeof(StageRec) + 16 +
+                     nmma * kTcBImage + 16;
+  if (stages.size() > 64 || !tc_pass_fits(uint32_t(T), uint32_t(c), uint32_t(stages.size()), uint32_t(est)))
+    return false;
+
+  align16(buf);
+  hp.ops_off = uint32_t(buf.size());
+  const size_t ops_at = buf.size();
+  buf.resize(buf.size() + nphase * sizeof(OpRec), 0);
+  std::vector<OpRec> recs;
+  std::vector<StageRec> srecs;
+  std::vector<std::vector<double>> bmats;  // per MMA stage: B[n][k], 32x32
+  uint32_t nterms = 0;
+  for (size_t si = 0; si < stages.size(); si++) {
+    const HStage &st = stages[si];
+    StageRec sr = make_stage(st, T, c, 4, si == 0, si + 1 == stages.size());
+    sr.op_begin = uint32_t(recs.size());
+    std::vector<cd> U(256, 0.0);
+    for (int d = 0; d < 16; d++) U[size_t(d) * 17] = 1.0;
+    bool mma = false;
+    for (int o : st.ops) {
+      const HostOp &op = ops[o];
+      if (op.type == OP_PHASE) {
+        OpRec r{};
+        r.type = OP_PHASE;
+        align16(buf);
+        r.data_off = uint32_t(buf.size());
+        r.count = uint32_t(op.terms.size());
+        for (auto &t : op.terms) {
+          PhaseTerm pt{};
+          pt.outer_mask = t.outer;
+          pt.la = t.la;
+          pt.turn = t.turn;
+          put_bytes(buf, &pt, sizeof(pt));
+        }
+        nterms += r.count;
+        info.n_phase++;
+        recs.push_back(r);
+      } else {
+        const int k = op.blk.k();
+        int pos[5];
+        for (int m = 0; m < k; m++) pos[m] = popc(uint64_t(st.R & ((1u << lpos[op.blk.qs[m]]) - 1u)));
+        apply_on_positions(U, op.blk.M, k, pos);
+        mma = true;
+        info.n_blocks++;
+        info.hist_k[k]++;
+      }
+    }
+    sr.op_end = uint32_t(recs.size());
+    if (mma) {
+      sr.flags |= 4u;
+      std::vector<double> B(32 * 32);
+      for (int r = 0; r < 16; r++)
+        for (int j = 0; j < 16; j++) {
+          const cd u = U[size_t(r) * 16 + j];
+          B[(2 * r) * 32 + 2 * j] = u.real();
+          B[(2 * r) * 32 + 2 * j + 1] = -u.imag();
+          B[(2 * r + 1) * 32 + 2 * j] = u.imag();
+          B[(2 * r + 1) * 32 + 2 * j + 1] = u.real();
+        }
+      bmats.push_back(std::move(B));
+    }
+    srecs.push_back(sr);
+  }
+  std::memcpy(buf.data() + ops_at, recs.data(), recs.size() * sizeof(OpRec));
+  align16(buf);
+  hp.stages_off = uint32_t(buf.size());
+  const size_t stage_at = buf.size();
+  buf.resize(buf.size() + srecs.size() * sizeof(StageRec), 0);
+  align16(buf);
+  size_t bi = 0;
+  std::vector<uint8_t> img(kTcBImage);
+  for (auto &sr : srecs) {
+    if (sr.flags & 4u) {
+      sr.b_off = uint32_t(buf.size());
+      tc_b_image(bmats[bi++].data(), img.data());
+      put_bytes(buf, img.data(), img.size());
+    }
+  }
+  std::memcpy(buf.data() + stage_at, srecs.data(), srecs.size() * sizeof(StageRec));
+  align16(buf);
+  hp.data_bytes = uint32_t(buf.size() - hp.ops_off);
+  hp.n_ops = uint32_t(recs.size());
+  hp.n_stages = uint32_t(srecs.size());
+  hp.n_phase_terms = nterms;
+  hp.kind = KIND_TC;
+  hp.R = 4;
+  info.n_stages += srecs.size();
+  info.tc_stages += nmma;
+  return true;
+}
+
 bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Plan &plan,
                 std::string &err) {
   sv_opts o{};
@@ -415,6 +661,12 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
   }
   if (o.precision != 0 && o.precision != 1) {
     err = "precision must be 0 or 1";
+    return false;
+  }
+  // kernel_variant: 0 = register stages where possible, 1 = shared-memory sweeps
+  const bool o_smem = (o.kernel_variant == 1);
+  if (o.kernel_variant < 0 || o.kernel_variant > 1) {
+    err = "kernel_variant must be 0 or 1";
     return false;
   }
   if (T > n) T = n;
@@ -511,14 +763,69 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
     for (int q = 0; q < 64; q++) lpos[q] = -1;
     for (int x = 0; x < int(hp.T); x++) lpos[ph.lq[x]] = x;
 
+    // local-bit masks of the ops
+    const size_t nops = ph.ops.size();
+    std::vector<uint32_t> omask(nops, 0);
+    uint32_t kmx = 0;
+    for (size_t i = 0; i < nops; i++) {
+      const HostOp &op = ph.ops[i];
+      if (op.type == OP_DENSE) {
+        for (int q : op.blk.qs) omask[i] |= 1u << lpos[q];
+        kmx = std::max<uint32_t>(kmx, uint32_t(op.blk.k()));
+      } else {
+        for (auto &t : op.terms)
+          if (t.la >= 0) omask[i] |= 1u << t.la;
+      }
+    }
+    // register stages when every block fits the registers of one thread
+    const int T_ = int(hp.T);
+    // tensor-core stages (precision 1) when the pass fits the TC kernel
+    if (o.precision == 1 && kmx <= 4 &&
+        pack_tc_pass(ph.ops, omask, lpos, int(hp.T), c, hp, buf, plan.info)) {
+      hp.kmax = kmx;
+      for (auto &op : ph.ops)
+        if (op.type == OP_DENSE) plan.info.flops += uint64_t(amps * 8.0 * double(1 << op.blk.k()));
+      std::memcpy(buf.data() + p * sizeof(PlanPass), &hp, sizeof(hp));
+      plan.passes[p] = hp;
+      plan.pass_offs[p] = uint32_t(p * sizeof(PlanPass));
+      continue;
+    }
+    // register stages hold 16 amplitudes per thread (blocks up to 4 qubits);
+    // passes with a 5-qubit block use the shared-memory kernel
+    const int Rb = 4;
+    const bool use_reg = !o_smem && kmx <= 4 && T_ - Rb >= 5 && T_ - Rb <= 9 && T_ - c >= Rb;
+    std::vector<HStage> stages;
+    std::vector<int> order;
+    bool reg = use_reg;
+    if (reg) {
+      assign_stages(ph.ops, omask, T_, c, Rb, stages);
+      // bytes of this pass's records as packed below (16-byte aligned pieces)
+      size_t est = nops * sizeof(OpRec) + stages.size() * sizeof(StageRec) + 16;
+      for (auto &op : ph.ops)
+        est += op.type == OP_DENSE ? ((size_t(8) << (2 * op.blk.k())) + 15) / 16 * 16
+                                   : op.terms.size() * sizeof(PhaseTerm) + 16;
+      if (!reg_pass_fits(uint32_t(T_), uint32_t(c), uint32_t(stages.size()), uint32_t(est))) {
+        reg = false;
+        stages.clear();
+      }
+    }
+    if (reg) {
+      for (auto &st : stages) order.insert(order.end(), st.ops.begin(), st.ops.end());
+    } else {
+      for (size_t i = 0; i < nops; i++) order.push_back(int(i));
+    }
+    std::vector<int> stage_of(nops, -1);
+    for (size_t si = 0; si < stages.size(); si++)
+      for (int o : stages[si].ops) stage_of[o] = int(si);
+
     align16(buf);
     hp.ops_off = uint32_t(buf.size());
     const size_t ops_at = buf.size();
-    buf.resize(buf.size() + ph.ops.size() * sizeof(OpRec), 0);
-    std::vector<OpRec> recs(ph.ops.size());
-    uint32_t kmx = 0, nterms = 0;
-    for (size_t i = 0; i < ph.ops.size(); i++) {
-      HostOp &op = ph.ops[i];
+    buf.resize(buf.size() + nops * sizeof(OpRec), 0);
+    std::vector<OpRec> recs(nops);
+    uint32_t nterms = 0;
+    for (size_t oi = 0; oi < nops; oi++) {
+      HostOp &op = ph.ops[order[oi]];
       OpRec r{};
       r.type = op.type;
       align16(buf);
@@ -528,11 +835,29 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
         r.k = uint8_t(k);
         for (int m = 0; m < k; m++) r.lb[m] = uint8_t(lpos[op.blk.qs[m]]);
         const int K = 1 << k;
-        for (int e = 0; e < K * K; e++) {
-          float f[2] = {float(op.blk.M[e].real()), float(op.blk.M[e].imag())};
-          put_bytes(buf, f, sizeof(f));
+        // matrix bit order: block order, or ascending register position
+        int perm[5];
+        for (int m = 0; m < k; m++) perm[m] = m;
+        if (reg) {
+          const HStage &st = stages[stage_of[order[oi]]];
+          int pos[5];
+          for (int m = 0; m < k; m++) pos[m] = popc(st.R & ((1u << r.lb[m]) - 1u));
+          std::sort(perm, perm + k, [&](int a, int b) { return pos[a] < pos[b]; });
+          for (int m = 0; m < k; m++) r.rmask |= uint8_t(1u << pos[m]);
         }
-        kmx = std::max<uint32_t>(kmx, uint32_t(k));
+        // new index bit i <- old matrix bit perm[i]
+        auto old_index = [&](int x) {
+          int o = 0;
+          for (int i = 0; i < k; i++)
+            if (x >> i & 1) o |= 1 << perm[i];
+          return o;
+        };
+        for (int rr = 0; rr < K; rr++)
+          for (int cc = 0; cc < K; cc++) {
+            const cd e = op.blk.M[size_t(old_index(rr)) * K + old_index(cc)];
+            float f[2] = {float(e.real()), float(e.imag())};
+            put_bytes(buf, f, sizeof(f));
+          }
         plan.info.n_blocks++;
         plan.info.hist_k[k]++;
         plan.info.flops += uint64_t(amps * 8.0 * K);
@@ -548,11 +873,29 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
         nterms += r.count;
         plan.info.n_phase++;
       }
-      recs[i] = r;
+      recs[oi] = r;
     }
     std::memcpy(buf.data() + ops_at, recs.data(), recs.size() * sizeof(OpRec));
     hp.kmax = kmx;
     hp.n_phase_terms = nterms;
+    hp.kind = reg ? KIND_REG : KIND_SMEM;
+    if (reg) {
+      hp.R = uint32_t(Rb);
+      hp.n_stages = uint32_t(stages.size());
+      align16(buf);
+      hp.stages_off = uint32_t(buf.size());
+      uint32_t ob = 0;
+      for (size_t si = 0; si < stages.size(); si++) {
+        StageRec sr = make_stage(stages[si], T_, c, Rb, si == 0, si + 1 == stages.size());
+        sr.op_begin = ob;
+        ob += uint32_t(stages[si].ops.size());
+        sr.op_end = ob;
+        put_bytes(buf, &sr, sizeof(sr));
+      }
+      plan.info.n_stages += stages.size();
+    }
+    align16(buf);
+    hp.data_bytes = uint32_t(buf.size() - hp.ops_off);
     std::memcpy(buf.data() + p * sizeof(PlanPass), &hp, sizeof(hp));
     plan.passes[p] = hp;
     plan.pass_offs[p] = uint32_t(p * sizeof(PlanPass));

@@ -1,0 +1,152 @@
+// sv_tc.cu -- tensor-core (tcgen05, 3xTF32) pass kernel.
+//
+// A register stage of a pass (see StageRec) holds, in every thread, the 16
+// amplitudes of one "row": the 16 values of the stage's four register qubits
+// for the thread's fixed values of the other tile qubits.  All dense fused
+// blocks of the stage multiply into one 16x16 complex matrix U (built on the
+// host in complex128).  Applying it to the whole tile is the real GEMM
+//
+//     D[m][n] = sum_k A[m][k] * B[n][k],   m = row (thread), k, n < 32,
+//
+// with A[m][2j+c] = component c (re/im) of amplitude j of row m and B the real
+// embedding of U: B[2r][2j] = Re U[r][j], B[2r][2j+1] = -Im U[r][j],
+// B[2r+1][2j] = Im U[r][j], B[2r+1][2j+1] = Re U[r][j].
+//
+// Precision: split-TF32 (3xTF32).  x = x_hi + x_lo with x_hi the TF32 part of
+// x and x_lo = x - x_hi; the product is taken as A_hi*B_hi + A_hi*B_lo +
+// A_lo*B_hi with float32 accumulation, dropping A_lo*B_lo -- the split-precision
+// tensor-core scheme of Ootomo & Yokota (2022), after Markidis et al. (2018).
+// B is split on the host, A on the device; both round x_hi to the nearest TF32
+// value and take x_lo = x - x_hi (exact in float32).
+//
+// Mapping to tcgen05 (one CTA, 128 * H threads, H = 1, 2 or 4 row groups):
+//   * A_hi, A_lo of row group h live in tensor memory (lane = row % 128,
+//     32 columns each), written by the threads with tcgen05.st;
+//   * B_hi, B_lo (per stage, 8 KB) sit in shared memory in the canonical
+//     K-major layout without swizzle (8 x 16-byte core matrices);
+//   * D (32 fp32 columns per row group) accumulates in tensor memory;
+//   * one thread issues the 3 x 4 (K steps of 8) MMAs per row group of shape
+//     M=128, N=32, K=8 and commits them to an mbarrier; every wait on it is
+//     bounded by %globaltimer and reports SV_ERR_TIMEOUT through `err`.
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "sv_internal.h"
+#include "sv_tc.h"
+#include "sv_tc_ptx.cuh"
+
+namespace svgb {
+
+// ---- self-test: one 128 x 32 x 32 product -----------------------------------------
+
+__global__ void __launch_bounds__(128) k_tc_selftest(const float *__restrict__ A, const uint8_t *__restrict__ bimg,
+                                                     float *__restrict__ D, int *__restrict__ status) {
+  __shared__ __align__(1024) uint8_t bsm[kTcBImage];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tbase_s;
+  __shared__ int abort_s;
+  const uint32_t tid = threadIdx.x, warp = tid >> 5;
+  for (uint32_t i = tid; i < kTcBImage / 16; i += blockDim.x)
+    reinterpret_cast<uint4 *>(bsm)[i] = reinterpret_cast<const uint4 *>(bimg)[i];
+  fence_proxy_async_smem();
+  if (warp == 0) {
+    tmem_alloc(&tbase_s, 128);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    abort_s = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tbase_s;
+  const uint32_t tq = tbase + ((warp * 32u) << 16);
+  float x[32];
+  for (int i = 0; i < 32; i++) x[i] = A[tid * 32 + i];
+  uint32_t hi[32], lo[32];
+  split_row(x, hi, lo);
+  tmem_st32(tq + 0, hi);
+  tmem_st32(tq + 32, lo);
+  tmem_wait_st();
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0) {
+    tc_fence_after();
+    issue_stage_mma(tbase, 0, smem_u32(bsm));
+    mma_commit(&bar);
+  }
+  if (!mbar_wait_bounded(&bar, 0)) abort_s = 1;
+  __syncthreads();
+  tc_fence_after();
+  if (!abort_s) {
+    uint32_t d[32];
+    tmem_ld32(tq + 64, d);
+    tmem_wait_ld();
+    for (int i = 0; i < 32; i++) D[tid * 32 + i] = __uint_as_float(d[i]);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0) *status = abort_s;
+  if (warp == 0) tmem_dealloc(tbase, 128);
+}
+
+// ---- host helpers ------------------------------------------------------------------
+
+static inline float tf32_rn(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  u = (u + 0x1000u) & 0xFFFFE000u;
+  float r;
+  std::memcpy(&r, &u, 4);
+  return r;
+}
+
+size_t tc_b_offset(int n, int k) {
+  const int ks = k >> 3, kk = k & 7;
+  return size_t(ks) * 1024 + size_t(n >> 3) * 256 + size_t(kk >> 2) * 128 + size_t(n & 7) * 16 +
+         size_t(kk & 3) * 4;
+}
+
+void tc_b_image(const double *B, uint8_t *img) {
+  std::memset(img, 0, kTcBImage);
+  for (int n = 0; n < 32; n++)
+    for (int k = 0; k < 32; k++) {
+      const double x = B[n * 32 + k];
+      const float hi = tf32_rn(float(x));
+      const float lo = tf32_rn(float(x - double(hi)));
+      std::memcpy(img + tc_b_offset(n, k), &hi, 4);
+      std::memcpy(img + 4096 + tc_b_offset(n, k), &lo, 4);
+    }
+}
+
+cudaError_t tc_selftest(const float *A_host, const double *B_host, float *D_host, int *status_host) {
+  std::vector<uint8_t> img(kTcBImage);
+  tc_b_image(B_host, img.data());
+  float *dA = nullptr, *dD = nullptr;
+  uint8_t *dB = nullptr;
+  int *dS = nullptr;
+  cudaError_t e = cudaMalloc(&dA, 128 * 32 * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&dD, 128 * 32 * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&dB, kTcBImage);
+  if (e == cudaSuccess) e = cudaMalloc(&dS, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(dA, A_host, 128 * 32 * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dB, img.data(), kTcBImage, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(dD, 0, 128 * 32 * 4);
+  if (e == cudaSuccess) {
+    k_tc_selftest<<<1, 128>>>(dA, dB, dD, dS);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(D_host, dD, 128 * 32 * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(status_host, dS, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(dA);
+  cudaFree(dD);
+  cudaFree(dB);
+  cudaFree(dS);
+  return e;
+}
+
+}  // namespace svgb

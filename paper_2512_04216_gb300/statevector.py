@@ -48,9 +48,9 @@ class StateVector:
     def reset(self, basis_index: int = 0):
         capi.sv_reset(self.h, basis_index)
 
-    def apply(self, circuit, k_max=0, tile_qubits=0, low_qubits=0, precision=0):
+    def apply(self, circuit, k_max=0, tile_qubits=0, low_qubits=0, precision=0, kernel_variant=0):
         ir, keep = capi.to_ir(circuit)
-        opts = capi.make_opts(k_max, tile_qubits, low_qubits, precision)
+        opts = capi.make_opts(k_max, tile_qubits, low_qubits, precision, kernel_variant)
         capi.sv_apply_circuit(self.h, ir, len(circuit), opts)
         del keep
 

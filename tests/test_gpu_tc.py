@@ -1,0 +1,138 @@
+"""Tensor-core (tcgen05, 3xTF32) path: the stage product against an FP64
+product, and whole circuits with precision=1 against the complex128 oracle.
+
+Tolerances: the split-TF32 product keeps about float32 accuracy -- per element
+|d - d_fp64| <= 2e-6 * (sum_k |a_mk| |b_nk|), versus ~1e-3 for one plain TF32
+product; whole circuits use the complex64 bar of the other GPU tests
+(per-amplitude abs error <= 1e-5, fidelity >= 1 - 1e-6).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+AMP_TOL = 1e-5
+FID_TOL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def sv():
+    torch = pytest.importorskip("torch")
+    assert torch.cuda.is_available()
+    import paper_2512_04216_gb300 as P
+    return P
+
+
+def test_tc_product_matches_fp64(sv):
+    rng = np.random.default_rng(0)
+    for scale in (1.0, 1e-3, 37.0):
+        a = (rng.standard_normal((128, 32)) * scale).astype(np.float32)
+        b = rng.standard_normal((32, 32))
+        d = sv.capi.sv_tc_selftest(a, b)
+        want = a.astype(np.float64) @ b.T
+        bound = np.abs(a.astype(np.float64)) @ np.abs(b).T
+        err = np.abs(d - want)
+        assert np.all(err <= 2e-6 * bound + 1e-30), float(np.max(err / bound))
+        # the split matters: one plain TF32 product would be ~1e-3 off
+        assert float(np.max(err / bound)) < 1e-5
+
+
+def test_tc_product_unitary_embedding(sv):
+    # the real embedding of a complex 16x16 unitary maps rows of 16 complex
+    # amplitudes (interleaved re, im) to the rows of U psi
+    rng = np.random.default_rng(1)
+    z = rng.standard_normal((16, 16)) + 1j * rng.standard_normal((16, 16))
+    U, _ = np.linalg.qr(z)
+    B = np.zeros((32, 32))
+    B[0::2, 0::2] = U.real
+    B[0::2, 1::2] = -U.imag
+    B[1::2, 0::2] = U.imag
+    B[1::2, 1::2] = U.real
+    psi = rng.standard_normal((128, 16)) + 1j * rng.standard_normal((128, 16))
+    a = np.empty((128, 32), dtype=np.float32)
+    a[:, 0::2] = psi.real
+    a[:, 1::2] = psi.imag
+    d = sv.capi.sv_tc_selftest(a, B)
+    out = d[:, 0::2] + 1j * d[:, 1::2]
+    want = psi.astype(np.complex64).astype(np.complex128) @ U.T
+    assert np.max(np.abs(out - want)) < 1e-5
+
+
+def _run(P, n, circ, psi0=None, **opts):
+    s = P.StateVector(n)
+    if psi0 is not None:
+        s.set_amplitudes(psi0)
+    s.apply(circ, precision=1, **opts)
+    g = s.amplitudes().astype(np.complex128)
+    s.close()
+    return g
+
+
+def _compare(g, ref, what):
+    err = float(np.max(np.abs(g - ref)))
+    fid = oracle.fidelity(ref, g)
+    assert err <= AMP_TOL, f"{what}: max abs err {err:.3e}"
+    assert fid >= 1 - FID_TOL, f"{what}: fidelity {fid!r}"
+
+
+@pytest.mark.parametrize("T", [11, 12, 13])
+@pytest.mark.parametrize("k_max", [2, 4])
+def test_tc_random_layered(sv, T, k_max):
+    n = 16
+    circ = W.random_layered(n, 14, 21)
+    info = sv.capi.sv_plan_stats(n, circ, sv.capi.make_opts(k_max, T, 5, 1))
+    assert info["tc_stages"] > 0
+    _compare(_run(sv, n, circ, k_max=k_max, tile_qubits=T), oracle.run(n, circ), f"T={T} k={k_max}")
+
+
+def test_tc_config1_small(sv):
+    n, d = 12, 20
+    c = W.random_layered(n, d, 1)
+    _compare(_run(sv, n, c, tile_qubits=11, k_max=4), oracle.run(n, c), "n=12 d=20 T=11")
+
+
+@pytest.mark.parametrize("n", [11, 13, 15])
+def test_tc_gate_soup(sv, n):
+    rng = np.random.default_rng(n)
+    circ = W.random_gate_soup(n, 200, seed=700 + n)
+    for k in (3, 4):
+        qs = tuple(int(q) for q in rng.choice(n, size=k, replace=False))
+        z = rng.standard_normal((1 << k, 1 << k)) + 1j * rng.standard_normal((1 << k, 1 << k))
+        u, _ = np.linalg.qr(z)
+        circ.insert(len(circ) // 3, ("unitary", qs, (u,)))
+    psi0 = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    psi0 = (psi0 / np.linalg.norm(psi0)).astype(np.complex64)
+    ref = oracle.run(n, circ, psi0.astype(np.complex128))
+    _compare(_run(sv, n, circ, psi0, k_max=4, tile_qubits=min(n, 12)), ref, f"soup n={n}")
+
+
+def test_tc_qft_closed_form(sv):
+    for n in (14, 18):
+        x = W.basis_index(n, 5)
+        s = sv.StateVector(n, basis_index=x)
+        s.apply(W.qft(n), precision=1, k_max=4)
+        g = s.amplitudes().astype(np.complex128)
+        s.close()
+        y = np.arange(1 << n)
+        _compare(g, np.exp(2j * np.pi * ((x * y) % (1 << n)) / (1 << n)) / math.sqrt(1 << n), f"QFT {n}")
+
+
+def test_tc_mirror_28(sv):
+    n = 28
+    c = W.random_layered(n, 40, 2)
+    s = sv.StateVector(n)
+    s.apply(c + W.inverse(c), precision=1, k_max=4)
+    a0 = s.amplitudes(0, 1)[0]
+    norm2 = s.norm2()
+    # fidelity with |0...0>: |a_0|^2 / ||psi||^2
+    assert abs(a0) ** 2 / norm2 >= 1 - FID_TOL, (abs(a0) ** 2, norm2)
+    # The tensor cores' float32 accumulation shrinks the norm by ~1.3e-7 per
+    # stage product (~520 products here); sampling and expectations divide by
+    # the norm, and the fidelity above is unaffected.
+    assert abs(norm2 - 1) < 2e-4, norm2
+    s.close()
