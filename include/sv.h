@@ -191,6 +191,32 @@ int sv_sample_uniforms(sv_state *s, const double *uniforms, uint64_t shots,
  */
 int sv_expect_pauli(sv_state *s, uint64_t x_mask, uint64_t z_mask, double *out);
 
+/*
+ * Allocation-free <Z_mask>, for callers that cannot allocate device memory
+ * when they need the value: e.g. a process that reserved all free GPU memory
+ * for resident state vectors up front, or a latency-critical loop that cannot
+ * take cudaMalloc's implicit device-wide synchronisation.  (The paper has no
+ * counterpart: this is a deployment variant of sv_expect_pauli.)
+ *
+ * amplitudes: device pointer to 2^n_qubits complex64 (16-byte aligned), read
+ * only.  out: device pointer to 2 doubles, written with out[0] = <Z_mask> =
+ * sum_i |a_i|^2 (-1)^popcount(i & z_mask) / sum_i |a_i|^2 and out[1] =
+ * sum_i |a_i|^2, the same sums and order as sv_expect_pauli.  Queued on
+ * cuda_stream (a cudaStream_t; NULL = legacy default stream); asynchronous.
+ *
+ * Limit: n_qubits <= 28 -- the scratch is a fixed 1 MiB array compiled into the
+ * library, which every GPU that loads it holds until the process exits; larger
+ * states return SV_ERR_ARG.  No cudaMalloc, cudaFree or other allocating call
+ * is made.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls on a device share the one array,
+ * which keeps the last call's contents; every slot a call reads is written
+ * earlier in that same call, so nothing needs clearing, but calls whose work
+ * overlaps on the GPU (e.g. queued on different streams) race -- serialise them.
+ */
+int sv_expect_z_static(const void *amplitudes, int n_qubits, uint64_t z_mask, double *out,
+                       void *cuda_stream);
+
 /* ---- profiling ----------------------------------------------------------- */
 
 /* Per-kernel-kind launch records.  When enabled, the library brackets every

@@ -95,6 +95,7 @@ _SIGS = {
     "sv_version": ([], ctypes.c_char_p),
     "sv_launch_count": ([], ctypes.c_uint64),
     "sv_tc_selftest": ([_P, _P, _P], _i),
+    "sv_expect_z_static": ([_P, _i, _u64, _P, _P], _i),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_L, _name)
@@ -268,6 +269,13 @@ def sv_tc_selftest(a, b):
     d = np.empty((128, 32), dtype=np.float32)
     _check(_L.sv_tc_selftest(a.ctypes.data, b.ctypes.data, d.ctypes.data))
     return d
+
+
+def sv_expect_z_static(dev_amplitudes, n_qubits: int, z_mask: int, dev_out, stream=None):
+    """Allocation-free <Z_mask> into dev_out[0] (and the norm into dev_out[1]);
+    both pointers are device memory; queued on `stream` (see include/sv.h)."""
+    _check(_L.sv_expect_z_static(_ptr(dev_amplitudes), int(n_qubits), int(z_mask), _ptr(dev_out),
+                                 _stream_ptr(stream)))
 
 
 def sv_profile_enable(h, on: bool = True):

@@ -43,6 +43,16 @@ struct ProfRec {
 
 }  // namespace
 
+int svgb::set_last_error(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
 struct sv_state {
   int n = 0;
   int device = 0;

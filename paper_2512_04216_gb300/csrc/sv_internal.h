@@ -140,4 +140,7 @@ cudaError_t launch_reset(float2 *amp, int n, uint64_t basis, cudaStream_t st);
 
 size_t reduce_parts(int n);
 
+// Records the calling thread's sv_last_error() message (sv_capi.cu); returns code.
+int set_last_error(int code, const char *fmt, ...);
+
 }  // namespace svgb
