@@ -103,6 +103,8 @@ typedef struct sv_plan_info {
   uint64_t upload_bytes; /* size of the packed plan copied host -> device per apply */
   uint64_t n_stages;   /* register stages over all register-stage passes */
   uint64_t tc_stages;  /* stages applied as one 3xTF32 tensor-core product (precision 1) */
+  uint64_t passes_by_kind[3]; /* passes run by the shared-memory sweep kernel, the
+                                 register-stage kernel and the tensor-core kernel */
 } sv_plan_info;
 
 /* ---- lifetime ------------------------------------------------------------ */
@@ -216,6 +218,51 @@ int sv_expect_pauli(sv_state *s, uint64_t x_mask, uint64_t z_mask, double *out);
  */
 int sv_expect_z_static(const void *amplitudes, int n_qubits, uint64_t z_mask, double *out,
                        void *cuda_stream);
+
+/* ---- batched circuits -----------------------------------------------------
+ *
+ * Many independent small circuits in one persistent kernel, captured once in
+ * a CUDA graph (the paper's batch execution, §IV-B, where per-circuit launch
+ * and transfer overheads make GPU simulation lose on small circuits, §II).
+ * Each CTA runs whole circuits: a state of <= 13 qubits stays in shared
+ * memory for the whole circuit; larger states (<= 24 qubits) live in a device
+ * arena owned by the batch.  Every circuit starts in |0...0> and is measured
+ * `shots[i]` times with counter-based SplitMix64 uniforms from `seeds[i]`
+ * (the same rule and draws as sv_sample).  Gates are fused into blocks of at
+ * most k_max <= 3 qubits; tile_qubits (<= 13) tiles the arena states.
+ */
+typedef struct sv_batch sv_batch;
+
+/* Plan every circuit (host), allocate the plan, arena and sample buffers, and
+ * capture the launch in a CUDA graph.  irs[i] / n_gates[i] / n_qubits[i]
+ * describe circuit i (host memory, read during the call).  keep_states != 0
+ * also copies every final state to the arena (for sv_batch_amplitudes).
+ * Work is queued on cuda_stream (NULL = legacy default stream). */
+int sv_batch_create(size_t n_circ, const sv_gate *const *irs, const size_t *n_gates, const int *n_qubits,
+                    const uint64_t *shots, const uint64_t *seeds, const sv_opts *opts, int keep_states,
+                    void *cuda_stream, sv_batch **out);
+/* Replay the captured graph (all circuits, all shots); asynchronous. */
+int sv_batch_launch(sv_batch *b);
+int sv_batch_synchronize(sv_batch *b);
+/* Samples of circuit i (caller's order) after the last launch: shots[i]
+ * uint64 into out (device pointer if on_device, else host; host copies sync). */
+int sv_batch_samples(sv_batch *b, size_t circuit, uint64_t *out, int on_device);
+/* Final state of circuit i (2^n complex64 into host memory; synchronous).
+ * States of <= 13 qubits are available only with keep_states. */
+int sv_batch_amplitudes(sv_batch *b, size_t circuit, void *out);
+/* Planned HBM passes over arena states and their algorithmic bytes. */
+int sv_batch_stats(const sv_batch *b, uint64_t *n_passes, uint64_t *hbm_bytes);
+int sv_batch_destroy(sv_batch *b);
+/* One-shot: create, launch, copy every circuit's samples to out[i] (host
+ * pointers; NULL skips), destroy. */
+int sv_batch_run(const sv_gate *const *irs, const size_t *n_gates, const int *n_qubits, size_t n_circ,
+                 const uint64_t *shots, const uint64_t *seeds, uint64_t *const *out, const sv_opts *opts);
+/* Autotuner: times every (k_max in 1..3, tile_qubits in 10..13) batch of the
+ * given circuits (typically a sample of a larger batch) over `reps` graph
+ * launches after one warm-up, and returns the fastest options in *best (and
+ * its time per launch in *best_ms, may be NULL). */
+int sv_batch_autotune(size_t n_circ, const sv_gate *const *irs, const size_t *n_gates, const int *n_qubits,
+                      const uint64_t *shots, const uint64_t *seeds, int reps, sv_opts *best, double *best_ms);
 
 /* ---- profiling ----------------------------------------------------------- */
 

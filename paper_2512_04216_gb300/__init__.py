@@ -9,12 +9,14 @@ that the build script can run before the library exists.
 """
 import importlib
 
-__all__ = ["capi", "StateVector", "build"]
+__all__ = ["capi", "StateVector", "Batch", "build"]
 
 
 def __getattr__(name):
-    if name in ("capi", "build", "statevector"):
+    if name in ("capi", "build", "statevector", "batch", "serve"):
         return importlib.import_module(f".{name}", __name__)
     if name == "StateVector":
         return importlib.import_module(".statevector", __name__).StateVector
+    if name == "Batch":
+        return importlib.import_module(".batch", __name__).Batch
     raise AttributeError(name)

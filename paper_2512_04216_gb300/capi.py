@@ -54,13 +54,15 @@ class sv_plan_info(ctypes.Structure):
                 ("n_phase", ctypes.c_uint64), ("n_passes", ctypes.c_uint64),
                 ("hist_k", ctypes.c_uint64 * 6), ("flops", ctypes.c_uint64),
                 ("bytes", ctypes.c_uint64), ("upload_bytes", ctypes.c_uint64),
-                ("n_stages", ctypes.c_uint64), ("tc_stages", ctypes.c_uint64)]
+                ("n_stages", ctypes.c_uint64), ("tc_stages", ctypes.c_uint64),
+                ("passes_by_kind", ctypes.c_uint64 * 3)]
 
     def as_dict(self):
         return {"n_gates": self.n_gates, "n_blocks": self.n_blocks, "n_phase": self.n_phase,
                 "n_passes": self.n_passes, "hist_k": list(self.hist_k), "flops": self.flops,
                 "bytes": self.bytes, "upload_bytes": self.upload_bytes,
-                "n_stages": self.n_stages, "tc_stages": self.tc_stages}
+                "n_stages": self.n_stages, "tc_stages": self.tc_stages,
+                "passes_by_kind": list(self.passes_by_kind)}
 
 
 class sv_kernel_stat(ctypes.Structure):
@@ -96,6 +98,15 @@ _SIGS = {
     "sv_launch_count": ([], ctypes.c_uint64),
     "sv_tc_selftest": ([_P, _P, _P], _i),
     "sv_expect_z_static": ([_P, _i, _u64, _P, _P], _i),
+    "sv_batch_create": ([ctypes.c_size_t, _P, _P, _P, _P, _P, _P, _i, _P, ctypes.POINTER(_P)], _i),
+    "sv_batch_launch": ([_P], _i),
+    "sv_batch_synchronize": ([_P], _i),
+    "sv_batch_samples": ([_P, ctypes.c_size_t, _P, _i], _i),
+    "sv_batch_amplitudes": ([_P, ctypes.c_size_t, _P], _i),
+    "sv_batch_stats": ([_P, _P, _P], _i),
+    "sv_batch_destroy": ([_P], _i),
+    "sv_batch_run": ([_P, _P, _P, ctypes.c_size_t, _P, _P, _P, _P], _i),
+    "sv_batch_autotune": ([ctypes.c_size_t, _P, _P, _P, _P, _P, _i, _P, _P], _i),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_L, _name)
@@ -276,6 +287,70 @@ def sv_expect_z_static(dev_amplitudes, n_qubits: int, z_mask: int, dev_out, stre
     both pointers are device memory; queued on `stream` (see include/sv.h)."""
     _check(_L.sv_expect_z_static(_ptr(dev_amplitudes), int(n_qubits), int(z_mask), _ptr(dev_out),
                                  _stream_ptr(stream)))
+
+
+class BatchArgs:
+    """Marshalled arrays for the sv_batch_* calls (keeps the IR arrays alive)."""
+
+    def __init__(self, circuits, n_qubits, shots, seeds):
+        self.irs = [to_ir(c) for c in circuits]
+        self.ptrs = np.array([ir.ctypes.data for ir, _ in self.irs], dtype=np.uint64)
+        self.n_gates = np.array([len(c) for c in circuits], dtype=np.uint64)
+        self.n_qubits = np.array(n_qubits, dtype=np.int32)
+        self.shots = np.array(shots, dtype=np.uint64)
+        self.seeds = np.array([int(x) & (2**64 - 1) for x in seeds], dtype=np.uint64)
+        self.n = len(circuits)
+
+
+def sv_batch_create(args: BatchArgs, opts=None, keep_states=False, stream=None):
+    h = _P()
+    _check(_L.sv_batch_create(args.n, args.ptrs.ctypes.data, args.n_gates.ctypes.data,
+                              args.n_qubits.ctypes.data, args.shots.ctypes.data, args.seeds.ctypes.data,
+                              ctypes.byref(opts) if opts is not None else None, int(bool(keep_states)),
+                              _stream_ptr(stream), ctypes.byref(h)))
+    return h
+
+
+def sv_batch_launch(h):
+    _check(_L.sv_batch_launch(h))
+
+
+def sv_batch_synchronize(h):
+    _check(_L.sv_batch_synchronize(h))
+
+
+def sv_batch_samples(h, circuit: int, out, on_device: bool = False):
+    _check(_L.sv_batch_samples(h, int(circuit), _ptr(out), int(bool(on_device))))
+
+
+def sv_batch_amplitudes(h, circuit: int, out):
+    _check(_L.sv_batch_amplitudes(h, int(circuit), _ptr(out)))
+
+
+def sv_batch_stats(h):
+    a, b = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_L.sv_batch_stats(h, ctypes.byref(a), ctypes.byref(b)))
+    return {"passes": a.value, "hbm_bytes": b.value}
+
+
+def sv_batch_destroy(h):
+    _check(_L.sv_batch_destroy(h))
+
+
+def sv_batch_run(args: BatchArgs, outs, opts=None):
+    ptrs = np.array([_ptr(o) or 0 for o in outs], dtype=np.uint64)
+    _check(_L.sv_batch_run(args.ptrs.ctypes.data, args.n_gates.ctypes.data, args.n_qubits.ctypes.data, args.n,
+                           args.shots.ctypes.data, args.seeds.ctypes.data, ptrs.ctypes.data,
+                           ctypes.byref(opts) if opts is not None else None))
+
+
+def sv_batch_autotune(args: BatchArgs, reps: int = 2):
+    best = sv_opts()
+    ms = ctypes.c_double()
+    _check(_L.sv_batch_autotune(args.n, args.ptrs.ctypes.data, args.n_gates.ctypes.data,
+                                args.n_qubits.ctypes.data, args.shots.ctypes.data, args.seeds.ctypes.data,
+                                int(reps), ctypes.byref(best), ctypes.byref(ms)))
+    return best, ms.value
 
 
 def sv_profile_enable(h, on: bool = True):

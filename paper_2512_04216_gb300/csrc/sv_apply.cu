@@ -21,128 +21,13 @@
 // fractions (exact modulo 2*pi) over the low and high halves of the tile index.
 #include <cstdint>
 
+#include "sv_device.cuh"
 #include "sv_internal.h"
 #include "sv_tc_ptx.cuh"
 
 namespace svgb {
 
 constexpr int kNT = 256;  // threads per CTA
-
-__device__ __forceinline__ uint64_t pdep_u64(uint64_t src, uint64_t mask) {
-  uint64_t out = 0;
-  while (mask) {
-    const uint64_t low = mask & (~mask + 1);
-    if (src & 1) out |= low;
-    src >>= 1;
-    mask &= mask - 1;
-  }
-  return out;
-}
-
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-}
-
-// Dense k-qubit block on local bits lb[0..K-1]: for every group (the 2^(T-K)
-// index patterns with those bits clear) gather 2^K amplitudes, multiply by the
-// 2^K x 2^K matrix, scatter back.
-template <int K>
-__device__ __forceinline__ void apply_dense(float2 *__restrict__ tile, const float2 *__restrict__ mat,
-                                            const uint8_t *lb, uint32_t T) {
-  constexpr int KK = 1 << K;
-  uint32_t sp[K];
-#pragma unroll
-  for (int m = 0; m < K; m++) sp[m] = lb[m];
-  // ascending order for zero-bit insertion
-#pragma unroll
-  for (int a = 0; a < K; a++)
-#pragma unroll
-    for (int b = 0; b + 1 < K - a; b++)
-      if (sp[b] > sp[b + 1]) {
-        const uint32_t t = sp[b];
-        sp[b] = sp[b + 1];
-        sp[b + 1] = t;
-      }
-  uint32_t off[KK];
-#pragma unroll
-  for (int j = 0; j < KK; j++) {
-    uint32_t o = 0;
-#pragma unroll
-    for (int m = 0; m < K; m++)
-      if ((j >> m) & 1) o |= 1u << lb[m];
-    off[j] = o;
-  }
-  const uint32_t groups = 1u << (T - K);
-  for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
-    uint32_t b = g;
-#pragma unroll
-    for (int m = 0; m < K; m++) b = ((b >> sp[m]) << (sp[m] + 1)) | (b & ((1u << sp[m]) - 1u));
-    float2 v[KK];
-#pragma unroll
-    for (int j = 0; j < KK; j++) v[j] = tile[b + off[j]];
-#pragma unroll
-    for (int r = 0; r < KK; r++) {
-      float re = 0.f, im = 0.f;
-#pragma unroll
-      for (int j = 0; j < KK; j++) {
-        const float2 m = mat[r * KK + j];
-        re = fmaf(m.x, v[j].x, re);
-        re = fmaf(-m.y, v[j].y, re);
-        im = fmaf(m.x, v[j].y, im);
-        im = fmaf(m.y, v[j].x, im);
-      }
-      tile[b + off[r]] = make_float2(re, im);
-    }
-  }
-}
-
-// Diagonal phase op.  Each term adds `turn` (2*pi / 2^32 units) to the phase of
-// every amplitude whose outer qubits in term.outer_mask are all 1 (fixed for
-// this tile) and whose local bit term.la is 1 (or unconditionally if la < 0).
-// The per-tile phase is then a sum of per-local-bit turns, tabulated over the
-// low and high halves of the tile index.
-__device__ __forceinline__ void apply_phase(float2 *__restrict__ tile, const PhaseTerm *__restrict__ terms,
-                                            uint32_t count, uint64_t base, uint32_t T,
-                                            uint32_t *acc, float2 *tab) {
-  if (threadIdx.x <= T) acc[threadIdx.x] = 0u;
-  __syncthreads();
-  for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) {
-    const PhaseTerm pt = terms[i];
-    if ((base & pt.outer_mask) == pt.outer_mask) atomicAdd(&acc[pt.la + 1], pt.turn);
-  }
-  __syncthreads();
-  const uint32_t h = T >> 1;
-  const uint32_t nlo = 1u << h, nhi = 1u << (T - h);
-  for (uint32_t e = threadIdx.x; e < nlo + nhi; e += blockDim.x) {
-    uint32_t turn;
-    if (e < nlo) {
-      turn = acc[0];
-      for (uint32_t j = 0; j < h; j++)
-        if ((e >> j) & 1u) turn += acc[1 + j];
-    } else {
-      const uint32_t e2 = e - nlo;
-      turn = 0u;
-      for (uint32_t j = 0; j < T - h; j++)
-        if ((e2 >> j) & 1u) turn += acc[1 + h + j];
-    }
-    float s, c;
-    sincospif(static_cast<float>(static_cast<int32_t>(turn)) * 4.656612873077393e-10f, &s, &c);
-    tab[e] = make_float2(c, s);
-  }
-  __syncthreads();
-  const uint32_t L = 1u << T, lmask = nlo - 1u;
-  for (uint32_t l = threadIdx.x; l < L; l += blockDim.x) {
-    const float2 a = tab[l & lmask], b = tab[nlo + (l >> h)];
-    const float2 f = make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-    const float2 v = tile[l];
-    tile[l] = make_float2(v.x * f.x - v.y * f.y, v.x * f.y + v.y * f.x);
-  }
-}
 
 template <int KMAX>
 __global__ void __launch_bounds__(kNT) k_pass(float2 *__restrict__ amp, const uint8_t *__restrict__ plan,
@@ -324,8 +209,8 @@ __device__ __forceinline__ void reg_phase(float2 (&v)[1 << R], const PhaseTerm *
 // amplitudes stream into `buf_in` with cp.async; stage 0 reads `buf_in`
 // (natural order: its lanes are the low tile bits), later stages exchange
 // through the swizzled `buf_x`, and the last stage stores straight to HBM.
-constexpr int kMaxStages = 24;     // stage tables kept in shared memory
-constexpr uint32_t kMaxPassData = 24 * 1024;
+constexpr int kMaxStages = 64;     // stage tables kept in shared memory
+constexpr uint32_t kMaxPassData = 160 * 1024;
 
 struct RegLayout {
   uint32_t L, nseg, NT, ns;
@@ -507,11 +392,11 @@ constexpr int kTcErrTimeout = 1;
 constexpr size_t kTcStaticSmem = 1024;  // bar, tbase, abort flag (aligned with the dynamic region)
 
 template <int NTMAX>
-__global__ void __launch_bounds__(NTMAX, 1) k_pass_tc(float2 *__restrict__ amp, const uint8_t *__restrict__ plan,
+__global__ void __launch_bounds__(NTMAX, NTMAX <= 128 ? 4 : (NTMAX <= 256 ? 2 : 1)) k_pass_tc(float2 *__restrict__ amp, const uint8_t *__restrict__ plan,
                                                       uint32_t pass_off, int *__restrict__ err) {
   constexpr int NR = 16;  // R = 4 register qubits
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar[8];  // one per issuing warp (<= 4 groups x 2)
   __shared__ uint32_t tbase_s;
   __shared__ int abort_s;
   const PlanPass *P = reinterpret_cast<const PlanPass *>(plan + pass_off);
@@ -543,10 +428,8 @@ __global__ void __launch_bounds__(NTMAX, 1) k_pass_tc(float2 *__restrict__ amp, 
     tmem_alloc(&tbase_s, ncols);
     tmem_relinquish();
   }
-  if (tid == 0) {
-    mbar_init(&bar, 1);
-    abort_s = 0;
-  }
+  if (tid < 8) mbar_init(&bar[tid], 1);
+  if (tid == 0) abort_s = 0;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -624,13 +507,18 @@ __global__ void __launch_bounds__(NTMAX, 1) k_pass_tc(float2 *__restrict__ amp, 
         tmem_wait_st();
         tc_fence_before();
         __syncthreads();
-        if (tid == 0) {
+        // issuers: lane 0 of warp 2g + h issues half h of group g's product
+        if ((tid & 31) == 0 && warp < kTcIssuersPerGroup * groups) {
           tc_fence_after();
-          const uint32_t bsa = smem_u32(data + (st.b_off - data_off));
-          for (uint32_t g = 0; g < groups; g++) issue_stage_mma(tbase, g, bsa);
-          mma_commit(&bar);
+          issue_stage_mma_half(tbase, warp / kTcIssuersPerGroup, warp % kTcIssuersPerGroup,
+                               smem_u32(data + (st.b_off - data_off)));
+          mma_commit(&bar[warp]);
         }
-        if (!mbar_wait_bounded(&bar, parity)) abort_s = 1;
+        {
+          const uint32_t g = tid >> 7;
+          if (!mbar_wait_bounded(&bar[2 * g], parity) || !mbar_wait_bounded(&bar[2 * g + 1], parity))
+            abort_s = 1;
+        }
         parity ^= 1u;
         __syncthreads();
         if (abort_s) {
@@ -639,9 +527,13 @@ __global__ void __launch_bounds__(NTMAX, 1) k_pass_tc(float2 *__restrict__ amp, 
         }
         tc_fence_after();
         tmem_ld32(tq + 64, r);
+        uint32_t r1[32];
+        tmem_ld32(tq + 96, r1);
         tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < NR; j++) v[j] = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+        for (int j = 0; j < NR; j++)
+          v[j] = make_float2(__fadd_rn(__uint_as_float(r[2 * j]), __uint_as_float(r1[2 * j])),
+                             __fadd_rn(__uint_as_float(r[2 * j + 1]), __uint_as_float(r1[2 * j + 1])));
       }
       const uint32_t oe = st.op_end;
       for (uint32_t o = st.op_begin; o < oe; o++) {

@@ -901,6 +901,7 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
     plan.pass_offs[p] = uint32_t(p * sizeof(PlanPass));
   }
   align16(buf);
+  for (auto &hp : plan.passes) plan.info.passes_by_kind[hp.kind < 3 ? hp.kind : 0]++;
   plan.info.n_passes = P;
   plan.info.bytes = uint64_t(double(P) * 16.0 * amps);
   plan.info.upload_bytes = buf.size();

@@ -24,10 +24,13 @@
 //     32 columns each), written by the threads with tcgen05.st;
 //   * B_hi, B_lo (per stage, 8 KB) sit in shared memory in the canonical
 //     K-major layout without swizzle (8 x 16-byte core matrices);
-//   * D (32 fp32 columns per row group) accumulates in tensor memory;
-//   * one thread issues the 3 x 4 (K steps of 8) MMAs per row group of shape
-//     M=128, N=32, K=8 and commits them to an mbarrier; every wait on it is
-//     bounded by %globaltimer and reports SV_ERR_TIMEOUT through `err`.
+//   * two accumulators D0, D1 (32 fp32 columns each per row group) live in
+//     tensor memory; two threads (lane 0 of two warps) per row group each issue
+//     the 3 products of half of the K steps (3 x 2 MMAs of shape M=128, N=32,
+//     K=8) into their own accumulator and commit them to their own mbarrier --
+//     one issuing thread waits ~230 cycles per tcgen05.mma, so issue is spread;
+//   * D = D0 + D1 is formed in registers after tcgen05.ld; every mbarrier wait
+//     is bounded by %globaltimer and reports SV_ERR_TIMEOUT through `err`.
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -43,7 +46,7 @@ namespace svgb {
 __global__ void __launch_bounds__(128) k_tc_selftest(const float *__restrict__ A, const uint8_t *__restrict__ bimg,
                                                      float *__restrict__ D, int *__restrict__ status) {
   __shared__ __align__(1024) uint8_t bsm[kTcBImage];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t tbase_s;
   __shared__ int abort_s;
   const uint32_t tid = threadIdx.x, warp = tid >> 5;
@@ -55,7 +58,8 @@ __global__ void __launch_bounds__(128) k_tc_selftest(const float *__restrict__ A
     tmem_relinquish();
   }
   if (tid == 0) {
-    mbar_init(&bar, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     abort_s = 0;
   }
   tc_fence_before();
@@ -72,19 +76,20 @@ __global__ void __launch_bounds__(128) k_tc_selftest(const float *__restrict__ A
   tmem_wait_st();
   tc_fence_before();
   __syncthreads();
-  if (tid == 0) {
+  if ((tid & 31) == 0 && warp < kTcIssuersPerGroup) {
     tc_fence_after();
-    issue_stage_mma(tbase, 0, smem_u32(bsm));
-    mma_commit(&bar);
+    issue_stage_mma_half(tbase, 0, warp, smem_u32(bsm));
+    mma_commit(&bar[warp]);
   }
-  if (!mbar_wait_bounded(&bar, 0)) abort_s = 1;
+  if (!mbar_wait_bounded(&bar[0], 0) || !mbar_wait_bounded(&bar[1], 0)) abort_s = 1;
   __syncthreads();
   tc_fence_after();
   if (!abort_s) {
-    uint32_t d[32];
-    tmem_ld32(tq + 64, d);
+    uint32_t d0[32], d1[32];
+    tmem_ld32(tq + 64, d0);
+    tmem_ld32(tq + 96, d1);
     tmem_wait_ld();
-    for (int i = 0; i < 32; i++) D[tid * 32 + i] = __uint_as_float(d[i]);
+    for (int i = 0; i < 32; i++) D[tid * 32 + i] = __fadd_rn(__uint_as_float(d0[i]), __uint_as_float(d1[i]));
   }
   tc_fence_before();
   __syncthreads();

@@ -8,7 +8,8 @@
 namespace svgb {
 
 constexpr uint32_t kTcBImage = 8192;       // B_hi (4 K steps x 1 KB) then B_lo
-constexpr uint32_t kTcColsPerGroup = 96;   // TMEM columns per 128-row group: A_hi, A_lo, D
+constexpr uint32_t kTcColsPerGroup = 128;  // TMEM columns per 128-row group: A_hi, A_lo, D0, D1
+constexpr uint32_t kTcIssuersPerGroup = 2; // MMA-issuing warps per row group (half the K steps each)
 
 // Byte offset of B[n][k] (n, k < 32) inside one 4 KB half of a stage image.
 size_t tc_b_offset(int n, int k);

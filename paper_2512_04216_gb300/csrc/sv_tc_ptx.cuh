@@ -123,16 +123,29 @@ __device__ __forceinline__ uint64_t b_desc(uint32_t saddr) {
 // Instruction descriptor: D f32, A/B tf32, both K-major, N=32, M=128.
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
 
-// The 3xTF32 product of one stage for row group h (issued by one thread).
-__device__ __forceinline__ void issue_stage_mma(uint32_t tbase, uint32_t h, uint32_t b_saddr) {
-  const uint32_t a_hi = tbase + h * kTcColsPerGroup, a_lo = a_hi + 32, d = a_hi + 64;
+// Half h (K steps 2h, 2h+1) of the 3xTF32 product of one stage for row group g,
+// accumulated into its own D_h (columns 64 + 32h of the group); issued by one
+// thread.  A single issuing thread waits ~230 cycles per tcgen05.mma whatever
+// the shape, so each group's products are split over two issuers and the two
+// partial accumulators are added after tcgen05.ld.
+__device__ __forceinline__ void issue_stage_mma_half(uint32_t tbase, uint32_t g, uint32_t h, uint32_t b_saddr) {
+  const uint32_t a_hi = tbase + g * kTcColsPerGroup, a_lo = a_hi + 32, d = a_hi + 64 + 32 * h;
   const uint32_t bhi = b_saddr, blo = b_saddr + 4 * 1024;
 #pragma unroll
-  for (uint32_t ks = 0; ks < 4; ks++) mma_tf32_ts(d, a_hi + 8 * ks, b_desc(blo + ks * 1024), kIdesc, ks > 0);
+  for (uint32_t i = 0; i < 2; i++) {
+    const uint32_t ks = 2 * h + i;
+    mma_tf32_ts(d, a_hi + 8 * ks, b_desc(blo + ks * 1024), kIdesc, i > 0);
+  }
 #pragma unroll
-  for (uint32_t ks = 0; ks < 4; ks++) mma_tf32_ts(d, a_lo + 8 * ks, b_desc(bhi + ks * 1024), kIdesc, 1);
+  for (uint32_t i = 0; i < 2; i++) {
+    const uint32_t ks = 2 * h + i;
+    mma_tf32_ts(d, a_lo + 8 * ks, b_desc(bhi + ks * 1024), kIdesc, 1);
+  }
 #pragma unroll
-  for (uint32_t ks = 0; ks < 4; ks++) mma_tf32_ts(d, a_hi + 8 * ks, b_desc(bhi + ks * 1024), kIdesc, 1);
+  for (uint32_t i = 0; i < 2; i++) {
+    const uint32_t ks = 2 * h + i;
+    mma_tf32_ts(d, a_hi + 8 * ks, b_desc(bhi + ks * 1024), kIdesc, 1);
+  }
 }
 
 // x_hi: x rounded to the nearest TF32 value (ties away from zero; the 13 low
