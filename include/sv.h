@@ -235,18 +235,22 @@ typedef struct sv_batch sv_batch;
 
 /* Plan every circuit (host), allocate the plan, arena and sample buffers, and
  * capture the launch in a CUDA graph.  irs[i] / n_gates[i] / n_qubits[i]
- * describe circuit i (host memory, read during the call).  keep_states != 0
- * also copies every final state to the arena (for sv_batch_amplitudes).
- * Work is queued on cuda_stream (NULL = legacy default stream). */
+ * describe circuit i (host memory, read during the call); shots[i] may be 0.
+ * zmasks (may be NULL): zmasks[i] != 0 also computes <Z_zmasks[i]> of circuit
+ * i (sv_batch_expectation).  keep_states != 0 also copies every final state to
+ * the arena (for sv_batch_amplitudes).  Work is queued on cuda_stream (NULL =
+ * legacy default stream). */
 int sv_batch_create(size_t n_circ, const sv_gate *const *irs, const size_t *n_gates, const int *n_qubits,
-                    const uint64_t *shots, const uint64_t *seeds, const sv_opts *opts, int keep_states,
-                    void *cuda_stream, sv_batch **out);
+                    const uint64_t *shots, const uint64_t *seeds, const uint64_t *zmasks, const sv_opts *opts,
+                    int keep_states, void *cuda_stream, sv_batch **out);
 /* Replay the captured graph (all circuits, all shots); asynchronous. */
 int sv_batch_launch(sv_batch *b);
 int sv_batch_synchronize(sv_batch *b);
 /* Samples of circuit i (caller's order) after the last launch: shots[i]
  * uint64 into out (device pointer if on_device, else host; host copies sync). */
 int sv_batch_samples(sv_batch *b, size_t circuit, uint64_t *out, int on_device);
+/* out2[0] = <Z_zmask> of circuit i, out2[1] = its norm (host; synchronous). */
+int sv_batch_expectation(sv_batch *b, size_t circuit, double *out2);
 /* Final state of circuit i (2^n complex64 into host memory; synchronous).
  * States of <= 13 qubits are available only with keep_states. */
 int sv_batch_amplitudes(sv_batch *b, size_t circuit, void *out);

@@ -9,8 +9,8 @@ from . import capi
 
 class Batch:
     def __init__(self, circuits, n_qubits, shots, seeds, k_max=0, tile_qubits=0, keep_states=False,
-                 stream=None):
-        self.args = capi.BatchArgs(circuits, n_qubits, shots, seeds)
+                 stream=None, zmasks=None, irs=None):
+        self.args = capi.BatchArgs(circuits, n_qubits, shots, seeds, zmasks, irs)
         self.opts = capi.make_opts(k_max, tile_qubits)
         self.h = capi.sv_batch_create(self.args, self.opts, keep_states, stream)
 
@@ -24,6 +24,10 @@ class Batch:
         out = np.empty(int(self.args.shots[i]), dtype=np.uint64)
         capi.sv_batch_samples(self.h, i, out, False)
         return out
+
+    def expectation(self, i: int):
+        """(<Z_zmask>, norm) of circuit i."""
+        return capi.sv_batch_expectation(self.h, i)
 
     def amplitudes(self, i: int) -> np.ndarray:
         out = np.empty(1 << int(self.args.n_qubits[i]), dtype=np.complex64)

@@ -98,7 +98,8 @@ _SIGS = {
     "sv_launch_count": ([], ctypes.c_uint64),
     "sv_tc_selftest": ([_P, _P, _P], _i),
     "sv_expect_z_static": ([_P, _i, _u64, _P, _P], _i),
-    "sv_batch_create": ([ctypes.c_size_t, _P, _P, _P, _P, _P, _P, _i, _P, ctypes.POINTER(_P)], _i),
+    "sv_batch_create": ([ctypes.c_size_t, _P, _P, _P, _P, _P, _P, _P, _i, _P, ctypes.POINTER(_P)], _i),
+    "sv_batch_expectation": ([_P, ctypes.c_size_t, _P], _i),
     "sv_batch_launch": ([_P], _i),
     "sv_batch_synchronize": ([_P], _i),
     "sv_batch_samples": ([_P, ctypes.c_size_t, _P, _i], _i),
@@ -290,22 +291,29 @@ def sv_expect_z_static(dev_amplitudes, n_qubits: int, z_mask: int, dev_out, stre
 
 
 class BatchArgs:
-    """Marshalled arrays for the sv_batch_* calls (keeps the IR arrays alive)."""
+    """Marshalled arrays for the sv_batch_* calls (keeps the IR arrays alive).
 
-    def __init__(self, circuits, n_qubits, shots, seeds):
-        self.irs = [to_ir(c) for c in circuits]
-        self.ptrs = np.array([ir.ctypes.data for ir, _ in self.irs], dtype=np.uint64)
-        self.n_gates = np.array([len(c) for c in circuits], dtype=np.uint64)
+    Give either ``circuits`` (gate lists) or ``irs``: (sv_gate array, n_gates)
+    pairs already marshalled with to_ir."""
+
+    def __init__(self, circuits, n_qubits, shots, seeds, zmasks=None, irs=None):
+        if irs is None:
+            irs = [(to_ir(c)[0], len(c)) for c in circuits]
+        self.irs = irs
+        self.ptrs = np.array([ir.ctypes.data for ir, _ in irs], dtype=np.uint64)
+        self.n_gates = np.array([ng for _, ng in irs], dtype=np.uint64)
         self.n_qubits = np.array(n_qubits, dtype=np.int32)
         self.shots = np.array(shots, dtype=np.uint64)
         self.seeds = np.array([int(x) & (2**64 - 1) for x in seeds], dtype=np.uint64)
-        self.n = len(circuits)
+        self.zmasks = np.array([int(z) for z in zmasks], dtype=np.uint64) if zmasks is not None else None
+        self.n = len(irs)
 
 
 def sv_batch_create(args: BatchArgs, opts=None, keep_states=False, stream=None):
     h = _P()
     _check(_L.sv_batch_create(args.n, args.ptrs.ctypes.data, args.n_gates.ctypes.data,
                               args.n_qubits.ctypes.data, args.shots.ctypes.data, args.seeds.ctypes.data,
+                              args.zmasks.ctypes.data if args.zmasks is not None else None,
                               ctypes.byref(opts) if opts is not None else None, int(bool(keep_states)),
                               _stream_ptr(stream), ctypes.byref(h)))
     return h
@@ -321,6 +329,12 @@ def sv_batch_synchronize(h):
 
 def sv_batch_samples(h, circuit: int, out, on_device: bool = False):
     _check(_L.sv_batch_samples(h, int(circuit), _ptr(out), int(bool(on_device))))
+
+
+def sv_batch_expectation(h, circuit: int):
+    out = np.empty(2, dtype=np.float64)
+    _check(_L.sv_batch_expectation(h, int(circuit), out.ctypes.data))
+    return float(out[0]), float(out[1])
 
 
 def sv_batch_amplitudes(h, circuit: int, out):

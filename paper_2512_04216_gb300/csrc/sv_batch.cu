@@ -40,9 +40,10 @@ struct alignas(16) BatchCirc {
   uint64_t scratch_off;  // double offset of the chunk-prefix array (global-state circuits)
   uint64_t out_off;      // uint64 offset of the circuit's samples
   uint64_t seed;
+  uint64_t zmask;        // flags bit 1: <Z_zmask> and the norm go to ex[2 * slot]
   uint32_t n, n_passes, shots, flags;  // flags bit 0: copy the final state to the arena
 };
-static_assert(sizeof(BatchCirc) == 56 || sizeof(BatchCirc) == 64, "BatchCirc layout");
+static_assert(sizeof(BatchCirc) == 64, "BatchCirc layout");
 
 struct BatchLayout {
   size_t off_tile, off_seg, off_mat, off_tab, off_acc, off_chunk, off_tot, total;
@@ -135,6 +136,34 @@ __device__ void batch_measure(const float2 *amps, uint32_t n, uint64_t seed, uin
   __syncthreads();
 }
 
+// sum p and sum p (-1)^popcount(i & zmask) over a state, double, CTA-wide;
+// thread 0 writes {<Z>, norm} to ex.
+__device__ void batch_expect(const float2 *amps, uint32_t n, uint64_t zmask, double *ex, double *tot) {
+  const uint32_t N = 1u << n;
+  double p = 0.0, pz = 0.0;
+  for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
+    const double q = p_of(amps[i]);
+    p += q;
+    pz += (__popcll(uint64_t(i) & zmask) & 1) ? -q : q;
+  }
+  __syncthreads();
+  tot[threadIdx.x] = p;
+  __syncthreads();
+  double sp = 0.0;
+  if (threadIdx.x == 0)
+    for (uint32_t t = 0; t < blockDim.x; t++) sp += tot[t];
+  __syncthreads();
+  tot[threadIdx.x] = pz;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sz = 0.0;
+    for (uint32_t t = 0; t < blockDim.x; t++) sz += tot[t];
+    ex[0] = sp > 0.0 ? sz / sp : 0.0;
+    ex[1] = sp;
+  }
+  __syncthreads();
+}
+
 template <int KMAX>
 __device__ __forceinline__ void batch_ops(float2 *tile, float2 *mat, uint32_t *acc, float2 *tab,
                                           const uint8_t *plan, const PlanPass &P, uint64_t base) {
@@ -163,7 +192,8 @@ template <int KMAX>
 __global__ void __launch_bounds__(kBatchNT) k_batch(const uint8_t *__restrict__ plans,
                                                    const BatchCirc *__restrict__ circs, uint32_t n_circ,
                                                    float2 *__restrict__ arena, double *__restrict__ scratch,
-                                                   uint64_t *__restrict__ out, uint32_t *__restrict__ counter) {
+                                                   uint64_t *__restrict__ out, double *__restrict__ ex,
+                                                   uint32_t *__restrict__ counter) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_next;
   const BatchLayout L = batch_layout(KMAX);
@@ -190,7 +220,8 @@ __global__ void __launch_bounds__(kBatchNT) k_batch(const uint8_t *__restrict__ 
         const PlanPass P = reinterpret_cast<const PlanPass *>(plan)[p];
         batch_ops<KMAX>(tile, mat, acc, tab, plan, P, 0);
       }
-      batch_measure(tile, n, C.seed, C.shots, out + C.out_off, chunk_s, tot);
+      if (C.shots) batch_measure(tile, n, C.seed, C.shots, out + C.out_off, chunk_s, tot);
+      if (C.flags & 2u) batch_expect(tile, n, C.zmask, ex + 2 * ci, tot);
       if (C.flags & 1u) {
         for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) arena[C.state_off + i] = tile[i];
       }
@@ -217,7 +248,8 @@ __global__ void __launch_bounds__(kBatchNT) k_batch(const uint8_t *__restrict__ 
           __syncthreads();
         }
       }
-      batch_measure(st, n, C.seed, C.shots, out + C.out_off, scratch + C.scratch_off, tot);
+      if (C.shots) batch_measure(st, n, C.seed, C.shots, out + C.out_off, scratch + C.scratch_off, tot);
+      if (C.flags & 2u) batch_expect(st, n, C.zmask, ex + 2 * ci, tot);
     }
   }
 }
@@ -239,6 +271,7 @@ struct sv_batch {
   float2 *arena = nullptr;
   double *scratch = nullptr;
   uint64_t *out = nullptr;
+  double *ex = nullptr;
   uint32_t *counter = nullptr;
   size_t out_count = 0, arena_count = 0;
   cudaGraph_t graph = nullptr;
@@ -263,6 +296,7 @@ void free_batch(sv_batch *b) {
   cudaFree(b->arena);
   cudaFree(b->scratch);
   cudaFree(b->out);
+  cudaFree(b->ex);
   cudaFree(b->counter);
   cudaSetDevice(prev);
   delete b;
@@ -290,7 +324,8 @@ cudaError_t enqueue_batch(sv_batch *b, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(b->counter, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   k_batch<KMAX><<<b->grid, kBatchNT, batch_layout(KMAX).total, st>>>(b->plan_dev, b->circ_dev, uint32_t(b->n_circ),
-                                                                    b->arena, b->scratch, b->out, b->counter);
+                                                                    b->arena, b->scratch, b->out, b->ex,
+                                                                    b->counter);
   return cudaGetLastError();
 }
 
@@ -315,8 +350,8 @@ cudaError_t enqueue_any(sv_batch *b, cudaStream_t st) {
 extern "C" {
 
 int sv_batch_create(size_t n_circ, const sv_gate *const *irs, const size_t *n_gates, const int *n_qubits,
-                    const uint64_t *shots, const uint64_t *seeds, const sv_opts *opts, int keep_states,
-                    void *cuda_stream, sv_batch **out) {
+                    const uint64_t *shots, const uint64_t *seeds, const uint64_t *zmasks, const sv_opts *opts,
+                    int keep_states, void *cuda_stream, sv_batch **out) {
   if (!out) return set_last_error(SV_ERR_ARG, "out is null");
   *out = nullptr;
   if (n_circ == 0 || !irs || !n_gates || !n_qubits || !shots || !seeds)
@@ -386,6 +421,14 @@ int sv_batch_create(size_t n_circ, const sv_gate *const *irs, const size_t *n_ga
     c.shots = uint32_t(shots[i]);
     c.seed = seeds[i];
     c.flags = b->keep ? 1u : 0u;
+    if (zmasks && zmasks[i]) {
+      if (zmasks[i] >> n) {
+        free_batch(b);
+        return set_last_error(SV_ERR_ARG, "circuit %zu: zmask has bits beyond n_qubits", i);
+      }
+      c.zmask = zmasks[i];
+      c.flags |= 2u;
+    }
     c.out_off = outs;
     outs += shots[i];
     if (n > kBatchSmemQubits || b->keep) {
@@ -420,6 +463,8 @@ int sv_batch_create(size_t n_circ, const sv_gate *const *irs, const size_t *n_ga
   if (e == cudaSuccess) e = cudaMalloc(&b->arena, std::max<uint64_t>(arena, 2) * sizeof(float2));
   if (e == cudaSuccess) e = cudaMalloc(&b->scratch, std::max<uint64_t>(scratch, 2) * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&b->out, std::max<uint64_t>(outs, 2) * sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMalloc(&b->ex, 2 * n_circ * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(b->ex, 0, 2 * n_circ * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&b->counter, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemcpy(b->plan_dev, plans.data(), plans.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
@@ -476,6 +521,17 @@ int sv_batch_samples(sv_batch *b, size_t circuit, uint64_t *out, int on_device) 
   return SV_OK;
 }
 
+int sv_batch_expectation(sv_batch *b, size_t circuit, double *out2) {
+  if (!b || !out2) return set_last_error(SV_ERR_ARG, "null argument");
+  if (circuit >= b->n_circ) return set_last_error(SV_ERR_ARG, "circuit index out of range");
+  const size_t slot = b->slot[circuit];
+  if (!(b->circ[slot].flags & 2u)) return set_last_error(SV_ERR_ARG, "circuit %zu has no zmask", circuit);
+  cudaError_t e = cudaMemcpyAsync(out2, b->ex + 2 * slot, 2 * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return set_last_error(SV_ERR_CUDA, "sv_batch_expectation: %s", cudaGetErrorString(e));
+  return SV_OK;
+}
+
 int sv_batch_amplitudes(sv_batch *b, size_t circuit, void *out) {
   if (!b || !out) return set_last_error(SV_ERR_ARG, "null argument");
   if (circuit >= b->n_circ) return set_last_error(SV_ERR_ARG, "circuit index out of range");
@@ -518,7 +574,7 @@ int sv_batch_autotune(size_t n_circ, const sv_gate *const *irs, const size_t *n_
       o.k_max = k;
       o.tile_qubits = t;
       sv_batch *b = nullptr;
-      rc = sv_batch_create(n_circ, irs, n_gates, n_qubits, shots, seeds, &o, 0, nullptr, &b);
+      rc = sv_batch_create(n_circ, irs, n_gates, n_qubits, shots, seeds, nullptr, &o, 0, nullptr, &b);
       if (rc == SV_ERR_UNSUPPORTED) continue;  // a block wider than this k_max
       if (rc) break;
       rc = sv_batch_launch(b);  // warm-up
@@ -547,7 +603,7 @@ int sv_batch_run(const sv_gate *const *irs, const size_t *n_gates, const int *n_
                  const uint64_t *shots, const uint64_t *seeds, uint64_t *const *out, const sv_opts *opts) {
   if (!out) return set_last_error(SV_ERR_ARG, "out is null");
   sv_batch *b = nullptr;
-  int rc = sv_batch_create(n_circ, irs, n_gates, n_qubits, shots, seeds, opts, 0, nullptr, &b);
+  int rc = sv_batch_create(n_circ, irs, n_gates, n_qubits, shots, seeds, nullptr, opts, 0, nullptr, &b);
   if (rc) return rc;
   rc = sv_batch_launch(b);
   for (size_t i = 0; rc == SV_OK && i < n_circ; i++)
