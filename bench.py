@@ -327,6 +327,89 @@ def run_reference(args):
     }
 
 
+def run_batch_mode(args):
+    """Config: many independent random layered circuits (n ~ U{10..20},
+    depth ~ U{10..60}, 4096 shots each) in one persistent graph-captured launch,
+    autotuned on a 256-circuit sample, against the plain one-circuit-at-a-time
+    path timed on a sample and scaled to the batch."""
+    import torch
+    from paper_2512_04216_gb300 import Batch, StateVector, capi
+    count = args.batch_circuits
+    mix = W.batch_mix(count, 3)
+    circs = [W.random_layered(n, d, s) for n, d, s in mix]
+    ns = [m[0] for m in mix]
+    shots = [4096] * count
+    seeds = [m[2] for m in mix]
+    sample_idx = list(range(0, count, max(1, count // 256)))
+    sargs = capi.BatchArgs([circs[i] for i in sample_idx], [ns[i] for i in sample_idx],
+                           [shots[i] for i in sample_idx], [seeds[i] for i in sample_idx])
+    best, best_ms = capi.sv_batch_autotune(sargs, reps=1)
+    b = Batch(circs, ns, shots, seeds, k_max=best.k_max, tile_qubits=best.tile_qubits)
+    for _ in range(args.warmup):
+        b.launch()
+    b.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = capi.sv_launch_count()
+    ev0.record()
+    for _ in range(args.steps):
+        b.launch()
+    b.synchronize()
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    stats = b.stats()
+    b.close()
+    # plain path: each circuit alone (create, apply, sample, destroy), on a sample
+    psample = list(range(0, count, max(1, count // 64)))
+    t0 = time.perf_counter()
+    for i in psample:
+        s = StateVector(ns[i])
+        s.apply(circs[i])
+        s.sample(shots[i], seeds[i])
+        s.close()
+    plain_s = (time.perf_counter() - t0) * count / len(psample)
+    return {
+        "metric": "batched circuits/s", "value": count / (ms * 1e-3), "unit": "circuits/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": f"{count} random layered circuits, n~U{{10..20}}, depth~U{{10..60}}, 4096 shots each, "
+                               "one persistent launch under a CUDA graph",
+                   "autotuned": {"k_max": best.k_max, "tile_qubits": best.tile_qubits, "sample_ms": best_ms},
+                   "arena_passes": stats["passes"]},
+        "plain_path": {"circuits_per_s": count / plain_s, "sample": f"{len(psample)} circuits, scaled"},
+        "speedup_vs_plain": (count / (ms * 1e-3)) / (count / plain_s),
+        "gpu_launches": int(capi.sv_launch_count() - launches0),
+    }
+
+
+def run_serve_mode(args):
+    """Config: Poisson stream of random layered circuits, n geometric-skewed on
+    8..30 (mean ~16), depth ~ U{10..100}, 1000 shots or a Z-string mask; served
+    by the continuous-batching loop and by the plain path."""
+    from paper_2512_04216_gb300 import serve
+    count = args.requests
+    specs0 = W.serving_requests(count, 4, 1.0)
+    reqs0 = serve.make_requests(specs0, W.random_layered)
+    for r in reqs0:
+        r.t = 0.0
+    plain_cap = serve.summarize(serve.run_plain(reqs0))["circuits_per_s"]
+    out = {"plain_capacity_circuits_per_s": plain_cap, "points": []}
+    for f in [float(x) for x in args.rate_factors.split(",")]:
+        rate = f * plain_cap
+        specs = W.serving_requests(count, 4, rate)
+        reqs = serve.make_requests(specs, W.random_layered)
+        srv = serve.summarize(serve.Server().run(reqs))
+        pl = serve.summarize(serve.run_plain(reqs))
+        out["points"].append({"rate_factor": f, "rate_hz": rate, "served": srv, "plain": pl,
+                              "circuits_per_s_ratio": srv["circuits_per_s"] / pl["circuits_per_s"]})
+    best = max(p["circuits_per_s_ratio"] for p in out["points"])
+    return {"metric": "mixed-stream circuits/s & p99 vs plain path", "value": best,
+            "unit": "x plain circuits/s", "n_gpus": 1, "higher_is_better": True, "vs_baseline": None,
+            "dtype": "c64", "data": "synthetic",
+            "config": {"workload": f"{count} Poisson requests per point, n geometric on 8..30 (mean ~16), "
+                                   "depth U{10..100}, 1000 shots or <Z>"}, "serving": out}
+
+
 def main():
     global N_QUBITS, DEPTH
     ap = argparse.ArgumentParser()
@@ -343,6 +426,11 @@ def main():
     ap.add_argument("--kernel-variant", type=int, default=0)
     ap.add_argument("--precision", type=int, default=OPTS["precision"],
                     help="0: FP32 CUDA cores; 1: 3xTF32 tensor-core stage products")
+    ap.add_argument("--workload", choices=["statevector", "batch", "serve"], default="statevector",
+                    help="statevector: the bench line; batch / serve: the batched and serving patterns")
+    ap.add_argument("--batch-circuits", type=int, default=4096)
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate-factors", default="0.5,1,2,4")
     args = ap.parse_args()
     N_QUBITS, DEPTH = args.n_qubits, args.depth
     OPTS.update(tile_qubits=args.tile_qubits, k_max=args.k_max, kernel_variant=args.kernel_variant,
@@ -354,6 +442,11 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
+        return
+    if args.workload != "statevector":
+        if rank == 0:
+            fn = run_batch_mode if args.workload == "batch" else run_serve_mode
+            print(json.dumps(fn(args)), flush=True)
         return
 
     if world > 1:
