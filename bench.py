@@ -44,6 +44,10 @@ SHOTS = 100_000
 ZMASK = 0b1011  # <Z_0 Z_1 Z_3>
 OPTS = dict(k_max=2, tile_qubits=12, low_qubits=5, precision=0, kernel_variant=0)
 METRIC = "state-vector apply HBM GB/s vs peak"
+# FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
 def workload_name():
     return (f"random layered n={N_QUBITS} depth={DEPTH} + QFT-{N_QUBITS} on a seeded basis state; "
             f"FP64 norm, CDF and {SHOTS} shots; <Z> expectation")
@@ -116,6 +120,23 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The slowest rank's figure (every rank calls this; a no-op without a process group)."""
+    import torch
+    import torch.distributed as td
+    if not (td.is_available() and td.is_initialized()) or td.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(bytes_per_step: float, steps: int, world: int, seconds: float) -> float:
+    """Whole-job GB/s: every replica moves bytes_per_step per step; the job takes
+    the slowest replica's time."""
+    return world * bytes_per_step * steps / seconds / 1e9
+
+
 def step_bytes(plan_rand, plan_qft, n):
     amps = float(1 << n)
     return plan_rand["bytes"] + plan_qft["bytes"] + 5 * 8.0 * amps  # 2 resets + cdf + norm + expect
@@ -137,6 +158,7 @@ def run_ours(args, rank, world, local_rank):
     plan_r = capi.sv_plan_stats(n, circ, opts)
     plan_q = capi.sv_plan_stats(n, qft, opts)
     bytes_step = step_bytes(plan_r, plan_q, n)
+    flops_pass_step = float(plan_r["flops"] + plan_q["flops"])
 
     stream = torch.cuda.Stream(dev)
     amps = torch.empty(1 << n, dtype=torch.complex64, device=dev)
@@ -200,11 +222,7 @@ def run_ours(args, rank, world, local_rank):
     launches = capi.sv_launch_count() - launches0
     prof = capi.sv_profile_read(h)
     capi.sv_profile_enable(h, False)
-    dev_ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([dev_ms], device=dev)
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        dev_ms = float(t.item())
+    dev_ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
     clocks = clk.summary()
 
     # ---- end-to-end steps through the public API, host buffers ----
@@ -215,11 +233,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.steps):
         step_e2e()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
 
     # parity spot check on the final state (QFT of |x>), outside the timed regions
     idx = np.array([0, 1, 12345, (1 << n) - 1], dtype=np.int64)
@@ -230,9 +244,29 @@ def run_ours(args, rank, world, local_rank):
 
     peak, peak_kind = peaks()
     pk = prof.get("pass_tc") or prof.get("pass") or {"launches": 0, "ms": float("nan"), "bytes": 0.0}
-    achieved = pk["bytes"] / (pk["ms"] * 1e-3) / 1e9 if pk["launches"] else float("nan")
-    value = world * bytes_step * args.steps / (dev_ms * 1e-3) / 1e9
-    e2e_val = world * bytes_step * args.steps / e2e_s / 1e9
+    pass_s = pk["ms"] * 1e-3
+    achieved = pk["bytes"] / pass_s / 1e9 if pk["launches"] else float("nan")
+    achieved_tf = flops_pass_step * args.steps / pass_s / 1e12 if pk["launches"] else float("nan")
+    # the pass kernels' lower bound is the larger of HBM time and FP32 FMA time
+    alu_bound = flops_pass_step / (FP32_PEAK_TFLOPS * 1e12) > (pk["bytes"] / max(args.steps, 1)) / (peak * 1e9)
+    if OPTS["precision"]:
+        alu_bound = False  # tensor-core stage products: reported against HBM
+    if alu_bound:
+        roof = {"bound": "alu", "achieved": round(achieved_tf, 2), "peak": round(FP32_PEAK_TFLOPS, 1),
+                "unit": "TFLOP/s", "frac": round(achieved_tf / FP32_PEAK_TFLOPS, 4),
+                "peak_source": "derived (152 SMs x 128 FP32 FMA/clk x 2 x 2.07 GHz)"}
+    else:
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_kind}
+    roof.update({"kernel": "pass kernel (one HBM pass over the state)",
+                 "traffic": PASS_TRAFFIC_BYTES,
+                 "algorithmic_bytes_per_launch": 16 * (1 << n),
+                 "algorithmic_flops_per_step": flops_pass_step,
+                 "hbm_GBps": round(achieved, 1), "hbm_frac": round(achieved / peak, 4),
+                 "fp32_TFLOPs": round(achieved_tf, 2), "fp32_frac": round(achieved_tf / FP32_PEAK_TFLOPS, 4),
+                 "avg_launch_ms": round(pk["ms"] / max(pk["launches"], 1), 4)})
+    value = job_value(bytes_step, args.steps, world, dev_ms * 1e-3)
+    e2e_val = job_value(bytes_step, args.steps, world, e2e_s)
     h2d = plan_r["upload_bytes"] + plan_q["upload_bytes"] + SHOTS * 8
     d2h = SHOTS * 8 + 8 + 3 * 8
     line = {
@@ -246,14 +280,11 @@ def run_ours(args, rank, world, local_rank):
                    "passes_per_step": plan_r["n_passes"] + plan_q["n_passes"],
                    "l2": f"inputs larger than L2 ({(8 << n) / 2**30:.3g} GiB state vs 129 MB L2)",
                    "parallelism": f"replicas{world}"},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "peak_source": peak_kind,
-                     "kernel": "k_pass (one HBM pass)",
-                     "traffic": PASS_TRAFFIC_BYTES,
-                     "algorithmic_bytes_per_launch": 16 * (1 << n),
-                     "avg_launch_ms": round(pk["ms"] / max(pk["launches"], 1), 4)},
+        "roofline": roof,
         "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
-                        "GB/s": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 and v["bytes"] else None}
+                        "GB/s": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 and v["bytes"] else None,
+                        "hbm_frac": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9 / peak, 4)
+                        if v["ms"] > 0 and v["bytes"] else None}
                     for k, v in prof.items()},
         "e2e": {"value": round(e2e_val, 1), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms_per_step": round(e2e_s * 1e3 / args.steps, 3)},
@@ -411,7 +442,7 @@ def run_serve_mode(args):
 
 
 def main():
-    global N_QUBITS, DEPTH
+    global N_QUBITS, DEPTH, SHOTS
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -426,13 +457,17 @@ def main():
     ap.add_argument("--kernel-variant", type=int, default=0)
     ap.add_argument("--precision", type=int, default=OPTS["precision"],
                     help="0: FP32 CUDA cores; 1: 3xTF32 tensor-core stage products")
-    ap.add_argument("--workload", choices=["statevector", "batch", "serve"], default="statevector",
-                    help="statevector: the bench line; batch / serve: the batched and serving patterns")
+    ap.add_argument("--workload", choices=["statevector", "large", "batch", "serve"], default="statevector",
+                    help="statevector: the bench line; large: the 34-qubit (128 GiB) single state, "
+                         "depth 30, 1e6 shots; batch / serve: the batched and serving patterns")
     ap.add_argument("--batch-circuits", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate-factors", default="0.5,1,2,4")
     args = ap.parse_args()
     N_QUBITS, DEPTH = args.n_qubits, args.depth
+    if args.workload == "large":
+        N_QUBITS, DEPTH, SHOTS = 34, 30, 1_000_000
+        args.no_cpu_baseline = True  # the complex128 oracle would need 256 GiB of host memory
     OPTS.update(tile_qubits=args.tile_qubits, k_max=args.k_max, kernel_variant=args.kernel_variant,
                 precision=args.precision)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -443,7 +478,7 @@ def main():
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
         return
-    if args.workload != "statevector":
+    if args.workload in ("batch", "serve"):
         if rank == 0:
             fn = run_batch_mode if args.workload == "batch" else run_serve_mode
             print(json.dumps(fn(args)), flush=True)

@@ -21,6 +21,15 @@ extern "C" {
  */
 int sv_tc_selftest(const float *a, const double *b, float *d);
 
+/*
+ * Exercises the device-side timeout path without faulting or hanging the GPU:
+ * one CTA waits on an mbarrier that nothing arrives on, with the same
+ * %globaltimer bound the tensor-core kernels use (limit_ms in [1, 10000]).
+ * Returns SV_ERR_TIMEOUT (the expected outcome), SV_ERR_ARG or SV_ERR_CUDA.
+ * Synchronous, current device.
+ */
+int sv_diag_bounded_wait(int limit_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -97,6 +97,7 @@ _SIGS = {
     "sv_version": ([], ctypes.c_char_p),
     "sv_launch_count": ([], ctypes.c_uint64),
     "sv_tc_selftest": ([_P, _P, _P], _i),
+    "sv_diag_bounded_wait": ([_i], _i),
     "sv_expect_z_static": ([_P, _i, _u64, _P, _P], _i),
     "sv_batch_create": ([ctypes.c_size_t, _P, _P, _P, _P, _P, _P, _P, _i, _P, ctypes.POINTER(_P)], _i),
     "sv_batch_expectation": ([_P, ctypes.c_size_t, _P], _i),
@@ -281,6 +282,11 @@ def sv_tc_selftest(a, b):
     d = np.empty((128, 32), dtype=np.float32)
     _check(_L.sv_tc_selftest(a.ctypes.data, b.ctypes.data, d.ctypes.data))
     return d
+
+
+def sv_diag_bounded_wait(limit_ms: int) -> int:
+    """Status of a bounded wait on nothing (include/sv_diag.h); SV_ERR_TIMEOUT expected."""
+    return int(_L.sv_diag_bounded_wait(int(limit_ms)))
 
 
 def sv_expect_z_static(dev_amplitudes, n_qubits: int, z_mask: int, dev_out, stream=None):

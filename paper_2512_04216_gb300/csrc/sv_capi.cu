@@ -554,6 +554,15 @@ int sv_tc_selftest(const float *a, const double *b, float *d) {
   return SV_OK;
 }
 
+int sv_diag_bounded_wait(int limit_ms) {
+  if (limit_ms < 1 || limit_ms > 10000) return fail(SV_ERR_ARG, "limit_ms must be in [1, 10000]");
+  int status = -1;
+  cudaError_t e = wait_nothing(uint32_t(limit_ms), &status);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "bounded-wait check");
+  if (status == 1) return fail(SV_ERR_TIMEOUT, "bounded wait gave up after %d ms (nothing arrived)", limit_ms);
+  return fail(SV_ERR_CUDA, "bounded-wait check: unexpected status %d", status);
+}
+
 int sv_profile_enable(sv_state *s, int on) {
   if (!s) return fail(SV_ERR_ARG, "null state");
   s->prof = on != 0;

@@ -97,6 +97,34 @@ __global__ void __launch_bounds__(128) k_tc_selftest(const float *__restrict__ A
   if (warp == 0) tmem_dealloc(tbase, 128);
 }
 
+// ---- bounded-wait check: an mbarrier that nothing arrives on -------------------------
+
+__global__ void k_wait_nothing(uint32_t limit_ns, int *status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  bool done = mbar_try_wait(&bar, 0);
+  const uint64_t t0 = global_ns();
+  while (!done && global_ns() - t0 < limit_ns) done = mbar_try_wait(&bar, 0);
+  __syncthreads();
+  if (threadIdx.x == 0) *status = done ? 0 : 1;
+}
+
+cudaError_t wait_nothing(uint32_t limit_ms, int *status_host) {
+  int *d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(d, 0xff, sizeof(int));
+  if (e == cudaSuccess) {
+    k_wait_nothing<<<1, 32>>>(limit_ms * 1000000u, d);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(status_host, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e;
+}
+
 // ---- host helpers ------------------------------------------------------------------
 
 static inline float tf32_rn(float f) {

@@ -17,5 +17,7 @@ size_t tc_b_offset(int n, int k);
 void tc_b_image(const double *B, uint8_t *img);
 // One 128x32 (A, host) times 32x32 (B[n][k], host) product on the tensor cores.
 cudaError_t tc_selftest(const float *A_host, const double *B_host, float *D_host, int *status_host);
+// Waits (bounded by limit_ms) on an mbarrier that nothing arrives on; *status_host = 1 on timeout.
+cudaError_t wait_nothing(uint32_t limit_ms, int *status_host);
 
 }  // namespace svgb
