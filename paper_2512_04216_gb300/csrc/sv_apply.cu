@@ -160,45 +160,64 @@ __device__ __forceinline__ void reg_dense_dispatch(float2 (&v)[1 << R], uint32_t
 }
 #undef SV_CASE
 
-// Phase tables for the current tile (see apply_phase); then every register
-// amplitude is multiplied by the phase of its local index la[j] | LB.
+// exp(2*pi*i * sum of the turns of terms [i0, i1) that apply to this thread)
+__device__ __forceinline__ float2 rphase_exp(const RegPhaseTerm *__restrict__ t, uint32_t i0, uint32_t i1,
+                                             uint64_t base, uint32_t LB) {
+  uint32_t a = 0;
+  for (uint32_t i = i0; i < i1; i++) {
+    const RegPhaseTerm x = t[i];
+    if ((base & x.outer_mask) == x.outer_mask && (LB & x.tmask) == x.tmask) a += x.turn;
+  }
+  if (a == 0) return make_float2(1.f, 0.f);
+  float sn, cs;
+  sincospif(static_cast<float>(static_cast<int32_t>(a)) * 4.656612873077393e-10f, &sn, &cs);
+  return make_float2(cs, sn);
+}
+
+template <int J>
+struct LowBit {
+  static constexpr int v = (J & 1) ? 0 : 1 + LowBit<(J >> 1)>::v;
+};
+template <>
+struct LowBit<0> {
+  static constexpr int v = 0;
+};
+
+// f[j] = f[j without its lowest bit] * e[1 + lowest bit of j], j = J .. 2^R - 1
+template <int J, int R>
+__device__ __forceinline__ void phase_tree(float2 (&f)[1 << R], const float2 (&e)[R + 1]) {
+  if constexpr (J < (1 << R)) {
+    f[J] = cmul(f[J & (J - 1)], e[1 + LowBit<J>::v]);
+    phase_tree<J + 1, R>(f, e);
+  }
+}
+
+// OP_RPHASE on the 2^R register amplitudes of one thread (record layout in
+// RegPhaseHdr).  The thread sums the turns of the terms that apply to it into
+// P and alpha_i (exact modulo 2^32), takes the 1 + R exponentials, and forms
+// the 2^R amplitude phases as products along a binary tree (at most R complex
+// products deep), times D[j].
 template <int R>
-__device__ __forceinline__ void reg_phase(float2 (&v)[1 << R], const PhaseTerm *__restrict__ terms,
-                                          uint32_t count, uint64_t base, uint32_t T,
-                                          const uint16_t *__restrict__ la, uint32_t LB, uint32_t *acc,
-                                          float2 *tab) {
-  __syncthreads();  // a previous phase op may still read the tables
-  if (threadIdx.x <= T) acc[threadIdx.x] = 0u;
-  __syncthreads();
-  for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) {
-    const PhaseTerm pt = terms[i];
-    if ((base & pt.outer_mask) == pt.outer_mask) atomicAdd(&acc[pt.la + 1], pt.turn);
+__device__ __forceinline__ void reg_rphase(float2 (&v)[1 << R], const uint8_t *__restrict__ rec, uint64_t base,
+                                           uint32_t LB) {
+  const RegPhaseHdr *h = reinterpret_cast<const RegPhaseHdr *>(rec);
+  const RegPhaseTerm *t = reinterpret_cast<const RegPhaseTerm *>(rec + sizeof(RegPhaseHdr));
+  float2 e[R + 1];
+#pragma unroll
+  for (int k = 0; k <= R; k++) {
+    const uint32_t i0 = k ? h->end[k - 1] : 0u, i1 = h->end[k];
+    e[k] = rphase_exp(t, i0, i1, base, LB);
   }
-  __syncthreads();
-  const uint32_t h = T >> 1;
-  const uint32_t nlo = 1u << h, nhi = 1u << (T - h);
-  for (uint32_t e = threadIdx.x; e < nlo + nhi; e += blockDim.x) {
-    uint32_t turn;
-    if (e < nlo) {
-      turn = acc[0];
-      for (uint32_t j = 0; j < h; j++)
-        if ((e >> j) & 1u) turn += acc[1 + j];
-    } else {
-      const uint32_t e2 = e - nlo;
-      turn = 0u;
-      for (uint32_t j = 0; j < T - h; j++)
-        if ((e2 >> j) & 1u) turn += acc[1 + h + j];
-    }
-    float sn, cs;
-    sincospif(static_cast<float>(static_cast<int32_t>(turn)) * 4.656612873077393e-10f, &sn, &cs);
-    tab[e] = make_float2(cs, sn);
-  }
-  __syncthreads();
-  const uint32_t lmask = nlo - 1u;
+  const bool has_d = h->has_d != 0;
+  // f[j] = e[0] * prod_{bit i of j} e[1 + i], built from f[j without its lowest bit]
+  float2 f[1 << R];
+  f[0] = e[0];
+  phase_tree<1, R>(f, e);
 #pragma unroll
   for (int j = 0; j < (1 << R); j++) {
-    const uint32_t l = uint32_t(la[j]) | LB;
-    v[j] = cmul(v[j], cmul(tab[l & lmask], tab[nlo + (l >> h)]));
+    float2 p = f[j];
+    if (has_d) p = cmul(p, h->d[j]);
+    v[j] = cmul(v[j], p);
   }
 }
 
@@ -326,8 +345,7 @@ __global__ void __launch_bounds__(NTMAX, NTMAX <= 256 ? 3 : 1) k_pass_reg(float2
         if (op.type == OP_DENSE) {
           reg_dense_dispatch<R>(v, op.rmask, reinterpret_cast<const float2 *>(data + (op.data_off - data_off)));
         } else {
-          reg_phase<R>(v, reinterpret_cast<const PhaseTerm *>(data + (op.data_off - data_off)), op.count,
-                       base, T, st.la, LB, acc, tab);
+          reg_rphase<R>(v, data + (op.data_off - data_off), base, LB);
         }
       }
     }
@@ -538,8 +556,7 @@ __global__ void __launch_bounds__(NTMAX, NTMAX <= 128 ? 4 : (NTMAX <= 256 ? 2 : 
       const uint32_t oe = st.op_end;
       for (uint32_t o = st.op_begin; o < oe; o++) {
         const OpRec op = ops[o];
-        reg_phase<4>(v, reinterpret_cast<const PhaseTerm *>(data + (op.data_off - data_off)), op.count, base, T,
-                     st.la, LB, acc, tab);
+        reg_rphase<4>(v, data + (op.data_off - data_off), base, LB);
       }
     }
     if (aborted) break;

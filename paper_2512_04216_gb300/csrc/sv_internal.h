@@ -11,7 +11,10 @@
 //             matrix bit m <-> local bit lb[m];
 //   OP_PHASE  a product of diagonal gates whose terms each touch at most one
 //             tile qubit (the others are fixed per CTA); phases are stored as
-//             32-bit fractions of a turn so sums wrap exactly modulo 2*pi.
+//             32-bit fractions of a turn so sums wrap exactly modulo 2*pi;
+//   OP_RPHASE the register-stage form of a diagonal product (KIND_REG and
+//             KIND_TC passes): terms may touch two tile qubits, and are
+//             pre-classified by the stage's register bits (RegPhaseHdr).
 #pragma once
 
 #include <atomic>
@@ -24,7 +27,7 @@ namespace svgb {
 extern std::atomic<uint64_t> g_launches;
 inline void count_launch(uint64_t k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
-enum : uint8_t { OP_DENSE = 1, OP_PHASE = 2 };
+enum : uint8_t { OP_DENSE = 1, OP_PHASE = 2, OP_RPHASE = 3 };
 
 constexpr int kMaxTile = 13;   // largest T (64 KiB of complex64 in shared memory)
 constexpr int kMaxK = 5;       // largest fused block
@@ -101,6 +104,28 @@ struct alignas(16) PhaseTerm {
   uint32_t turn;        // phase as a fraction of 2*pi, scaled by 2^32
 };
 
+// OP_RPHASE record, relative to the stage holding it (register bits rb[0..R-1],
+// thread-local bits the rest).  The phase of register amplitude j of a thread
+// whose thread-local index bits are LB is
+//     2*pi/2^32 * ( P + sum_{i: bit i of j} alpha_i ) + arg D[j]
+// where P sums the class-0 terms and alpha_i the class-(1+i) terms that apply
+// (outer qubits outer_mask all 1 in this tile, thread-local bits tmask all 1 in
+// LB), and D[j] collects the terms that depend on register bits only.  Terms
+// are stored by class: class c occupies [end[c-1], end[c]).
+struct alignas(16) RegPhaseHdr {
+  uint32_t end[5];      // cumulative term counts of classes 0..4
+  uint32_t has_d;       // D differs from the identity
+  uint32_t pad_[2];
+  float2 d[16];         // register-only diagonal
+};
+struct alignas(16) RegPhaseTerm {
+  uint64_t outer_mask;  // outer qubits that must all be 1
+  uint32_t tmask;       // thread-local bits (as a tile-local index mask) that must all be 1
+  uint32_t turn;        // fraction of 2*pi, scaled by 2^32
+};
+
+static_assert(sizeof(RegPhaseHdr) == 160, "RegPhaseHdr layout");
+static_assert(sizeof(RegPhaseTerm) == 16, "RegPhaseTerm layout");
 static_assert(sizeof(PlanPass) == 112, "PlanPass layout");
 static_assert(sizeof(StageRec) == 160, "StageRec layout");
 static_assert(sizeof(OpRec) == 16, "OpRec layout");

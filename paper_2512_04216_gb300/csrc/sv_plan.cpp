@@ -17,7 +17,11 @@
 //     blocks it touches when the union fits, else those blocks are emitted and
 //     the gate opens a new one).  Block matrices are built in complex128 and
 //     stored as complex64.  Diagonal gates with at most one tile qubit become
-//     phase terms instead.
+//     phase terms instead; in passes that run on register stages, so do
+//     diagonal gates on two tile qubits (a controlled phase between two tile
+//     qubits costs one term of a phase op instead of a 4x4 block), unless an
+//     open block already holds their qubits or can take them while no phase op
+//     is being collected.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -242,6 +246,7 @@ static uint32_t to_turn(double phi) {
 struct HostTerm {
   uint64_t outer;  // outer qubits required to be 1
   int la;          // local bit required to be 1 (-1 none)
+  int lb;          // second local bit required to be 1 (-1 none; la < lb)
   uint32_t turn;
 };
 
@@ -264,24 +269,28 @@ static void diag_terms(const GateM &g, const int *lpos, std::vector<HostTerm> &o
       if ((T & S) == T) a += ((popc(uint64_t(S ^ T)) & 1) ? -1.0 : 1.0) * ph[T];
     uint32_t turn = to_turn(a);
     if (turn == 0) continue;
-    HostTerm t{0, -1, turn};
+    HostTerm t{0, -1, -1, turn};
     for (int x = 0; x < g.k; x++)
       if (S >> x & 1) {
-        int q = g.q[x];
-        if (lpos[q] >= 0) t.la = lpos[q];
-        else t.outer |= uint64_t(1) << q;
+        const int q = g.q[x];
+        if (lpos[q] < 0) t.outer |= uint64_t(1) << q;
+        else if (t.la < 0) t.la = lpos[q];
+        else t.lb = lpos[q];
       }
+    if (t.lb >= 0 && t.lb < t.la) std::swap(t.la, t.lb);
     out.push_back(t);
   }
 }
 
 static void merge_terms(std::vector<HostTerm> &terms) {
   std::sort(terms.begin(), terms.end(), [](const HostTerm &a, const HostTerm &b) {
-    return a.la != b.la ? a.la < b.la : a.outer < b.outer;
+    if (a.la != b.la) return a.la < b.la;
+    if (a.lb != b.lb) return a.lb < b.lb;
+    return a.outer < b.outer;
   });
   std::vector<HostTerm> out;
   for (auto &t : terms) {
-    if (!out.empty() && out.back().la == t.la && out.back().outer == t.outer)
+    if (!out.empty() && out.back().la == t.la && out.back().lb == t.lb && out.back().outer == t.outer)
       out.back().turn += t.turn;
     else
       out.push_back(t);
@@ -296,7 +305,7 @@ static void merge_terms(std::vector<HostTerm> &terms) {
 // ---------------------------------------------------------------------------
 
 static void fuse_pass(const std::vector<GateM> &gates, const std::vector<uint32_t> &acc,
-                      uint64_t Q, const int *lpos, int kmax, std::vector<HostOp> &ops) {
+                      uint64_t Q, const int *lpos, int kmax, bool pairs, std::vector<HostOp> &ops) {
   std::vector<Block> open;
   std::vector<HostTerm> pending;
   uint64_t pending_local = 0;
@@ -338,15 +347,19 @@ static void fuse_pass(const std::vector<GateM> &gates, const std::vector<uint32_
     const uint64_t local = g.mask & Q;
     const bool outer = (g.mask & ~Q) != 0;
     bool to_phase = false;
-    if (g.diag && popc(local) <= 1) {
-      if (outer) {
-        to_phase = true;
-      } else {
-        // a local one-qubit diagonal gate: absorb it into an open block that has
-        // room, else keep it with the phase terms
-        to_phase = true;
+    if (g.diag && popc(local) <= (pairs ? 2 : 1)) {
+      to_phase = true;
+      if (!outer) {
+        // a local diagonal gate: absorb it into an open block that holds its
+        // qubits; with no phase op being collected, also into open blocks that
+        // can take it within k_max (a new phase op costs more than a wider block)
+        uint64_t U = local;
         for (auto &b : open)
-          if ((b.mask & local) && popc(b.mask | g.mask) <= kmax) to_phase = false;
+          if (b.mask & local) U |= b.mask;
+        bool inside = false;
+        for (auto &b : open)
+          if ((b.mask & local) == local) inside = true;
+        if (inside || (pending.empty() && (U & ~local) && popc(U) <= kmax)) to_phase = false;
       }
     }
     if (to_phase) {
@@ -397,6 +410,55 @@ static void put_bytes(std::vector<uint8_t> &buf, const void *p, size_t n) {
 }
 static void align16(std::vector<uint8_t> &buf) {
   while (buf.size() % 16) buf.push_back(0);
+}
+
+// Register stages hold 16 amplitudes per thread (R = 4 register bits); the
+// persistent kernels take 9 <= T <= 13 with at least 4 non-low tile bits.
+static bool T_reg_ok(int T, int c) { return T - 4 >= 5 && T - 4 <= 9 && T - c >= 4; }
+
+// Appends the OP_RPHASE record of a phase op placed in a register stage whose
+// register bits are R (register index i <-> i-th lowest bit of R); returns the
+// number of stored terms.  Terms on register bits only fold into D.
+static uint32_t put_rphase(const std::vector<HostTerm> &terms, uint32_t R, std::vector<uint8_t> &buf) {
+  RegPhaseHdr h{};
+  uint32_t dturn[16] = {0};
+  std::vector<RegPhaseTerm> cls[5];
+  for (const HostTerm &t : terms) {
+    uint32_t tmask = 0, jm = 0;
+    int nreg = 0, reg0 = -1;
+    for (int b : {t.la, t.lb}) {
+      if (b < 0) continue;
+      if ((R >> b) & 1u) {
+        const int i = popc(uint64_t(R & ((1u << b) - 1u)));
+        jm |= 1u << i;
+        if (reg0 < 0) reg0 = i;
+        nreg++;
+      } else {
+        tmask |= 1u << b;
+      }
+    }
+    if (tmask == 0 && t.outer == 0) {
+      for (int j = 0; j < 16; j++)
+        if ((uint32_t(j) & jm) == jm) dturn[j] += t.turn;
+    } else {
+      // a term has at most two qubits, so here it has at most one register bit
+      cls[nreg ? 1 + reg0 : 0].push_back(RegPhaseTerm{t.outer, tmask, t.turn});
+    }
+  }
+  uint32_t n = 0;
+  for (int k = 0; k < 5; k++) {
+    n += uint32_t(cls[k].size());
+    h.end[k] = n;
+  }
+  for (int j = 0; j < 16; j++) {
+    if (dturn[j]) h.has_d = 1;
+    const double a = 2.0 * M_PI * double(dturn[j]) / 4294967296.0;
+    h.d[j] = make_float2(float(std::cos(a)), float(std::sin(a)));
+  }
+  put_bytes(buf, &h, sizeof(h));
+  for (int k = 0; k < 5; k++)
+    if (!cls[k].empty()) put_bytes(buf, cls[k].data(), cls[k].size() * sizeof(RegPhaseTerm));
+  return n;
 }
 
 // ---------------------------------------------------------------------------
@@ -545,7 +607,7 @@ static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint3
     for (int o : st.ops) {
       if (ops[o].type == OP_PHASE) {
         nphase++;
-        terms_bytes += ops[o].terms.size() * sizeof(PhaseTerm);
+        terms_bytes += ops[o].terms.size() * sizeof(RegPhaseTerm) + sizeof(RegPhaseHdr);
       } else {
         mma = true;
       }
@@ -576,17 +638,10 @@ static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint3
       const HostOp &op = ops[o];
       if (op.type == OP_PHASE) {
         OpRec r{};
-        r.type = OP_PHASE;
+        r.type = OP_RPHASE;
         align16(buf);
         r.data_off = uint32_t(buf.size());
-        r.count = uint32_t(op.terms.size());
-        for (auto &t : op.terms) {
-          PhaseTerm pt{};
-          pt.outer_mask = t.outer;
-          pt.la = t.la;
-          pt.turn = t.turn;
-          put_bytes(buf, &pt, sizeof(pt));
-        }
+        r.count = put_rphase(op.terms, st.R, buf);
         nterms += r.count;
         info.n_phase++;
         recs.push_back(r);
@@ -695,7 +750,9 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
   struct PassH {
     uint64_t Q;
     std::vector<HostOp> ops;
+    std::vector<uint32_t> acc;  // accepted gates (program order)
     int lq[32];
+    bool pairs;                 // fused with two-local-qubit phase terms
   };
   std::vector<PassH> passes;
 
@@ -737,7 +794,12 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
         ph.lq[j] = q;
         j++;
       }
-    fuse_pass(gates, acc, Q, lpos, kmax, ph.ops);
+    // two-local-qubit phase terms only where the pass can run on register stages
+    int wmax = 1;
+    for (uint32_t gi : acc) wmax = std::max(wmax, gates[gi].k);
+    ph.pairs = !o_smem && kmax <= 4 && wmax <= 4 && T_reg_ok(popc(Q), c);
+    fuse_pass(gates, acc, Q, lpos, kmax, ph.pairs, ph.ops);
+    ph.acc = std::move(acc);
     passes.push_back(std::move(ph));
     remaining.swap(rest);
   }
@@ -764,19 +826,27 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
     for (int x = 0; x < int(hp.T); x++) lpos[ph.lq[x]] = x;
 
     // local-bit masks of the ops
-    const size_t nops = ph.ops.size();
-    std::vector<uint32_t> omask(nops, 0);
+    size_t nops = 0;
+    std::vector<uint32_t> omask;
     uint32_t kmx = 0;
-    for (size_t i = 0; i < nops; i++) {
-      const HostOp &op = ph.ops[i];
-      if (op.type == OP_DENSE) {
-        for (int q : op.blk.qs) omask[i] |= 1u << lpos[q];
-        kmx = std::max<uint32_t>(kmx, uint32_t(op.blk.k()));
-      } else {
-        for (auto &t : op.terms)
-          if (t.la >= 0) omask[i] |= 1u << t.la;
+    auto op_masks = [&]() {
+      nops = ph.ops.size();
+      omask.assign(nops, 0);
+      kmx = 0;
+      for (size_t i = 0; i < nops; i++) {
+        const HostOp &op = ph.ops[i];
+        if (op.type == OP_DENSE) {
+          for (int q : op.blk.qs) omask[i] |= 1u << lpos[q];
+          kmx = std::max<uint32_t>(kmx, uint32_t(op.blk.k()));
+        } else {
+          for (auto &t : op.terms) {
+            if (t.la >= 0) omask[i] |= 1u << t.la;
+            if (t.lb >= 0) omask[i] |= 1u << t.lb;
+          }
+        }
       }
-    }
+    };
+    op_masks();
     // register stages when every block fits the registers of one thread
     const int T_ = int(hp.T);
     // tensor-core stages (precision 1) when the pass fits the TC kernel
@@ -803,11 +873,19 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
       size_t est = nops * sizeof(OpRec) + stages.size() * sizeof(StageRec) + 16;
       for (auto &op : ph.ops)
         est += op.type == OP_DENSE ? ((size_t(8) << (2 * op.blk.k())) + 15) / 16 * 16
-                                   : op.terms.size() * sizeof(PhaseTerm) + 16;
+                                   : op.terms.size() * sizeof(RegPhaseTerm) + sizeof(RegPhaseHdr) + 16;
       if (!reg_pass_fits(uint32_t(T_), uint32_t(c), uint32_t(stages.size()), uint32_t(est))) {
         reg = false;
         stages.clear();
       }
+    }
+    if (!reg && ph.pairs) {
+      // the shared-memory kernel takes phase terms with one tile qubit only
+      ph.ops.clear();
+      fuse_pass(gates, ph.acc, ph.Q, lpos, kmax, false, ph.ops);
+      ph.pairs = false;
+      op_masks();
+      hp.n_ops = uint32_t(nops);
     }
     if (reg) {
       for (auto &st : stages) order.insert(order.end(), st.ops.begin(), st.ops.end());
@@ -861,6 +939,11 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
         plan.info.n_blocks++;
         plan.info.hist_k[k]++;
         plan.info.flops += uint64_t(amps * 8.0 * K);
+      } else if (reg) {
+        r.type = OP_RPHASE;
+        r.count = put_rphase(op.terms, stages[stage_of[order[oi]]].R, buf);
+        nterms += r.count;
+        plan.info.n_phase++;
       } else {
         r.count = uint32_t(op.terms.size());
         for (auto &t : op.terms) {

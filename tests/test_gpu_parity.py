@@ -107,6 +107,37 @@ def test_diagonal_gates_outside_tile(sv):
         s.close()
 
 
+@pytest.mark.parametrize("n", [11, 15])
+def test_interleaved_diagonals(sv, n):
+    """Diagonal gates on two tile qubits between dense gates (the QFT pattern):
+    register-stage passes turn them into phase ops whose terms split by the
+    stage's register bits; every kernel path must agree with the oracle."""
+    rng = np.random.default_rng(40 + n)
+    circ = []
+    for _ in range(8):
+        for q in rng.choice(n, 3, replace=False):
+            circ.append(("u3", (int(q),), tuple(float(x) for x in rng.uniform(-3, 3, 3))))
+        for _ in range(24):
+            a, b = (int(x) for x in rng.choice(n, 2, replace=False))
+            kind = ["cp", "cz", "rz", "p", "t", "s", "cx", "h"][int(rng.integers(8))]
+            if kind == "cp":
+                circ.append((kind, (a, b), (float(rng.uniform(-4, 4)),)))
+            elif kind in ("cz", "cx"):
+                circ.append((kind, (a, b), ()))
+            elif kind in ("rz", "p"):
+                circ.append((kind, (a,), (float(rng.uniform(-4, 4)),)))
+            else:
+                circ.append((kind, (a,), ()))
+    ref = oracle.run(n, circ)
+    for opts in (dict(), dict(tile_qubits=9, low_qubits=4), dict(tile_qubits=13, k_max=1),
+                 dict(tile_qubits=10, k_max=3), dict(tile_qubits=12, k_max=4),
+                 dict(tile_qubits=11, precision=1), dict(tile_qubits=13, precision=1, k_max=2),
+                 dict(kernel_variant=1)):
+        s, g = _run_gpu(sv, n, circ, **opts)
+        _compare(g, ref, f"interleaved n={n} {opts}")
+        s.close()
+
+
 def test_ghz_and_qft_closed_forms(sv):
     n = 14
     s, g = _run_gpu(sv, n, W.ghz(n))
