@@ -85,10 +85,14 @@ typedef struct sv_opts {
   int32_t low_qubits;  /* c: low qubits every tile contains, so each global access
                           is a run of 2^c contiguous amplitudes (1..T; default 5) */
   int32_t precision;   /* 0 = FP32 CUDA cores for every block;
-                          1 = 3xTF32 tensor cores (tcgen05) for 4-5 qubit blocks */
+                          1 = 3xTF32 tensor cores (tcgen05): all dense blocks of a
+                          register stage as one 16x16 complex product */
   int32_t kernel_variant; /* 0 = amplitudes stay in registers across the ops of a
-                          stage, shared memory only between stages (default);
-                          1 = every op sweeps the shared-memory tile */
+                          stage, shared memory only between stages (default): 32
+                          amplitudes per thread when a pass's blocks have at most 2
+                          qubits and T <= 12, else 16;
+                          1 = every op sweeps the shared-memory tile;
+                          2 = register stages with 16 amplitudes per thread */
 } sv_opts;
 
 /* Statistics of the fusion + pass plan of a circuit (host-side only). */

@@ -110,12 +110,14 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 
 // Dense block on the register positions in MASK (matrix bit i <-> i-th set bit).
+// Element (a + ib) is stored as (a, a, -b, b): each complex product-accumulate
+// is two paired FMAs, (a, a) * (x.re, x.im) + (-b, b) * (x.im, x.re).
 template <int R, int MASK>
-__device__ __forceinline__ void reg_dense(float2 (&v)[1 << R], const float2 *__restrict__ m) {
+__device__ __forceinline__ void reg_dense(float2 (&v)[1 << R], const float4 *__restrict__ m) {
   constexpr int K = popc_c(MASK);
   constexpr int KK = 1 << K;
-  constexpr bool kInRegs = K <= 2;
-  float2 mm[kInRegs ? KK * KK : 1];
+  constexpr bool kInRegs = K <= 1;  // wider matrices are read from shared memory (broadcast)
+  float4 mm[kInRegs ? KK * KK : 1];
   if constexpr (kInRegs) {
 #pragma unroll
     for (int e = 0; e < KK * KK; e++) mm[e] = m[e];
@@ -128,28 +130,27 @@ __device__ __forceinline__ void reg_dense(float2 (&v)[1 << R], const float2 *__r
     for (int j = 0; j < KK; j++) x[j] = v[g | dep_c(j, MASK)];
 #pragma unroll
     for (int r = 0; r < KK; r++) {
-      float re = 0.f, im = 0.f;
+      if constexpr (!kInRegs) asm volatile("" ::: "memory");
+      float4 e = kInRegs ? mm[r * KK] : m[r * KK];
+      float2 o = __fmul2_rn(make_float2(e.x, e.y), x[0]);
+      o = __ffma2_rn(make_float2(e.z, e.w), make_float2(x[0].y, x[0].x), o);
 #pragma unroll
-      for (int j = 0; j < KK; j++) {
-        float2 e;
-        if constexpr (kInRegs) e = mm[r * KK + j];
-        else e = m[r * KK + j];
-        re = fmaf(e.x, x[j].x, re);
-        re = fmaf(-e.y, x[j].y, re);
-        im = fmaf(e.x, x[j].y, im);
-        im = fmaf(e.y, x[j].x, im);
+      for (int j = 1; j < KK; j++) {
+        e = kInRegs ? mm[r * KK + j] : m[r * KK + j];
+        o = __ffma2_rn(make_float2(e.x, e.y), x[j], o);
+        o = __ffma2_rn(make_float2(e.z, e.w), make_float2(x[j].y, x[j].x), o);
       }
-      v[g | dep_c(r, MASK)] = make_float2(re, im);
+      v[g | dep_c(r, MASK)] = o;
     }
   }
 }
 
 #define SV_CASE(M) \
-  case M: if constexpr ((M) < (1 << R)) reg_dense<R, (M)>(v, m); break;
+  case M: if constexpr ((M) < (1 << R) && popc_c(M) <= (R == 5 ? 2 : 4)) reg_dense<R, (M)>(v, m); break;
 
 template <int R>
 __device__ __forceinline__ void reg_dense_dispatch(float2 (&v)[1 << R], uint32_t mask,
-                                                   const float2 *__restrict__ m) {
+                                                   const float4 *__restrict__ m) {
   switch (mask) {
     SV_CASE(1) SV_CASE(2) SV_CASE(3) SV_CASE(4) SV_CASE(5) SV_CASE(6) SV_CASE(7)
     SV_CASE(8) SV_CASE(9) SV_CASE(10) SV_CASE(11) SV_CASE(12) SV_CASE(13) SV_CASE(14) SV_CASE(15)
@@ -233,21 +234,20 @@ constexpr uint32_t kMaxPassData = 160 * 1024;
 
 struct RegLayout {
   uint32_t L, nseg, NT, ns;
-  size_t off_in, off_x, off_seg, off_tab, off_acc, off_tt, off_data, total;
+  size_t off_in, off_x, off_seg, off_tt, off_data, total;
 };
 
-__host__ __device__ inline RegLayout reg_layout(uint32_t T, uint32_t c, uint32_t ns, uint32_t data_bytes) {
+__host__ __device__ inline RegLayout reg_layout(uint32_t T, uint32_t c, uint32_t ns, uint32_t data_bytes,
+                                                uint32_t R = 4) {
   RegLayout r;
   r.L = 1u << T;
   r.nseg = 1u << (T - c);
-  r.NT = 1u << (T - 4);
+  r.NT = 1u << (T - R);
   r.ns = ns;
   size_t o = 0;
   r.off_in = o; o += size_t(r.L) * 8;
   r.off_x = o; o += size_t(r.L) * 8;
   r.off_seg = o; o += size_t(r.nseg) * 8;
-  r.off_tab = o; o += 256 * 8;
-  r.off_acc = o; o += 64 * 4;
   r.off_tt = o; o += size_t(ns) * r.NT * 4;
   o = (o + 15) & ~size_t(15);
   r.off_data = o; o += data_bytes;
@@ -255,8 +255,11 @@ __host__ __device__ inline RegLayout reg_layout(uint32_t T, uint32_t c, uint32_t
   return r;
 }
 
+// 16 amplitudes per thread (blocks up to 4 qubits): 128 registers, two CTAs
+// of 256 threads per SM; 32 amplitudes per thread (blocks up to 2 qubits):
+// three CTAs of 128 threads per SM.
 template <int R, int NTMAX>
-__global__ void __launch_bounds__(NTMAX, NTMAX <= 256 ? 3 : 1) k_pass_reg(float2 *__restrict__ amp,
+__global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 3 : 1) : (NTMAX <= 256 ? 2 : 1)) k_pass_reg(float2 *__restrict__ amp,
                                                                  const uint8_t *__restrict__ plan,
                                                                  uint32_t pass_off) {
   constexpr int NR = 1 << R;
@@ -266,12 +269,10 @@ __global__ void __launch_bounds__(NTMAX, NTMAX <= 256 ? 3 : 1) k_pass_reg(float2
   const uint32_t ns = P->n_stages;
   const uint32_t data_off = P->ops_off, data_bytes = P->data_bytes;
   const uint64_t outer_mask = P->outer_mask, n_tiles = P->n_tiles;
-  const RegLayout lay = reg_layout(T, c, ns, data_bytes);
+  const RegLayout lay = reg_layout(T, c, ns, data_bytes, R);
   float2 *buf_in = reinterpret_cast<float2 *>(smem + lay.off_in);
   float2 *buf_x = reinterpret_cast<float2 *>(smem + lay.off_x);
   uint64_t *segoff = reinterpret_cast<uint64_t *>(smem + lay.off_seg);
-  float2 *tab = reinterpret_cast<float2 *>(smem + lay.off_tab);
-  uint32_t *acc = reinterpret_cast<uint32_t *>(smem + lay.off_acc);
   uint32_t *tt = reinterpret_cast<uint32_t *>(smem + lay.off_tt);
   uint8_t *data = smem + lay.off_data;
   const uint32_t tid = threadIdx.x, NT = blockDim.x;
@@ -343,7 +344,7 @@ __global__ void __launch_bounds__(NTMAX, NTMAX <= 256 ? 3 : 1) k_pass_reg(float2
       for (uint32_t o = st.op_begin; o < oe; o++) {
         const OpRec op = ops[o];
         if (op.type == OP_DENSE) {
-          reg_dense_dispatch<R>(v, op.rmask, reinterpret_cast<const float2 *>(data + (op.data_off - data_off)));
+          reg_dense_dispatch<R>(v, op.rmask, reinterpret_cast<const float4 *>(data + (op.data_off - data_off)));
         } else {
           reg_rphase<R>(v, data + (op.data_off - data_off), base, LB);
         }
@@ -368,7 +369,7 @@ constexpr size_t kSmemOptIn = 232448;  // 227 KiB per CTA on sm_100-class parts
 template <int R, int NTMAX>
 static cudaError_t launch_reg(float2 *amp, const uint8_t *plan, uint32_t off, const PlanPass &hp,
                               cudaStream_t st) {
-  const RegLayout lay = reg_layout(hp.T, hp.c, hp.n_stages, hp.data_bytes);
+  const RegLayout lay = reg_layout(hp.T, hp.c, hp.n_stages, hp.data_bytes, R);
   static unsigned long long configured = 0;
   static int sms[64] = {0};
   int dev = 0;
@@ -395,9 +396,9 @@ static cudaError_t launch_reg(float2 *amp, const uint8_t *plan, uint32_t off, co
 }
 
 // Whether a KIND_REG pass fits the persistent kernel's shared-memory tables.
-bool reg_pass_fits(uint32_t T, uint32_t c, uint32_t n_stages, uint32_t data_bytes) {
-  return T <= uint32_t(kMaxTile) && T >= 9 && n_stages <= uint32_t(kMaxStages) &&
-         data_bytes <= kMaxPassData && reg_layout(T, c, n_stages, data_bytes).total <= kSmemOptIn;
+bool reg_pass_fits(uint32_t T, uint32_t c, uint32_t R, uint32_t n_stages, uint32_t data_bytes) {
+  return (R == 4 || R == 5) && T <= uint32_t(kMaxTile) && T >= R + 5 && n_stages <= uint32_t(kMaxStages) &&
+         data_bytes <= kMaxPassData && reg_layout(T, c, n_stages, data_bytes, R).total <= kSmemOptIn;
 }
 
 
@@ -426,8 +427,6 @@ __global__ void __launch_bounds__(NTMAX, NTMAX <= 128 ? 4 : (NTMAX <= 256 ? 2 : 
   float2 *buf_in = reinterpret_cast<float2 *>(smem + lay.off_in);
   float2 *buf_x = reinterpret_cast<float2 *>(smem + lay.off_x);
   uint64_t *segoff = reinterpret_cast<uint64_t *>(smem + lay.off_seg);
-  float2 *tab = reinterpret_cast<float2 *>(smem + lay.off_tab);
-  uint32_t *acc = reinterpret_cast<uint32_t *>(smem + lay.off_acc);
   uint32_t *tt = reinterpret_cast<uint32_t *>(smem + lay.off_tt);
   uint8_t *data = smem + lay.off_data;
   const uint32_t tid = threadIdx.x, NT = blockDim.x, warp = tid >> 5;
@@ -671,6 +670,10 @@ cudaError_t launch_pass(float2 *amp, const uint8_t *plan_dev, uint32_t pass_off,
     return launch_tc<512>(amp, plan_dev, pass_off, hp, err, stream);
   }
   if (hp.kind == KIND_REG) {
+    if (hp.R == 5) {
+      if (hp.T <= 12) return launch_reg<5, 128>(amp, plan_dev, pass_off, hp, stream);
+      return launch_reg<5, 256>(amp, plan_dev, pass_off, hp, stream);
+    }
     if (hp.R != 4) return cudaErrorInvalidValue;
     if (hp.T <= 12) return launch_reg<4, 256>(amp, plan_dev, pass_off, hp, stream);
     return launch_reg<4, 512>(amp, plan_dev, pass_off, hp, stream);

@@ -94,7 +94,9 @@ struct alignas(16) OpRec {
   uint8_t lb[5];        // DENSE: local bits, matrix bit m <-> lb[m]
   uint8_t rmask;        // DENSE in a KIND_REG pass: register positions (matrix bits in
                         // ascending register order)
-  uint32_t data_off;    // DENSE: byte offset of float2[4^k] (row-major); PHASE: of PhaseTerm[]
+  uint32_t data_off;    // DENSE: byte offset of the row-major matrix: float2 (re, im) per
+                        // element, or in KIND_REG passes float4 (re, re, -im, im);
+                        // PHASE: of PhaseTerm[]; RPHASE: of RegPhaseHdr + terms
   uint32_t count;       // PHASE: number of terms
 };
 
@@ -113,10 +115,10 @@ struct alignas(16) PhaseTerm {
 // LB), and D[j] collects the terms that depend on register bits only.  Terms
 // are stored by class: class c occupies [end[c-1], end[c]).
 struct alignas(16) RegPhaseHdr {
-  uint32_t end[5];      // cumulative term counts of classes 0..4
+  uint32_t end[6];      // cumulative term counts of classes 0..R (R <= 5)
   uint32_t has_d;       // D differs from the identity
-  uint32_t pad_[2];
-  float2 d[16];         // register-only diagonal
+  uint32_t pad_;
+  float2 d[32];         // register-only diagonal (2^R entries used)
 };
 struct alignas(16) RegPhaseTerm {
   uint64_t outer_mask;  // outer qubits that must all be 1
@@ -124,7 +126,7 @@ struct alignas(16) RegPhaseTerm {
   uint32_t turn;        // fraction of 2*pi, scaled by 2^32
 };
 
-static_assert(sizeof(RegPhaseHdr) == 160, "RegPhaseHdr layout");
+static_assert(sizeof(RegPhaseHdr) == 288, "RegPhaseHdr layout");
 static_assert(sizeof(RegPhaseTerm) == 16, "RegPhaseTerm layout");
 static_assert(sizeof(PlanPass) == 112, "PlanPass layout");
 static_assert(sizeof(StageRec) == 160, "StageRec layout");
@@ -138,7 +140,7 @@ cudaError_t launch_pass(float2 *amp, const uint8_t *plan_dev, uint32_t pass_off,
 // Whether a tensor-core pass fits the kernel's shared memory.
 bool tc_pass_fits(uint32_t T, uint32_t c, uint32_t n_stages, uint32_t data_bytes);
 // Whether a register-stage pass fits the persistent kernel's shared-memory tables.
-bool reg_pass_fits(uint32_t T, uint32_t c, uint32_t n_stages, uint32_t data_bytes);
+bool reg_pass_fits(uint32_t T, uint32_t c, uint32_t R, uint32_t n_stages, uint32_t data_bytes);
 
 // Measurement kernels (sv_measure.cu).
 struct MeasureScratch {

@@ -412,17 +412,19 @@ static void align16(std::vector<uint8_t> &buf) {
   while (buf.size() % 16) buf.push_back(0);
 }
 
-// Register stages hold 16 amplitudes per thread (R = 4 register bits); the
-// persistent kernels take 9 <= T <= 13 with at least 4 non-low tile bits.
-static bool T_reg_ok(int T, int c) { return T - 4 >= 5 && T - 4 <= 9 && T - c >= 4; }
+// Register stages hold 2^Rb amplitudes per thread (Rb = 4 or 5 register
+// bits); the persistent kernels take Rb + 5 <= T <= 13 with at least Rb
+// non-low tile bits.
+static bool T_reg_ok(int T, int c, int Rb) { return T - Rb >= 5 && T <= kMaxTile && T - c >= Rb; }
 
 // Appends the OP_RPHASE record of a phase op placed in a register stage whose
 // register bits are R (register index i <-> i-th lowest bit of R); returns the
 // number of stored terms.  Terms on register bits only fold into D.
 static uint32_t put_rphase(const std::vector<HostTerm> &terms, uint32_t R, std::vector<uint8_t> &buf) {
   RegPhaseHdr h{};
-  uint32_t dturn[16] = {0};
-  std::vector<RegPhaseTerm> cls[5];
+  const int Rb = popc(uint64_t(R));
+  uint32_t dturn[32] = {0};
+  std::vector<RegPhaseTerm> cls[6];
   for (const HostTerm &t : terms) {
     uint32_t tmask = 0, jm = 0;
     int nreg = 0, reg0 = -1;
@@ -438,7 +440,7 @@ static uint32_t put_rphase(const std::vector<HostTerm> &terms, uint32_t R, std::
       }
     }
     if (tmask == 0 && t.outer == 0) {
-      for (int j = 0; j < 16; j++)
+      for (int j = 0; j < (1 << Rb); j++)
         if ((uint32_t(j) & jm) == jm) dturn[j] += t.turn;
     } else {
       // a term has at most two qubits, so here it has at most one register bit
@@ -446,17 +448,17 @@ static uint32_t put_rphase(const std::vector<HostTerm> &terms, uint32_t R, std::
     }
   }
   uint32_t n = 0;
-  for (int k = 0; k < 5; k++) {
+  for (int k = 0; k < 6; k++) {
     n += uint32_t(cls[k].size());
     h.end[k] = n;
   }
-  for (int j = 0; j < 16; j++) {
+  for (int j = 0; j < 32; j++) {
     if (dturn[j]) h.has_d = 1;
     const double a = 2.0 * M_PI * double(dturn[j]) / 4294967296.0;
     h.d[j] = make_float2(float(std::cos(a)), float(std::sin(a)));
   }
   put_bytes(buf, &h, sizeof(h));
-  for (int k = 0; k < 5; k++)
+  for (int k = 0; k < 6; k++)
     if (!cls[k].empty()) put_bytes(buf, cls[k].data(), cls[k].size() * sizeof(RegPhaseTerm));
   return n;
 }
@@ -718,12 +720,15 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
     err = "precision must be 0 or 1";
     return false;
   }
-  // kernel_variant: 0 = register stages where possible, 1 = shared-memory sweeps
+  // kernel_variant: 0 = register stages where possible (32 amplitudes per
+  // thread when the pass's blocks have at most 2 qubits and T <= 12, else 16),
+  // 1 = shared-memory sweeps, 2 = register stages with 16 amplitudes per thread
   const bool o_smem = (o.kernel_variant == 1);
-  if (o.kernel_variant < 0 || o.kernel_variant > 1) {
-    err = "kernel_variant must be 0 or 1";
+  if (o.kernel_variant < 0 || o.kernel_variant > 2) {
+    err = "kernel_variant must be 0, 1 or 2";
     return false;
   }
+  const bool o_r5 = (o.kernel_variant == 0);
   if (T > n) T = n;
   if (c > T) c = T;
   // a pass must be able to take any single gate (up to 5 qubits) next to the c low qubits
@@ -797,7 +802,7 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
     // two-local-qubit phase terms only where the pass can run on register stages
     int wmax = 1;
     for (uint32_t gi : acc) wmax = std::max(wmax, gates[gi].k);
-    ph.pairs = !o_smem && kmax <= 4 && wmax <= 4 && T_reg_ok(popc(Q), c);
+    ph.pairs = !o_smem && kmax <= 4 && wmax <= 4 && T_reg_ok(popc(Q), c, 4);
     fuse_pass(gates, acc, Q, lpos, kmax, ph.pairs, ph.ops);
     ph.acc = std::move(acc);
     passes.push_back(std::move(ph));
@@ -860,10 +865,10 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
       plan.pass_offs[p] = uint32_t(p * sizeof(PlanPass));
       continue;
     }
-    // register stages hold 16 amplitudes per thread (blocks up to 4 qubits);
-    // passes with a 5-qubit block use the shared-memory kernel
-    const int Rb = 4;
-    const bool use_reg = !o_smem && kmx <= 4 && T_ - Rb >= 5 && T_ - Rb <= 9 && T_ - c >= Rb;
+    // register stages hold 2^Rb amplitudes per thread (blocks up to 4
+    // qubits); passes with 5-qubit blocks use the shared-memory kernel
+    const int Rb = (o_r5 && kmx <= 2 && T_ <= 12 && T_reg_ok(T_, c, 5)) ? 5 : 4;
+    const bool use_reg = !o_smem && kmx <= 4 && T_reg_ok(T_, c, Rb);
     std::vector<HStage> stages;
     std::vector<int> order;
     bool reg = use_reg;
@@ -872,9 +877,9 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
       // bytes of this pass's records as packed below (16-byte aligned pieces)
       size_t est = nops * sizeof(OpRec) + stages.size() * sizeof(StageRec) + 16;
       for (auto &op : ph.ops)
-        est += op.type == OP_DENSE ? ((size_t(8) << (2 * op.blk.k())) + 15) / 16 * 16
+        est += op.type == OP_DENSE ? ((size_t(16) << (2 * op.blk.k())) + 15) / 16 * 16
                                    : op.terms.size() * sizeof(RegPhaseTerm) + sizeof(RegPhaseHdr) + 16;
-      if (!reg_pass_fits(uint32_t(T_), uint32_t(c), uint32_t(stages.size()), uint32_t(est))) {
+      if (!reg_pass_fits(uint32_t(T_), uint32_t(c), uint32_t(Rb), uint32_t(stages.size()), uint32_t(est))) {
         reg = false;
         stages.clear();
       }
@@ -933,8 +938,15 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
         for (int rr = 0; rr < K; rr++)
           for (int cc = 0; cc < K; cc++) {
             const cd e = op.blk.M[size_t(old_index(rr)) * K + old_index(cc)];
-            float f[2] = {float(e.real()), float(e.imag())};
-            put_bytes(buf, f, sizeof(f));
+            if (reg) {
+              // register stages: (re, re, -im, im), the operands of two paired FMAs
+              const float a = float(e.real()), b = float(e.imag());
+              float f[4] = {a, a, -b, b};
+              put_bytes(buf, f, sizeof(f));
+            } else {
+              float f[2] = {float(e.real()), float(e.imag())};
+              put_bytes(buf, f, sizeof(f));
+            }
           }
         plan.info.n_blocks++;
         plan.info.hist_k[k]++;

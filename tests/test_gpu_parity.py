@@ -53,7 +53,7 @@ def test_small_random_layered_default(sv):
     s.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("k_max", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("T,c", [(6, 1), (8, 3), (9, 5), (10, 5), (12, 5), (13, 4), (13, 5)])
 def test_random_layered_plans(sv, k_max, T, c, variant):
@@ -129,7 +129,8 @@ def test_interleaved_diagonals(sv, n):
             else:
                 circ.append((kind, (a,), ()))
     ref = oracle.run(n, circ)
-    for opts in (dict(), dict(tile_qubits=9, low_qubits=4), dict(tile_qubits=13, k_max=1),
+    for opts in (dict(), dict(kernel_variant=2), dict(tile_qubits=13),
+                 dict(tile_qubits=9, low_qubits=4), dict(tile_qubits=13, k_max=1),
                  dict(tile_qubits=10, k_max=3), dict(tile_qubits=12, k_max=4),
                  dict(tile_qubits=11, precision=1), dict(tile_qubits=13, precision=1, k_max=2),
                  dict(kernel_variant=1)):
