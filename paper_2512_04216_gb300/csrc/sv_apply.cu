@@ -109,38 +109,98 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// out = sum_j M[r][j] x[j] for one output row, element (a + ib) stored as
+// (a, a, -b, b): each complex product-accumulate is two paired FMAs,
+// (a, a) * (x.re, x.im) + (-b, b) * (x.im, x.re).
+template <int KK>
+__device__ __forceinline__ float2 row_dot(const float4 (&e)[KK], const float2 (&x)[KK]) {
+  float2 o = __fmul2_rn(make_float2(e[0].x, e[0].y), x[0]);
+  o = __ffma2_rn(make_float2(e[0].z, e[0].w), make_float2(x[0].y, x[0].x), o);
+#pragma unroll
+  for (int j = 1; j < KK; j++) {
+    o = __ffma2_rn(make_float2(e[j].x, e[j].y), x[j], o);
+    o = __ffma2_rn(make_float2(e[j].z, e[j].w), make_float2(x[j].y, x[j].x), o);
+  }
+  return o;
+}
+
 // Dense block on the register positions in MASK (matrix bit i <-> i-th set bit).
-// Element (a + ib) is stored as (a, a, -b, b): each complex product-accumulate
-// is two paired FMAs, (a, a) * (x.re, x.im) + (-b, b) * (x.im, x.re).
+// One-qubit blocks keep the matrix in registers.  Two-qubit blocks take the
+// matrix in two halves of two rows; each half is applied to every group of
+// the thread at once (independent FMA chains), the first half's outputs wait
+// in registers until the second half has read its inputs.  Wider blocks read
+// each row from shared memory per group.
 template <int R, int MASK>
 __device__ __forceinline__ void reg_dense(float2 (&v)[1 << R], const float4 *__restrict__ m) {
   constexpr int K = popc_c(MASK);
   constexpr int KK = 1 << K;
-  constexpr bool kInRegs = K <= 1;  // wider matrices are read from shared memory (broadcast)
-  float4 mm[kInRegs ? KK * KK : 1];
-  if constexpr (kInRegs) {
+  constexpr int NG = (1 << R) / KK;
+  if constexpr (K == 2) {
+    float2 t0[NG], t1[NG];
+    {
+      asm volatile("" ::: "memory");
+      float4 e0[4], e1[4];
 #pragma unroll
-    for (int e = 0; e < KK * KK; e++) mm[e] = m[e];
-  }
-#pragma unroll
-  for (int g = 0; g < (1 << R); g++) {
-    if (g & MASK) continue;
-    float2 x[KK];
-#pragma unroll
-    for (int j = 0; j < KK; j++) x[j] = v[g | dep_c(j, MASK)];
-#pragma unroll
-    for (int r = 0; r < KK; r++) {
-      if constexpr (!kInRegs) asm volatile("" ::: "memory");
-      float4 e = kInRegs ? mm[r * KK] : m[r * KK];
-      float2 o = __fmul2_rn(make_float2(e.x, e.y), x[0]);
-      o = __ffma2_rn(make_float2(e.z, e.w), make_float2(x[0].y, x[0].x), o);
-#pragma unroll
-      for (int j = 1; j < KK; j++) {
-        e = kInRegs ? mm[r * KK + j] : m[r * KK + j];
-        o = __ffma2_rn(make_float2(e.x, e.y), x[j], o);
-        o = __ffma2_rn(make_float2(e.z, e.w), make_float2(x[j].y, x[j].x), o);
+      for (int j = 0; j < 4; j++) {
+        e0[j] = m[j];
+        e1[j] = m[4 + j];
       }
-      v[g | dep_c(r, MASK)] = o;
+      int gi = 0;
+#pragma unroll
+      for (int g = 0; g < (1 << R); g++) {
+        if (g & MASK) continue;
+        float2 x[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) x[j] = v[g | dep_c(j, MASK)];
+        t0[gi] = row_dot<4>(e0, x);
+        t1[gi] = row_dot<4>(e1, x);
+        gi++;
+      }
+    }
+    {
+      asm volatile("" ::: "memory");
+      float4 e2[4], e3[4];
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        e2[j] = m[8 + j];
+        e3[j] = m[12 + j];
+      }
+      int gi = 0;
+#pragma unroll
+      for (int g = 0; g < (1 << R); g++) {
+        if (g & MASK) continue;
+        float2 x[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) x[j] = v[g | dep_c(j, MASK)];
+        const float2 o2 = row_dot<4>(e2, x), o3 = row_dot<4>(e3, x);
+        v[g | dep_c(0, MASK)] = t0[gi];
+        v[g | dep_c(1, MASK)] = t1[gi];
+        v[g | dep_c(2, MASK)] = o2;
+        v[g | dep_c(3, MASK)] = o3;
+        gi++;
+      }
+    }
+  } else {
+    constexpr bool kInRegs = K <= 1;
+    float4 mm[kInRegs ? KK * KK : 1];
+    if constexpr (kInRegs) {
+#pragma unroll
+      for (int e = 0; e < KK * KK; e++) mm[e] = m[e];
+    }
+#pragma unroll
+    for (int g = 0; g < (1 << R); g++) {
+      if (g & MASK) continue;
+      float2 x[KK];
+#pragma unroll
+      for (int j = 0; j < KK; j++) x[j] = v[g | dep_c(j, MASK)];
+#pragma unroll
+      for (int r = 0; r < KK; r++) {
+        if constexpr (!kInRegs) asm volatile("" ::: "memory");
+        float4 e[KK];
+#pragma unroll
+        for (int j = 0; j < KK; j++) e[j] = kInRegs ? mm[r * KK + j] : m[r * KK + j];
+        v[g | dep_c(r, MASK)] = row_dot<KK>(e, x);
+      }
     }
   }
 }
