@@ -11,7 +11,11 @@
 //     qubits, always including the c lowest).  Diagonal gates need not fit Q:
 //     their effect on a tile depends on outer qubits only through a per-tile
 //     constant.  A rejected gate blocks its qubits for the rest of the scan, so
-//     every accepted gate commutes with every rejected gate before it.
+//     every accepted gate commutes with every rejected gate before it.  Two
+//     choices of Q are tried per pass and the one accepting more non-diagonal
+//     gates is kept: growing Q in scan order (first come, first served), and
+//     growing Q one qubit or one two-qubit gate at a time by the most gates a
+//     scan of the next unapplied gates then accepts per added qubit.
 //  2. Fusion.  Within a pass, gates are merged into dense blocks of at most
 //     k_max qubits (open blocks on disjoint qubit sets; a gate merges the open
 //     blocks it touches when the union fits, else those blocks are emitted and
@@ -701,6 +705,80 @@ static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint3
   return true;
 }
 
+// Accepted / rejected split of `rem` for a fixed tile set Q.
+static void scan_fixed(const std::vector<GateM> &gates, const std::vector<uint32_t> &rem, uint64_t Q,
+                       std::vector<uint32_t> &acc, std::vector<uint32_t> &rest) {
+  uint64_t blocked = 0;
+  acc.clear();
+  rest.clear();
+  for (uint32_t gi : rem) {
+    const GateM &g = gates[gi];
+    if (!(g.mask & blocked) && (g.diag || (g.mask & ~Q) == 0)) {
+      acc.push_back(gi);
+    } else {
+      blocked |= g.mask;
+      rest.push_back(gi);
+    }
+  }
+}
+
+// Non-diagonal gates among the first `limit` of `rem` that a fixed Q accepts.
+static int count_fixed(const std::vector<GateM> &gates, const std::vector<uint32_t> &rem, size_t limit,
+                       uint64_t Q) {
+  uint64_t blocked = 0;
+  int cnt = 0;
+  for (size_t i = 0; i < limit; i++) {
+    const GateM &g = gates[rem[i]];
+    if (!(g.mask & blocked) && (g.diag || (g.mask & ~Q) == 0)) {
+      cnt += !g.diag;
+    } else {
+      blocked |= g.mask;
+    }
+  }
+  return cnt;
+}
+
+// Tile set grown by look-ahead: start from the low qubits and the first
+// unapplied gate, then repeatedly add the single qubit, or the two outside
+// qubits of a gate in the look-ahead window, that lets a scan of the window
+// accept the most non-diagonal gates per added qubit.
+static uint64_t lookahead_tile(const std::vector<GateM> &gates, const std::vector<uint32_t> &rem, int n,
+                               int T, uint64_t lowmask) {
+  constexpr size_t kWindow = 96;
+  const size_t W = std::min(rem.size(), kWindow);
+  uint64_t Q = lowmask;
+  for (uint32_t gi : rem)
+    if (!gates[gi].diag) {
+      if (popc(Q | gates[gi].mask) <= T) Q |= gates[gi].mask;
+      break;
+    }
+  std::vector<uint64_t> cand;
+  while (popc(Q) < T) {
+    cand.clear();
+    for (int q = 0; q < n; q++)
+      if (!((Q >> q) & 1)) cand.push_back(uint64_t(1) << q);
+    if (popc(Q) + 2 <= T)
+      for (size_t i = 0; i < W; i++) {
+        const uint64_t m = gates[rem[i]].mask & ~Q;
+        if (popc(m) == 2) cand.push_back(m);
+      }
+    std::sort(cand.begin(), cand.end());
+    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+    double best = -1.0;
+    uint64_t best_m = 0;
+    for (uint64_t m : cand) {
+      const double sc = double(count_fixed(gates, rem, W, Q | m)) / popc(m);
+      if (sc > best) {
+        best = sc;
+        best_m = m;
+      }
+    }
+    if (!best_m) break;
+    Q |= best_m;
+  }
+  return Q;
+}
+
 bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Plan &plan,
                 std::string &err) {
   sv_opts o{};
@@ -788,6 +866,28 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
     }
     // fill the tile set up to T qubits with the lowest unused qubits
     for (int q = 0; q < n && popc(Q) < T; q++) Q |= uint64_t(1) << q;
+    // rescan with the full tile set, and compare with the look-ahead tile set
+    if (T < n) {
+      auto nondiag = [&](const std::vector<uint32_t> &a) {
+        size_t k = 0;
+        for (uint32_t gi : a) k += !gates[gi].diag;
+        return k;
+      };
+      std::vector<uint32_t> acc2, rest2;
+      scan_fixed(gates, remaining, Q, acc2, rest2);
+      if (nondiag(acc2) >= nondiag(acc)) {
+        acc.swap(acc2);
+        rest.swap(rest2);
+      }
+      uint64_t Ql = lookahead_tile(gates, remaining, n, T, lowmask);
+      for (int q = 0; q < n && popc(Ql) < T; q++) Ql |= uint64_t(1) << q;
+      scan_fixed(gates, remaining, Ql, acc2, rest2);
+      if (nondiag(acc2) > nondiag(acc)) {
+        acc.swap(acc2);
+        rest.swap(rest2);
+        Q = Ql;
+      }
+    }
     PassH ph;
     ph.Q = Q;
     int lpos[64];
