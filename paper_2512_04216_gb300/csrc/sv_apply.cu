@@ -319,9 +319,9 @@ __host__ __device__ inline RegLayout reg_layout(uint32_t T, uint32_t c, uint32_t
 // of 256 threads per SM; 32 amplitudes per thread (blocks up to 2 qubits):
 // three CTAs of 128 threads per SM.
 template <int R, int NTMAX>
-__global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 3 : 1) : (NTMAX <= 256 ? 2 : 1)) k_pass_reg(float2 *__restrict__ amp,
-                                                                 const uint8_t *__restrict__ plan,
-                                                                 uint32_t pass_off) {
+__global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 3 : 1) : (NTMAX <= 256 ? 2 : 1))
+    k_pass_reg(float2 *__restrict__ amp, const uint8_t *__restrict__ plan, uint32_t pass_off,
+               const __grid_constant__ RegPassParams prm) {
   constexpr int NR = 1 << R;
   extern __shared__ __align__(16) unsigned char smem[];
   const PlanPass *P = reinterpret_cast<const PlanPass *>(plan + pass_off);
@@ -332,7 +332,6 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 3 : 1) : (NTMA
   const RegLayout lay = reg_layout(T, c, ns, data_bytes, R);
   float2 *buf_in = reinterpret_cast<float2 *>(smem + lay.off_in);
   float2 *buf_x = reinterpret_cast<float2 *>(smem + lay.off_x);
-  uint64_t *segoff = reinterpret_cast<uint64_t *>(smem + lay.off_seg);
   uint32_t *tt = reinterpret_cast<uint32_t *>(smem + lay.off_tt);
   uint8_t *data = smem + lay.off_data;
   const uint32_t tid = threadIdx.x, NT = blockDim.x;
@@ -344,7 +343,6 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 3 : 1) : (NTMA
     for (uint32_t i = tid; i < data_bytes / 16; i += NT) dst[i] = src[i];
   }
   const uint64_t hm = P->high_mask;
-  for (uint32_t s = tid; s < lay.nseg; s += NT) segoff[s] = pdep_u64(s, hm);
   __syncthreads();
   const StageRec *stages = reinterpret_cast<const StageRec *>(data + (P->stages_off - data_off));
   const OpRec *ops = reinterpret_cast<const OpRec *>(data);
@@ -357,13 +355,23 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 3 : 1) : (NTMA
   }
   const uint32_t lowmask = (1u << c) - 1u;
   const uint32_t cs = c - 1u, cmask = (1u << cs) - 1u;
-  const uint32_t nchunk = lay.L >> 1;
+  constexpr int NK = NR / 2;  // 16-byte chunks per thread per tile
+  unsigned char *sin = reinterpret_cast<unsigned char *>(buf_in);
+  unsigned char *sx = reinterpret_cast<unsigned char *>(buf_x);
+  // tile-invariant per-thread parts of the addresses
+  const uint32_t t_ld = (tt[tid] & 0xffffu) * 8u;
+  uint64_t t_st;
+  {
+    const uint32_t LB = tt[(ns - 1) * NT + tid] & 0xffffu;
+    t_st = pdep_u64(LB >> c, hm) + (LB & lowmask);
+  }
+  const uint64_t t_cp = pdep_u64(tid >> cs, hm) + (uint64_t(tid & cmask) << 1);
 
   uint64_t tile = blockIdx.x;
   uint64_t base = tile < n_tiles ? pdep_u64(tile, outer_mask) : 0;
   if (tile < n_tiles) {
-    for (uint32_t i = tid; i < nchunk; i += NT)
-      cp_async16(buf_in + 2 * i, amp + base + segoff[i >> cs] + (uint64_t(i & cmask) << 1));
+#pragma unroll
+    for (int k = 0; k < NK; k++) cp_async16(sin + (tid + k * NT) * 16u, amp + base + t_cp + prm.ko[k]);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
   __syncthreads();
@@ -372,33 +380,42 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 3 : 1) : (NTMA
   while (tile < n_tiles) {
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
-    {
-      const StageRec &st = stages[0];
-      const uint32_t LB = tt[tid] & 0xffffu;
 #pragma unroll
-      for (int j = 0; j < NR; j++) v[j] = buf_in[uint32_t(st.la[j]) | LB];
-    }
+    for (int j = 0; j < NR; j++) v[j] = *reinterpret_cast<const float2 *>(sin + t_ld + prm.lo[j]);
     __syncthreads();  // buf_in is free: prefetch the next tile
     const uint64_t next = tile + gridDim.x;
     const uint64_t base_next = next < n_tiles ? pdep_u64(next, outer_mask) : 0;
     if (next < n_tiles) {
-      for (uint32_t i = tid; i < nchunk; i += NT)
-        cp_async16(buf_in + 2 * i, amp + base_next + segoff[i >> cs] + (uint64_t(i & cmask) << 1));
+#pragma unroll
+      for (int k = 0; k < NK; k++) cp_async16(sin + (tid + k * NT) * 16u, amp + base_next + t_cp + prm.ko[k]);
       asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
     for (uint32_t s = 0; s < ns; s++) {
       const StageRec &st = stages[s];
       const uint32_t w = tt[s * NT + tid];
-      const uint32_t LB = w & 0xffffu, PB = w >> 16;
+      const uint32_t LB = w & 0xffffu;
       if (s > 0) {
         const StageRec &pv = stages[s - 1];
-        const uint32_t PBp = tt[(s - 1) * NT + tid] >> 16;
+        const uint32_t PBp = (tt[(s - 1) * NT + tid] >> 16) * 8u, PB = (w >> 16) * 8u;
+        uint32_t xo[NR];
+        const uint4 *q = reinterpret_cast<const uint4 *>(pv.xo);
+#pragma unroll
+        for (int j = 0; j < NR / 4; j++) {
+          const uint4 t4 = q[j];
+          xo[4 * j] = t4.x; xo[4 * j + 1] = t4.y; xo[4 * j + 2] = t4.z; xo[4 * j + 3] = t4.w;
+        }
         __syncthreads();  // previous readers of buf_x are done
 #pragma unroll
-        for (int j = 0; j < NR; j++) buf_x[uint32_t(pv.pa[j]) ^ PBp] = v[j];
+        for (int j = 0; j < NR; j++) *reinterpret_cast<float2 *>(sx + (xo[j] ^ PBp)) = v[j];
+        q = reinterpret_cast<const uint4 *>(st.xo);
+#pragma unroll
+        for (int j = 0; j < NR / 4; j++) {
+          const uint4 t4 = q[j];
+          xo[4 * j] = t4.x; xo[4 * j + 1] = t4.y; xo[4 * j + 2] = t4.z; xo[4 * j + 3] = t4.w;
+        }
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < NR; j++) v[j] = buf_x[uint32_t(st.pa[j]) ^ PB];
+        for (int j = 0; j < NR; j++) v[j] = *reinterpret_cast<const float2 *>(sx + (xo[j] ^ PB));
       }
       const uint32_t oe = st.op_end;
       for (uint32_t o = st.op_begin; o < oe; o++) {
@@ -411,13 +428,9 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 3 : 1) : (NTMA
       }
     }
     {
-      const StageRec &st = stages[ns - 1];
-      const uint32_t LB = tt[(ns - 1) * NT + tid] & 0xffffu;
+      float2 *dst = amp + base + t_st;
 #pragma unroll
-      for (int j = 0; j < NR; j++) {
-        const uint32_t l = uint32_t(st.la[j]) | LB;
-        __stcs(amp + base + segoff[l >> c] + (l & lowmask), v[j]);
-      }
+      for (int j = 0; j < NR; j++) __stcs(dst + prm.go[j], v[j]);
     }
     tile = next;
     base = base_next;
@@ -428,7 +441,7 @@ constexpr size_t kSmemOptIn = 232448;  // 227 KiB per CTA on sm_100-class parts
 
 template <int R, int NTMAX>
 static cudaError_t launch_reg(float2 *amp, const uint8_t *plan, uint32_t off, const PlanPass &hp,
-                              cudaStream_t st) {
+                              const RegPassParams &prm, cudaStream_t st) {
   const RegLayout lay = reg_layout(hp.T, hp.c, hp.n_stages, hp.data_bytes, R);
   static unsigned long long configured = 0;
   static int sms[64] = {0};
@@ -450,7 +463,7 @@ static cudaError_t launch_reg(float2 *amp, const uint8_t *plan, uint32_t off, co
   if (per_sm < 1) per_sm = 1;
   const uint64_t want = uint64_t(sms[dev < 64 ? dev : 0] > 0 ? sms[dev < 64 ? dev : 0] : 1) * per_sm;
   const unsigned grid = unsigned(hp.n_tiles < want ? hp.n_tiles : want);
-  k_pass_reg<R, NTMAX><<<grid, nt, lay.total, st>>>(amp, plan, off);
+  k_pass_reg<R, NTMAX><<<grid, nt, lay.total, st>>>(amp, plan, off, prm);
   count_launch();
   return cudaGetLastError();
 }
@@ -723,20 +736,21 @@ static cudaError_t launch_k(float2 *amp, const uint8_t *plan, uint32_t off, cons
 }
 
 cudaError_t launch_pass(float2 *amp, const uint8_t *plan_dev, uint32_t pass_off,
-                        const PlanPass &hp, int *err, cudaStream_t stream) {
+                        const PlanPass &hp, const RegPassParams *prm, int *err, cudaStream_t stream) {
   if (hp.kind == KIND_TC) {
     if (hp.T <= 11) return launch_tc<128>(amp, plan_dev, pass_off, hp, err, stream);
     if (hp.T == 12) return launch_tc<256>(amp, plan_dev, pass_off, hp, err, stream);
     return launch_tc<512>(amp, plan_dev, pass_off, hp, err, stream);
   }
   if (hp.kind == KIND_REG) {
+    if (!prm) return cudaErrorInvalidValue;
     if (hp.R == 5) {
-      if (hp.T <= 12) return launch_reg<5, 128>(amp, plan_dev, pass_off, hp, stream);
-      return launch_reg<5, 256>(amp, plan_dev, pass_off, hp, stream);
+      if (hp.T <= 12) return launch_reg<5, 128>(amp, plan_dev, pass_off, hp, *prm, stream);
+      return launch_reg<5, 256>(amp, plan_dev, pass_off, hp, *prm, stream);
     }
     if (hp.R != 4) return cudaErrorInvalidValue;
-    if (hp.T <= 12) return launch_reg<4, 256>(amp, plan_dev, pass_off, hp, stream);
-    return launch_reg<4, 512>(amp, plan_dev, pass_off, hp, stream);
+    if (hp.T <= 12) return launch_reg<4, 256>(amp, plan_dev, pass_off, hp, *prm, stream);
+    return launch_reg<4, 512>(amp, plan_dev, pass_off, hp, *prm, stream);
   }
   switch (hp.kmax) {
     case 0:

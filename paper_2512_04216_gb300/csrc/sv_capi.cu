@@ -395,7 +395,8 @@ int sv_apply_circuit(sv_state *s, const sv_gate *ir, size_t n_gates, const sv_op
   for (size_t p = 0; p < plan.passes.size(); p++) {
     const char *kname = plan.passes[p].kind == KIND_TC ? "pass_tc" : "pass";
     CK(s, timed(s, kname, pass_bytes, [&] {
-         return launch_pass(s->amp, s->plan_dev, plan.pass_offs[p], plan.passes[p], s->derr, s->stream);
+         return launch_pass(s->amp, s->plan_dev, plan.pass_offs[p], plan.passes[p], &plan.rparams[p], s->derr,
+                            s->stream);
        }));
   }
   return SV_OK;

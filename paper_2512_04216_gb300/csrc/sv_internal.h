@@ -70,6 +70,16 @@ struct alignas(16) StageRec {
   uint32_t flags;       // bit 0: load from HBM, bit 1: store to HBM,
                         // bit 2: KIND_TC stage with a tensor-core product
   uint32_t b_off;       // KIND_TC: byte offset of the stage's 8 KB B_hi/B_lo image
+  uint32_t xo[32];      // pa[j] * 8: byte offset of register amplitude j in the exchange buffer
+};
+
+// Tile-invariant address tables of a KIND_REG pass, passed to the kernel by
+// value (its loops over j and k unroll, so every entry is a compile-time
+// constant-bank operand).  A thread adds its own part once per CTA.
+struct RegPassParams {
+  uint32_t lo[32];      // first stage: la[j] * 8, byte offset in the natural-order tile
+  uint64_t go[32];      // last stage: amplitude offset of la[j] from the tile base in HBM
+  uint64_t ko[16];      // prefetch: amplitude offset of 16-byte chunk row k (chunks k*NT..)
 };
 
 // Columns of the shared-memory swizzle: local bit b < 4 maps to itself, local
@@ -129,14 +139,15 @@ struct alignas(16) RegPhaseTerm {
 static_assert(sizeof(RegPhaseHdr) == 288, "RegPhaseHdr layout");
 static_assert(sizeof(RegPhaseTerm) == 16, "RegPhaseTerm layout");
 static_assert(sizeof(PlanPass) == 112, "PlanPass layout");
-static_assert(sizeof(StageRec) == 160, "StageRec layout");
+static_assert(sizeof(StageRec) == 288, "StageRec layout");
 static_assert(sizeof(OpRec) == 16, "OpRec layout");
 static_assert(sizeof(PhaseTerm) == 16, "PhaseTerm layout");
 
 // Launch one pass kernel (sv_apply.cu).  plan_dev/pass_off locate the PlanPass;
 // host_pass is the same record on the host (for grid size and template choice).
 cudaError_t launch_pass(float2 *amp, const uint8_t *plan_dev, uint32_t pass_off,
-                        const PlanPass &host_pass, int *err, cudaStream_t stream);
+                        const PlanPass &host_pass, const RegPassParams *reg_params, int *err,
+                        cudaStream_t stream);
 // Whether a tensor-core pass fits the kernel's shared memory.
 bool tc_pass_fits(uint32_t T, uint32_t c, uint32_t n_stages, uint32_t data_bytes);
 // Whether a register-stage pass fits the persistent kernel's shared-memory tables.

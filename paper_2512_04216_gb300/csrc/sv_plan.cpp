@@ -569,6 +569,7 @@ static StageRec make_stage(const HStage &hs, int T, int c, int Rb, bool load, bo
       if ((j >> i) & 1) l |= 1u << sr.rb[i];
     sr.la[j] = uint16_t(l);
     sr.pa[j] = uint16_t(swz(l));
+    sr.xo[j] = uint32_t(swz(l)) * 8u;
   }
   sr.flags = (load ? 1u : 0u) | (store ? 2u : 0u);
   (void)c;
@@ -703,6 +704,30 @@ static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint3
   info.n_stages += srecs.size();
   info.tc_stages += nmma;
   return true;
+}
+
+static uint64_t pdep_host(uint64_t x, uint64_t mask) {
+  uint64_t out = 0;
+  for (int b = 0; b < 64 && x; b++)
+    if ((mask >> b) & 1) {
+      if (x & 1) out |= uint64_t(1) << b;
+      x >>= 1;
+    }
+  return out;
+}
+
+// Address tables of a KIND_REG pass (see RegPassParams).
+static RegPassParams reg_params(const PlanPass &hp, const StageRec &first, const StageRec &last) {
+  RegPassParams p{};
+  const uint32_t c = hp.c, cs = c - 1u, lowmask = (1u << c) - 1u;
+  const uint32_t NT = 1u << (hp.T - hp.R);
+  for (int j = 0; j < (1 << hp.R); j++) {
+    p.lo[j] = uint32_t(first.la[j]) * 8u;
+    const uint32_t l = last.la[j];
+    p.go[j] = pdep_host(l >> c, hp.high_mask) + (l & lowmask);
+  }
+  for (uint32_t k = 0; k < (1u << (hp.R - 1)); k++) p.ko[k] = pdep_host(uint64_t(k) * (NT >> cs), hp.high_mask);
+  return p;
 }
 
 // Accepted / rejected split of `rem` for a fixed tile set Q.
@@ -915,6 +940,7 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
   buf.resize(P * sizeof(PlanPass), 0);
   plan.passes.resize(P);
   plan.pass_offs.resize(P);
+  plan.rparams.assign(P, RegPassParams{});
   const double amps = std::ldexp(1.0, n);
   for (size_t p = 0; p < P; p++) {
     PassH &ph = passes[p];
@@ -1080,13 +1106,17 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
       align16(buf);
       hp.stages_off = uint32_t(buf.size());
       uint32_t ob = 0;
+      StageRec first{}, last{};
       for (size_t si = 0; si < stages.size(); si++) {
         StageRec sr = make_stage(stages[si], T_, c, Rb, si == 0, si + 1 == stages.size());
         sr.op_begin = ob;
         ob += uint32_t(stages[si].ops.size());
         sr.op_end = ob;
         put_bytes(buf, &sr, sizeof(sr));
+        if (si == 0) first = sr;
+        if (si + 1 == stages.size()) last = sr;
       }
+      plan.rparams[p] = reg_params(hp, first, last);
       plan.info.n_stages += stages.size();
     }
     align16(buf);

@@ -25,6 +25,7 @@ struct Plan {
   std::vector<uint8_t> bytes;        // packed PlanPass[P], OpRec[], matrices, terms
   std::vector<PlanPass> passes;      // host copies
   std::vector<uint32_t> pass_offs;   // byte offset of each PlanPass
+  std::vector<RegPassParams> rparams;  // KIND_REG passes: kernel address tables
   sv_plan_info info{};
 };
 
