@@ -124,19 +124,55 @@ __device__ __forceinline__ float2 row_dot(const float4 (&e)[KK], const float2 (&
   return o;
 }
 
+// acc[g] (+)= M[r][j] x_g[j] for every group g of the thread, loop over j
+// outermost so consecutive paired FMAs belong to independent chains.
+// Element (a + ib) is stored as (a, a, -b, b): each complex product-accumulate
+// is two paired FMAs, (a, a) * (x.re, x.im) + (-b, b) * (x.im, x.re).
+template <int R, int MASK, int ROW>
+__device__ __forceinline__ void rows_all_groups(const float2 (&v)[1 << R], const float4 (&e)[1 << popc_c(MASK)],
+                                                float2 (&acc)[(1 << R) >> popc_c(MASK)]) {
+  constexpr int KK = 1 << popc_c(MASK);
+#pragma unroll
+  for (int j = 0; j < KK; j++) {
+    int gi = 0;
+#pragma unroll
+    for (int g = 0; g < (1 << R); g++) {
+      if (g & MASK) continue;
+      const float2 x = v[g | dep_c(j, MASK)];
+      if (j == 0) acc[gi] = __fmul2_rn(make_float2(e[0].x, e[0].y), x);
+      else acc[gi] = __ffma2_rn(make_float2(e[j].x, e[j].y), x, acc[gi]);
+      acc[gi] = __ffma2_rn(make_float2(e[j].z, e[j].w), make_float2(x.y, x.x), acc[gi]);
+      gi++;
+    }
+  }
+}
+
 // Dense block on the register positions in MASK (matrix bit i <-> i-th set bit).
-// One-qubit blocks keep the matrix in registers.  Two-qubit blocks take the
-// matrix in two halves of two rows; each half is applied to every group of
-// the thread at once (independent FMA chains), the first half's outputs wait
-// in registers until the second half has read its inputs.  Wider blocks read
-// each row from shared memory per group.
+// Blocks of one and two qubits take the matrix one or two rows at a time and
+// apply them to every group of the thread at once (independent FMA chains);
+// outputs wait in registers until every row has read the group's inputs.
+// Wider blocks read each row from shared memory per group.
 template <int R, int MASK>
 __device__ __forceinline__ void reg_dense(float2 (&v)[1 << R], const float4 *__restrict__ m) {
   constexpr int K = popc_c(MASK);
   constexpr int KK = 1 << K;
   constexpr int NG = (1 << R) / KK;
-  if constexpr (K == 2) {
+  if constexpr (K == 1) {
+    float4 e0[2], e1[2];
+    e0[0] = m[0]; e0[1] = m[1]; e1[0] = m[2]; e1[1] = m[3];
     float2 t0[NG], t1[NG];
+    rows_all_groups<R, MASK, 0>(v, e0, t0);
+    rows_all_groups<R, MASK, 1>(v, e1, t1);
+    int gi = 0;
+#pragma unroll
+    for (int g = 0; g < (1 << R); g++) {
+      if (g & MASK) continue;
+      v[g | dep_c(0, MASK)] = t0[gi];
+      v[g | dep_c(1, MASK)] = t1[gi];
+      gi++;
+    }
+  } else if constexpr (K == 2) {
+    float2 t0[NG], t1[NG], t2[NG], t3[NG];
     {
       asm volatile("" ::: "memory");
       float4 e0[4], e1[4];
@@ -145,17 +181,8 @@ __device__ __forceinline__ void reg_dense(float2 (&v)[1 << R], const float4 *__r
         e0[j] = m[j];
         e1[j] = m[4 + j];
       }
-      int gi = 0;
-#pragma unroll
-      for (int g = 0; g < (1 << R); g++) {
-        if (g & MASK) continue;
-        float2 x[4];
-#pragma unroll
-        for (int j = 0; j < 4; j++) x[j] = v[g | dep_c(j, MASK)];
-        t0[gi] = row_dot<4>(e0, x);
-        t1[gi] = row_dot<4>(e1, x);
-        gi++;
-      }
+      rows_all_groups<R, MASK, 0>(v, e0, t0);
+      rows_all_groups<R, MASK, 1>(v, e1, t1);
     }
     {
       asm volatile("" ::: "memory");
@@ -165,28 +192,20 @@ __device__ __forceinline__ void reg_dense(float2 (&v)[1 << R], const float4 *__r
         e2[j] = m[8 + j];
         e3[j] = m[12 + j];
       }
-      int gi = 0;
+      rows_all_groups<R, MASK, 2>(v, e2, t2);
+      rows_all_groups<R, MASK, 3>(v, e3, t3);
+    }
+    int gi = 0;
 #pragma unroll
-      for (int g = 0; g < (1 << R); g++) {
-        if (g & MASK) continue;
-        float2 x[4];
-#pragma unroll
-        for (int j = 0; j < 4; j++) x[j] = v[g | dep_c(j, MASK)];
-        const float2 o2 = row_dot<4>(e2, x), o3 = row_dot<4>(e3, x);
-        v[g | dep_c(0, MASK)] = t0[gi];
-        v[g | dep_c(1, MASK)] = t1[gi];
-        v[g | dep_c(2, MASK)] = o2;
-        v[g | dep_c(3, MASK)] = o3;
-        gi++;
-      }
+    for (int g = 0; g < (1 << R); g++) {
+      if (g & MASK) continue;
+      v[g | dep_c(0, MASK)] = t0[gi];
+      v[g | dep_c(1, MASK)] = t1[gi];
+      v[g | dep_c(2, MASK)] = t2[gi];
+      v[g | dep_c(3, MASK)] = t3[gi];
+      gi++;
     }
   } else {
-    constexpr bool kInRegs = K <= 1;
-    float4 mm[kInRegs ? KK * KK : 1];
-    if constexpr (kInRegs) {
-#pragma unroll
-      for (int e = 0; e < KK * KK; e++) mm[e] = m[e];
-    }
 #pragma unroll
     for (int g = 0; g < (1 << R); g++) {
       if (g & MASK) continue;
@@ -195,10 +214,10 @@ __device__ __forceinline__ void reg_dense(float2 (&v)[1 << R], const float4 *__r
       for (int j = 0; j < KK; j++) x[j] = v[g | dep_c(j, MASK)];
 #pragma unroll
       for (int r = 0; r < KK; r++) {
-        if constexpr (!kInRegs) asm volatile("" ::: "memory");
+        asm volatile("" ::: "memory");
         float4 e[KK];
 #pragma unroll
-        for (int j = 0; j < KK; j++) e[j] = kInRegs ? mm[r * KK + j] : m[r * KK + j];
+        for (int j = 0; j < KK; j++) e[j] = m[r * KK + j];
         v[g | dep_c(r, MASK)] = row_dot<KK>(e, x);
       }
     }
@@ -356,10 +375,10 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 3 : 1) : (NTMA
   const uint32_t lowmask = (1u << c) - 1u;
   const uint32_t cs = c - 1u, cmask = (1u << cs) - 1u;
   constexpr int NK = NR / 2;  // 16-byte chunks per thread per tile
-  unsigned char *sin = reinterpret_cast<unsigned char *>(buf_in);
-  unsigned char *sx = reinterpret_cast<unsigned char *>(buf_x);
+  const uint32_t sin = static_cast<uint32_t>(__cvta_generic_to_shared(buf_in));
+  const uint32_t sx = static_cast<uint32_t>(__cvta_generic_to_shared(buf_x));
   // tile-invariant per-thread parts of the addresses
-  const uint32_t t_ld = (tt[tid] & 0xffffu) * 8u;
+  const uint32_t t_ld = sin + (tt[tid] & 0xffffu) * 8u;
   uint64_t t_st;
   {
     const uint32_t LB = tt[(ns - 1) * NT + tid] & 0xffffu;
@@ -371,7 +390,7 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 3 : 1) : (NTMA
   uint64_t base = tile < n_tiles ? pdep_u64(tile, outer_mask) : 0;
   if (tile < n_tiles) {
 #pragma unroll
-    for (int k = 0; k < NK; k++) cp_async16(sin + (tid + k * NT) * 16u, amp + base + t_cp + prm.ko[k]);
+    for (int k = 0; k < NK; k++) cp_async16_s(sin + (tid + k * NT) * 16u, amp + base + t_cp + prm.ko[k]);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
   __syncthreads();
@@ -381,13 +400,13 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 3 : 1) : (NTMA
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < NR; j++) v[j] = *reinterpret_cast<const float2 *>(sin + t_ld + prm.lo[j]);
+    for (int j = 0; j < NR; j++) v[j] = lds64(t_ld + prm.lo[j]);
     __syncthreads();  // buf_in is free: prefetch the next tile
     const uint64_t next = tile + gridDim.x;
     const uint64_t base_next = next < n_tiles ? pdep_u64(next, outer_mask) : 0;
     if (next < n_tiles) {
 #pragma unroll
-      for (int k = 0; k < NK; k++) cp_async16(sin + (tid + k * NT) * 16u, amp + base_next + t_cp + prm.ko[k]);
+      for (int k = 0; k < NK; k++) cp_async16_s(sin + (tid + k * NT) * 16u, amp + base_next + t_cp + prm.ko[k]);
       asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
     for (uint32_t s = 0; s < ns; s++) {
@@ -406,7 +425,7 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 3 : 1) : (NTMA
         }
         __syncthreads();  // previous readers of buf_x are done
 #pragma unroll
-        for (int j = 0; j < NR; j++) *reinterpret_cast<float2 *>(sx + (xo[j] ^ PBp)) = v[j];
+        for (int j = 0; j < NR; j++) sts64(sx + (xo[j] ^ PBp), v[j]);
         q = reinterpret_cast<const uint4 *>(st.xo);
 #pragma unroll
         for (int j = 0; j < NR / 4; j++) {
@@ -415,7 +434,7 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 3 : 1) : (NTMA
         }
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < NR; j++) v[j] = *reinterpret_cast<const float2 *>(sx + (xo[j] ^ PB));
+        for (int j = 0; j < NR; j++) v[j] = lds64(sx + (xo[j] ^ PB));
       }
       const uint32_t oe = st.op_end;
       for (uint32_t o = st.op_begin; o < oe; o++) {
