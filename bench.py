@@ -51,9 +51,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 def workload_name():
     return (f"random layered n={N_QUBITS} depth={DEPTH} + QFT-{N_QUBITS} on a seeded basis state; "
             f"FP64 norm, CDF and {SHOTS} shots; <Z> expectation")
-# DRAM bytes of one pass-kernel launch from ncu; None until captured for the
-# current kernel (see profiles/).
-PASS_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) of one pass-kernel launch from an ncu capture of the
+# current kernel, keyed by (n, tile qubits, precision, kernel variant); see profiles/.
+PASS_TRAFFIC_BYTES = {(28, 12, 0, 0): 4233800000}
 
 
 def peaks():
@@ -259,7 +259,8 @@ def run_ours(args, rank, world, local_rank):
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": peak_kind}
     roof.update({"kernel": "pass kernel (one HBM pass over the state)",
-                 "traffic": PASS_TRAFFIC_BYTES,
+                 "traffic": PASS_TRAFFIC_BYTES.get((n, OPTS["tile_qubits"], OPTS["precision"],
+                                                    OPTS.get("kernel_variant", 0))),
                  "algorithmic_bytes_per_launch": 16 * (1 << n),
                  "algorithmic_flops_per_step": flops_pass_step,
                  "hbm_GBps": round(achieved, 1), "hbm_frac": round(achieved / peak, 4),
