@@ -316,17 +316,23 @@ struct RegLayout {
   size_t off_in, off_x, off_seg, off_tt, off_data, total;
 };
 
+// KIND_REG passes with 32 amplitudes per thread load their first stage straight from
+// HBM (no prefetch buffer), so four CTAs fit an SM; register passes keep no segment table.
+__host__ __device__ constexpr bool reg_direct(uint32_t R) { return R == 5; }
+
 __host__ __device__ inline RegLayout reg_layout(uint32_t T, uint32_t c, uint32_t ns, uint32_t data_bytes,
-                                                uint32_t R = 4) {
+                                                uint32_t R = 4, bool reg = false) {
   RegLayout r;
   r.L = 1u << T;
   r.nseg = 1u << (T - c);
   r.NT = 1u << (T - R);
   r.ns = ns;
   size_t o = 0;
-  r.off_in = o; o += size_t(r.L) * 8;
+  r.off_in = o;
+  if (!(reg && reg_direct(R))) o += size_t(r.L) * 8;
   r.off_x = o; o += size_t(r.L) * 8;
-  r.off_seg = o; o += size_t(r.nseg) * 8;
+  r.off_seg = o;
+  if (!reg) o += size_t(r.nseg) * 8;
   r.off_tt = o; o += size_t(ns) * r.NT * 4;
   o = (o + 15) & ~size_t(15);
   r.off_data = o; o += data_bytes;
@@ -338,7 +344,7 @@ __host__ __device__ inline RegLayout reg_layout(uint32_t T, uint32_t c, uint32_t
 // of 256 threads per SM; 32 amplitudes per thread (blocks up to 2 qubits):
 // three CTAs of 128 threads per SM.
 template <int R, int NTMAX>
-__global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 3 : 1) : (NTMAX <= 256 ? 2 : 1))
+__global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 4 : 1) : (NTMAX <= 256 ? 2 : 1))
     k_pass_reg(float2 *__restrict__ amp, const uint8_t *__restrict__ plan, uint32_t pass_off,
                const __grid_constant__ RegPassParams prm) {
   constexpr int NR = 1 << R;
@@ -348,7 +354,8 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 3 : 1) : (NTMA
   const uint32_t ns = P->n_stages;
   const uint32_t data_off = P->ops_off, data_bytes = P->data_bytes;
   const uint64_t outer_mask = P->outer_mask, n_tiles = P->n_tiles;
-  const RegLayout lay = reg_layout(T, c, ns, data_bytes, R);
+  constexpr bool kDirect = reg_direct(R);
+  const RegLayout lay = reg_layout(T, c, ns, data_bytes, R, true);
   float2 *buf_in = reinterpret_cast<float2 *>(smem + lay.off_in);
   float2 *buf_x = reinterpret_cast<float2 *>(smem + lay.off_x);
   uint32_t *tt = reinterpret_cast<uint32_t *>(smem + lay.off_tt);
@@ -385,10 +392,15 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 3 : 1) : (NTMA
     t_st = pdep_u64(LB >> c, hm) + (LB & lowmask);
   }
   const uint64_t t_cp = pdep_u64(tid >> cs, hm) + (uint64_t(tid & cmask) << 1);
+  uint64_t t_gl;
+  {
+    const uint32_t LB = tt[tid] & 0xffffu;
+    t_gl = pdep_u64(LB >> c, hm) + (LB & lowmask);
+  }
 
   uint64_t tile = blockIdx.x;
   uint64_t base = tile < n_tiles ? pdep_u64(tile, outer_mask) : 0;
-  if (tile < n_tiles) {
+  if (!kDirect && tile < n_tiles) {
 #pragma unroll
     for (int k = 0; k < NK; k++) cp_async16_s(sin + (tid + k * NT) * 16u, amp + base + t_cp + prm.ko[k]);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -397,17 +409,24 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 3 : 1) : (NTMA
 
   float2 v[NR];
   while (tile < n_tiles) {
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < NR; j++) v[j] = lds64(t_ld + prm.lo[j]);
-    __syncthreads();  // buf_in is free: prefetch the next tile
     const uint64_t next = tile + gridDim.x;
     const uint64_t base_next = next < n_tiles ? pdep_u64(next, outer_mask) : 0;
-    if (next < n_tiles) {
+    if constexpr (kDirect) {
+      // first stage straight from HBM: lanes hold consecutive amplitudes
+      const float2 *src = amp + base + t_gl;
 #pragma unroll
-      for (int k = 0; k < NK; k++) cp_async16_s(sin + (tid + k * NT) * 16u, amp + base_next + t_cp + prm.ko[k]);
-      asm volatile("cp.async.commit_group;\n" ::: "memory");
+      for (int j = 0; j < NR; j++) v[j] = __ldcs(src + prm.gi[j]);
+    } else {
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < NR; j++) v[j] = lds64(t_ld + prm.lo[j]);
+      __syncthreads();  // buf_in is free: prefetch the next tile
+      if (next < n_tiles) {
+#pragma unroll
+        for (int k = 0; k < NK; k++) cp_async16_s(sin + (tid + k * NT) * 16u, amp + base_next + t_cp + prm.ko[k]);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+      }
     }
     for (uint32_t s = 0; s < ns; s++) {
       const StageRec &st = stages[s];
@@ -461,7 +480,7 @@ constexpr size_t kSmemOptIn = 232448;  // 227 KiB per CTA on sm_100-class parts
 template <int R, int NTMAX>
 static cudaError_t launch_reg(float2 *amp, const uint8_t *plan, uint32_t off, const PlanPass &hp,
                               const RegPassParams &prm, cudaStream_t st) {
-  const RegLayout lay = reg_layout(hp.T, hp.c, hp.n_stages, hp.data_bytes, R);
+  const RegLayout lay = reg_layout(hp.T, hp.c, hp.n_stages, hp.data_bytes, R, true);
   static unsigned long long configured = 0;
   static int sms[64] = {0};
   int dev = 0;
@@ -490,7 +509,7 @@ static cudaError_t launch_reg(float2 *amp, const uint8_t *plan, uint32_t off, co
 // Whether a KIND_REG pass fits the persistent kernel's shared-memory tables.
 bool reg_pass_fits(uint32_t T, uint32_t c, uint32_t R, uint32_t n_stages, uint32_t data_bytes) {
   return (R == 4 || R == 5) && T <= uint32_t(kMaxTile) && T >= R + 5 && n_stages <= uint32_t(kMaxStages) &&
-         data_bytes <= kMaxPassData && reg_layout(T, c, n_stages, data_bytes, R).total <= kSmemOptIn;
+         data_bytes <= kMaxPassData && reg_layout(T, c, n_stages, data_bytes, R, true).total <= kSmemOptIn;
 }
 
 

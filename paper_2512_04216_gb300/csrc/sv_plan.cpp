@@ -723,7 +723,8 @@ static RegPassParams reg_params(const PlanPass &hp, const StageRec &first, const
   const uint32_t NT = 1u << (hp.T - hp.R);
   for (int j = 0; j < (1 << hp.R); j++) {
     p.lo[j] = uint32_t(first.la[j]) * 8u;
-    const uint32_t l = last.la[j];
+    const uint32_t f = first.la[j], l = last.la[j];
+    p.gi[j] = pdep_host(f >> c, hp.high_mask) + (f & lowmask);
     p.go[j] = pdep_host(l >> c, hp.high_mask) + (l & lowmask);
   }
   for (uint32_t k = 0; k < (1u << (hp.R - 1)); k++) p.ko[k] = pdep_host(uint64_t(k) * (NT >> cs), hp.high_mask);
