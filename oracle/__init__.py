@@ -76,6 +76,10 @@ class Oracle:
         L.orc_sample.argtypes = [P, u64, P, u64, ctypes.c_double, P, P]
         L.orc_sample.restype = u64
         L.orc_expect_z.argtypes = [P, u64, u64]
+        L.orc_measure.argtypes = [P, u64, ctypes.c_int, ctypes.c_double, P]
+        L.orc_measure.restype = ctypes.c_int
+        L.orc_reset_qubit.argtypes = [P, u64, ctypes.c_int, ctypes.c_double]
+        L.orc_reset_qubit.restype = ctypes.c_int
         L.orc_expect_z.restype = ctypes.c_double
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_set_threads.restype = None
@@ -149,6 +153,20 @@ class Oracle:
         return float(self.L.orc_expect_z(psi.ctypes.data, psi.shape[0], int(zmask)))
 
 
+    def measure(self, psi, q: int, u: float):
+        """Mid-circuit measurement of qubit q: returns (outcome, prob, collapsed copy)."""
+        psi = np.array(psi, dtype=np.complex128, copy=True)
+        prob = ctypes.c_double()
+        out = self.L.orc_measure(psi.ctypes.data, psi.shape[0], int(q), float(u), ctypes.byref(prob))
+        return int(out), float(prob.value), psi
+
+    def reset_qubit(self, psi, q: int, u: float):
+        """Reset of qubit q to |0> by measurement: returns (outcome, new copy)."""
+        psi = np.array(psi, dtype=np.complex128, copy=True)
+        out = self.L.orc_reset_qubit(psi.ctypes.data, psi.shape[0], int(q), float(u))
+        return int(out), psi
+
+
 def basis(n: int, index: int = 0) -> np.ndarray:
     psi = np.zeros(1 << n, dtype=np.complex128)
     psi[index] = 1.0
@@ -176,6 +194,8 @@ def cdf(psi): return default().cdf(psi)
 def sample(psi, uniforms, eps=1e-9): return default().sample(psi, uniforms, eps)
 def sample_cdf(C, uniforms, eps=1e-9): return default().sample_cdf(C, uniforms, eps)
 def expect_z(psi, zmask): return default().expect_z(psi, zmask)
+def measure(psi, q, u): return default().measure(psi, q, u)
+def reset_qubit(psi, q, u): return default().reset_qubit(psi, q, u)
 
 
 def fidelity(a, b) -> float:

@@ -31,6 +31,15 @@
  *     such i;
  *   - <Z_mask> = sum_i p_i (-1)^popcount(i & mask) / C_{N-1}.
  *
+ * Mid-circuit measurement of one qubit (§III-B: execution up to a
+ * measurement or reset, then per-shot continuation from a copy of the state):
+ *   - m_b = sum of p_i over indices whose bit q equals b (sequential double);
+ *   - with uniform u, the outcome is 0 when u * (m_0 + m_1) < m_0, else 1
+ *     (the same strict rule as the draw above, over the two outcomes);
+ *   - the state collapses: amplitudes with bit q != outcome become 0, the rest
+ *     are multiplied by 1 / sqrt(m_outcome);
+ *   - a reset is that measurement followed by X on q when the outcome is 1.
+ *
  * Parity pinning: see tests/test_oracle_pins.py (closed forms for GHZ and QFT,
  * an explicit DFT matrix, Kronecker-product brute force for n <= 8, textbook
  * gate identities, norm preservation, circuit * inverse = |0...0>, sampler and
@@ -267,4 +276,40 @@ double orc_expect_z(const cplx *psi, uint64_t N, uint64_t zmask) {
     den += p;
   }
   return num / den;
+}
+
+/* Mid-circuit measurement of qubit q with uniform u: collapses psi in place and
+ * returns the outcome; *prob = m_outcome / (m_0 + m_1). */
+int orc_measure(cplx *psi, uint64_t N, int q, double u, double *prob) {
+  const uint64_t bit = (uint64_t)1 << q;
+  double m0 = 0.0, m1 = 0.0;
+  for (uint64_t i = 0; i < N; i++) {
+    double re = creal(psi[i]), im = cimag(psi[i]);
+    double p = re * re + im * im;
+    if (i & bit) m1 += p; else m0 += p;
+  }
+  const int outcome = (u * (m0 + m1) < m0) ? 0 : 1;
+  const double m = outcome ? m1 : m0;
+  const double scale = 1.0 / sqrt(m);
+  for (uint64_t i = 0; i < N; i++) {
+    if (((i & bit) != 0) == outcome) psi[i] *= scale;
+    else psi[i] = 0.0;
+  }
+  if (prob) *prob = m / (m0 + m1);
+  return outcome;
+}
+
+/* Reset of qubit q: measure with u, then flip q when the outcome was 1. */
+int orc_reset_qubit(cplx *psi, uint64_t N, int q, double u) {
+  const int outcome = orc_measure(psi, N, q, u, NULL);
+  if (outcome) {
+    const uint64_t bit = (uint64_t)1 << q;
+    for (uint64_t i = 0; i < N; i++)
+      if (i & bit) {
+        cplx t = psi[i];
+        psi[i] = psi[i ^ bit];
+        psi[i ^ bit] = t;
+      }
+  }
+  return outcome;
 }

@@ -353,5 +353,67 @@ def pin_validate(o):
     assert not o.validate(3, [("u3", (0,), (float("nan"), 0.0, 0.0))]), "NaN accepted"
 
 
+def pin_measure(o):
+    """Mid-circuit measurement and reset against closed forms and a projector
+    built by Kronecker products."""
+    # basis states: deterministic outcome, state unchanged
+    for n, x in ((3, 0b101), (5, 0b10110)):
+        psi = _basis(n, x)
+        for q in range(n):
+            for u in (0.0, 0.37, 0.999):
+                b, p, out = o.measure(psi, q, u)
+                assert b == (x >> q) & 1 and p == 1.0, "basis measurement"
+                _close(out, psi, what="basis collapse")
+    # one qubit U3(θ,φ,λ)|0>: P(1) = sin^2(θ/2), post-measurement states are basis states
+    for th, ph in ((1.1, 0.4), (2.5, -2.0), (0.3, 3.0)):
+        psi = o.run(1, [("u3", (0,), (th, ph, 0.7))])
+        p0 = math.cos(th / 2) ** 2
+        b, p, out = o.measure(psi, 0, p0 - 1e-6)
+        assert b == 0 and abs(p - p0) < 1e-12, "U3 outcome 0"
+        _close(out, np.array([1.0, 0.0]), what="U3 collapse to |0>")
+        b, p, out = o.measure(psi, 0, p0 + 1e-6)
+        assert b == 1 and abs(p - (1 - p0)) < 1e-12, "U3 outcome 1"
+        _close(out, np.array([0.0, np.exp(1j * ph)]), what="U3 collapse to |1> keeps the phase")
+    # GHZ: one measurement fixes every qubit
+    n = 5
+    g = o.run(n, W.ghz(n))
+    for q in range(n):
+        b, p, out = o.measure(g, q, 0.49)
+        assert b == 0 and abs(p - 0.5) < 1e-12
+        _close(out, _basis(n, 0), what="GHZ -> |0..0>")
+        b, p, out = o.measure(g, q, 0.51)
+        assert b == 1
+        _close(out, _basis(n, (1 << n) - 1), what="GHZ -> |1..1>")
+    # projector brute force on random states
+    rng = np.random.default_rng(21)
+    for n in (1, 3, 4):
+        v = random_state(n, rng)
+        for q in range(n):
+            proj = [np.diag([1.0, 0.0]), np.diag([0.0, 1.0])]
+            m = []
+            for b in (0, 1):
+                P = _kron_all([proj[b] if k == q else np.eye(2) for k in range(n - 1, -1, -1)])
+                w = P @ v
+                m.append((float(np.vdot(w, w).real), w))
+            m0, m1 = m[0][0], m[1][0]
+            for u in rng.uniform(0, 1, 6):
+                want = 0 if u * (m0 + m1) < m0 else 1
+                if abs(u * (m0 + m1) - m0) < 1e-9:
+                    continue
+                b, p, out = o.measure(v, q, u)
+                assert b == want, "outcome rule"
+                assert abs(p - m[b][0] / (m0 + m1)) < 1e-12, "outcome probability"
+                _close(out, m[b][1] / math.sqrt(m[b][0]), what="projected state")
+    # reset: |x> -> |x with bit q cleared>; GHZ reset picks a branch then clears it
+    for x, q in ((0b110, 1), (0b110, 0), (0b111, 2)):
+        b, out = o.reset_qubit(_basis(3, x), q, 0.5)
+        assert b == (x >> q) & 1
+        _close(out, _basis(3, x & ~(1 << q)), what="reset of a basis state")
+    b, out = o.reset_qubit(g, 2, 0.9)
+    assert b == 1
+    _close(out, _basis(5, 0b11011), what="reset on GHZ")
+
+
 ALL_PINS = [pin_gate_identities, pin_kron_bruteforce, pin_apply_matrix_k5, pin_ghz, pin_qft,
-            pin_norm_and_mirror, pin_norm_sum, pin_sampler, pin_expectation, pin_validate]
+            pin_norm_and_mirror, pin_norm_sum, pin_sampler, pin_expectation, pin_validate,
+            pin_measure]

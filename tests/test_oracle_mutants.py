@@ -31,6 +31,12 @@ MUTANTS = {
                     "num += (__builtin_popcountll(i & zmask) & 1) ? p : -p;"),
     "expect_unnormalised": ("return num / den;", "return num;"),
     "validate_allows_duplicates": ("if (g[a].q[x] == g[a].q[y]) return -1;", "(void)y;"),
+    "measure_rule_flipped": ("const int outcome = (u * (m0 + m1) < m0) ? 0 : 1;",
+                             "const int outcome = (u * (m0 + m1) < m0) ? 1 : 0;"),
+    "measure_not_renormalised": ("const double scale = 1.0 / sqrt(m);", "const double scale = 1.0;"),
+    "measure_wrong_qubit": ("int orc_measure(cplx *psi, uint64_t N, int q, double u, double *prob) {\n  const uint64_t bit = (uint64_t)1 << q;",
+                            "int orc_measure(cplx *psi, uint64_t N, int q, double u, double *prob) {\n  const uint64_t bit = (uint64_t)1 << (q ^ 1);"),
+    "reset_no_flip": ("  if (outcome) {\n    const uint64_t bit", "  if (0) {\n    const uint64_t bit"),
 }
 
 
