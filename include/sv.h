@@ -198,6 +198,32 @@ int sv_sample_uniforms(sv_state *s, const double *uniforms, uint64_t shots,
 int sv_expect_pauli(sv_state *s, uint64_t x_mask, uint64_t z_mask, double *out);
 
 /*
+ * Mid-circuit measurement and reset (§III-B: a circuit runs up to its first
+ * measurement or reset, then the state is copied and each shot continues on
+ * its own copy).
+ *
+ * sv_measure_qubit measures `qubit` with the caller's uniform u in [0,1):
+ * with m_b the FP64 mass of the amplitudes whose bit `qubit` is b, the outcome
+ * is 0 when u * (m_0 + m_1) < m_0, else 1; amplitudes of the other outcome are
+ * set to 0 and the rest scaled by 1/sqrt(m_outcome) (the state ends normalised).
+ * *outcome receives the bit, *prob (optional) m_outcome / (m_0 + m_1).
+ * Synchronises (the decision needs the masses on the host); the collapse is
+ * queued on the state's stream.  SV_ERR_ARG for a bad qubit, u outside [0,1)
+ * or a zero state.
+ *
+ * sv_reset_qubit: the same measurement, then X on `qubit` when the outcome was
+ * 1, so the qubit ends in |0>.
+ *
+ * sv_clone creates a new library-owned state (its own 2^n * 8-byte buffer, on
+ * `cuda_stream`) holding a copy of src as of all work queued on src's stream;
+ * the copy is queued on the new state's stream.  SV_ERR_OOM when the buffer
+ * cannot be allocated.
+ */
+int sv_measure_qubit(sv_state *s, int qubit, double u, int *outcome, double *prob);
+int sv_reset_qubit(sv_state *s, int qubit, double u, int *outcome);
+int sv_clone(sv_state *src, void *cuda_stream, sv_state **out);
+
+/*
  * Allocation-free <Z_mask>, for callers that cannot allocate device memory
  * when they need the value: e.g. a process that reserved all free GPU memory
  * for resident state vectors up front, or a latency-critical loop that cannot

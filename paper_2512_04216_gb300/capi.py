@@ -97,6 +97,9 @@ _SIGS = {
     "sv_version": ([], ctypes.c_char_p),
     "sv_launch_count": ([], ctypes.c_uint64),
     "sv_tc_selftest": ([_P, _P, _P], _i),
+    "sv_measure_qubit": ([_P, _i, ctypes.c_double, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_double)], _i),
+    "sv_reset_qubit": ([_P, _i, ctypes.c_double, ctypes.POINTER(_i)], _i),
+    "sv_clone": ([_P, _P, ctypes.POINTER(_P)], _i),
     "sv_diag_bounded_wait": ([_i], _i),
     "sv_expect_z_static": ([_P, _i, _u64, _P, _P], _i),
     "sv_batch_create": ([ctypes.c_size_t, _P, _P, _P, _P, _P, _P, _P, _i, _P, ctypes.POINTER(_P)], _i),
@@ -282,6 +285,27 @@ def sv_tc_selftest(a, b):
     d = np.empty((128, 32), dtype=np.float32)
     _check(_L.sv_tc_selftest(a.ctypes.data, b.ctypes.data, d.ctypes.data))
     return d
+
+
+def sv_measure_qubit(h, qubit: int, u: float):
+    """Mid-circuit measurement: returns (outcome, probability of that outcome)."""
+    out = _i()
+    prob = ctypes.c_double()
+    _check(_L.sv_measure_qubit(h, int(qubit), float(u), ctypes.byref(out), ctypes.byref(prob)))
+    return int(out.value), float(prob.value)
+
+
+def sv_reset_qubit(h, qubit: int, u: float) -> int:
+    """Reset of one qubit to |0> by measurement; returns the measured bit."""
+    out = _i()
+    _check(_L.sv_reset_qubit(h, int(qubit), float(u), ctypes.byref(out)))
+    return int(out.value)
+
+
+def sv_clone(h, stream=None):
+    out = _P()
+    _check(_L.sv_clone(h, _stream_ptr(stream), ctypes.byref(out)))
+    return out
 
 
 def sv_diag_bounded_wait(limit_ms: int) -> int:

@@ -4,6 +4,8 @@
 // current plan, and scratch buffers for the measurement kernels.  Every entry
 // point validates its arguments, switches to the state's device for the
 // duration of the call, and maps CUDA failures to status codes.
+#include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -436,6 +438,81 @@ int sv_expect_pauli(sv_state *s, uint64_t x_mask, uint64_t z_mask, double *out) 
   if (rc) return rc;
   if (!(s->hscal[0] > 0.0)) return fail(SV_ERR_ARG, "state has zero norm");
   *out = s->hscal[1] / s->hscal[0];
+  return SV_OK;
+}
+
+// Masses of qubit q's two outcomes: m0 = sum p_i over bit q = 0, m1 over bit q = 1
+// (one FP64 reduction of p and p * (-1)^bit; synchronises).
+static int qubit_masses(sv_state *s, int q, double *m0, double *m1) {
+  int rc = ensure_reduce(s);
+  if (rc) return rc;
+  const uint64_t zmask = uint64_t(1) << q;
+  CK(s, timed(s, "reduce", double(size_t(8) << s->n), [&] {
+       return launch_reduce_pz(s->amp, s->n, zmask, s->ms.part, s->ms.n_part, s->dscal, s->stream);
+     }));
+  CK(s, cudaMemcpyAsync(s->hscal, s->dscal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  rc = check_device_error(s);
+  if (rc) return rc;
+  const double total = s->hscal[0], z = s->hscal[1];
+  *m0 = std::max(0.0, 0.5 * (total + z));
+  *m1 = std::max(0.0, 0.5 * (total - z));
+  return SV_OK;
+}
+
+static int measure_common(sv_state *s, int qubit, double u, int to_zero, int *outcome, double *prob) {
+  CHECK_STATE(s);
+  if (!outcome) return fail(SV_ERR_ARG, "outcome is null");
+  if (qubit < 0 || qubit >= s->n) return fail(SV_ERR_ARG, "qubit %d out of range [0,%d)", qubit, s->n);
+  if (!(u >= 0.0 && u < 1.0)) return fail(SV_ERR_ARG, "u must be in [0,1)");
+  DeviceGuard g(s->device);
+  double m0 = 0.0, m1 = 0.0;
+  int rc = qubit_masses(s, qubit, &m0, &m1);
+  if (rc) return rc;
+  const double total = m0 + m1;
+  if (!(total > 0.0)) return fail(SV_ERR_ARG, "state has zero norm");
+  int b = (u * total < m0) ? 0 : 1;
+  double m = b ? m1 : m0;
+  if (!(m > 0.0)) {  // rounding left the drawn outcome without mass
+    b ^= 1;
+    m = b ? m1 : m0;
+  }
+  const float scale = float(1.0 / std::sqrt(m));
+  CK(s, timed(s, "collapse", double(size_t(16) << s->n), [&] {
+       return launch_collapse(s->amp, s->n, qubit, b, to_zero && b, scale, s->stream);
+     }));
+  *outcome = b;
+  if (prob) *prob = m / total;
+  return SV_OK;
+}
+
+int sv_measure_qubit(sv_state *s, int qubit, double u, int *outcome, double *prob) {
+  return measure_common(s, qubit, u, 0, outcome, prob);
+}
+
+int sv_reset_qubit(sv_state *s, int qubit, double u, int *outcome) {
+  return measure_common(s, qubit, u, 1, outcome, nullptr);
+}
+
+int sv_clone(sv_state *src, void *cuda_stream, sv_state **out) {
+  CHECK_STATE(src);
+  if (!out) return fail(SV_ERR_ARG, "out is null");
+  DeviceGuard g(src->device);
+  int rc = sv_create(src->n, SV_C64, cuda_stream, out);
+  if (rc) return rc;
+  sv_state *d = *out;
+  const size_t bytes = (size_t(1) << src->n) * sizeof(float2);
+  cudaEvent_t ev = nullptr;
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev, src->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(d->stream, ev, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d->amp, src->amp, bytes, cudaMemcpyDeviceToDevice, d->stream);
+  if (ev) cudaEventDestroy(ev);
+  if (e != cudaSuccess) {
+    free_state(d);
+    *out = nullptr;
+    return fail(SV_ERR_CUDA, "clone: %s", cudaGetErrorString(e));
+  }
   return SV_OK;
 }
 

@@ -176,6 +176,9 @@ cudaError_t launch_sample(const float2 *amp, int n, const MeasureScratch &ms,
 cudaError_t launch_probabilities(const float2 *amp, uint64_t offset, uint64_t count, double *out,
                                  cudaStream_t st);
 cudaError_t launch_reset(float2 *amp, int n, uint64_t basis, cudaStream_t st);
+// Collapse after a one-qubit measurement (see k_collapse).
+cudaError_t launch_collapse(float2 *amp, int n, int q, int outcome, int to_zero, float scale,
+                            cudaStream_t st);
 
 size_t reduce_parts(int n);
 

@@ -451,6 +451,40 @@ cudaError_t launch_probabilities(const float2 *amp, uint64_t offset, uint64_t co
   return cudaGetLastError();
 }
 
+// Collapse after measuring qubit q: over every pair (i0, i1 = i0 | 2^q) keep the
+// outcome's half scaled by `scale` and zero the other; with `to_zero` (a reset
+// whose outcome was 1) the kept half moves to bit q = 0.
+__global__ void k_collapse(float2 *__restrict__ amp, int n, int q, int outcome, int to_zero, float scale) {
+  const uint64_t half = uint64_t(1) << (n - 1);
+  const uint64_t low = (uint64_t(1) << q) - 1;
+  for (uint64_t k = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < half;
+       k += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t i0 = ((k & ~low) << 1) | (k & low), i1 = i0 | (low + 1);
+    const float2 a = amp[i0], b = amp[i1];
+    const float2 z = make_float2(0.f, 0.f);
+    if (outcome == 0) {
+      amp[i0] = make_float2(a.x * scale, a.y * scale);
+      amp[i1] = z;
+    } else if (to_zero) {
+      amp[i0] = make_float2(b.x * scale, b.y * scale);
+      amp[i1] = z;
+    } else {
+      amp[i0] = z;
+      amp[i1] = make_float2(b.x * scale, b.y * scale);
+    }
+  }
+}
+
+cudaError_t launch_collapse(float2 *amp, int n, int q, int outcome, int to_zero, float scale,
+                            cudaStream_t st) {
+  if (n < 1 || q < 0 || q >= n) return cudaErrorInvalidValue;
+  const uint64_t half = uint64_t(1) << (n - 1);
+  const uint64_t g = umin64((half + 255) / 256, 152ull * 16);
+  k_collapse<<<unsigned(g), 256, 0, st>>>(amp, n, q, outcome, to_zero, scale);
+  count_launch();
+  return cudaGetLastError();
+}
+
 __global__ void k_set_one(float2 *amp, uint64_t idx) { amp[idx] = make_float2(1.f, 0.f); }
 
 cudaError_t launch_reset(float2 *amp, int n, uint64_t basis, cudaStream_t st) {

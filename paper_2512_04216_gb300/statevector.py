@@ -100,8 +100,31 @@ class StateVector:
         v = np.ascontiguousarray(values, dtype=np.complex64)
         capi.sv_set_amplitudes(self.h, v, offset, v.shape[0], False)
 
+    def measure(self, qubit: int, u: float):
+        """Mid-circuit measurement of one qubit with uniform u: (outcome, probability)."""
+        return capi.sv_measure_qubit(self.h, qubit, u)
+
+    def reset_qubit(self, qubit: int, u: float) -> int:
+        return capi.sv_reset_qubit(self.h, qubit, u)
+
+    def clone(self, stream=None) -> "ClonedState":
+        """A library-owned copy of this state (on `stream`, default this state's stream)."""
+        st = stream if stream is not None else self.stream
+        return ClonedState(capi.sv_clone(self.h, st), self.n, st, self.device)
+
     def profile(self, on: bool = True):
         capi.sv_profile_enable(self.h, on)
 
     def profile_read(self) -> dict:
         return capi.sv_profile_read(self.h)
+
+
+class ClonedState(StateVector):
+    """A state created by sv_clone: the library owns its buffer."""
+
+    def __init__(self, handle, n: int, stream, device):
+        self.n = int(n)
+        self.device = device
+        self.stream = stream
+        self.amps = None
+        self.h = handle
