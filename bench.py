@@ -414,6 +414,71 @@ def run_batch_mode(args):
     }
 
 
+def run_dynamic_mode(args):
+    """Per-shot trajectories with mid-circuit measurement (§III-B): a 28-qubit
+    random prefix (depth 20) runs once; each trajectory clones the state,
+    measures qubits 3 and 17, resets qubit 25, applies a depth-2 suffix and
+    draws one bitstring.  Reports trajectories/s and the collapse kernel's HBM
+    rate (16 B per amplitude: read and write once)."""
+    import torch
+    from paper_2512_04216_gb300 import StateVector, capi
+    n = 28
+    traj = 8
+    prefix, suffix = W.random_layered(n, 20, 31), W.random_layered(n, 2, 32)
+    s = StateVector(n)
+    s.apply(prefix)
+    torch.cuda.synchronize()
+    u = W.shot_uniforms(33, 4 * traj * (args.steps + args.warmup))
+    peak, peak_kind = peaks()
+    prof_tot = {}
+
+    def trajectory(k, prof):
+        c = s.clone()
+        if prof:
+            capi.sv_profile_enable(c.h, True)
+        c.measure(3, float(u[4 * k]))
+        c.measure(17, float(u[4 * k + 1]))
+        c.reset_qubit(25, float(u[4 * k + 2]))
+        c.apply(suffix)
+        c.sample_uniforms(np.array([u[4 * k + 3]]))
+        if prof:
+            for name, v in capi.sv_profile_read(c.h).items():
+                t = prof_tot.setdefault(name, {"launches": 0, "ms": 0.0, "bytes": 0.0})
+                for key in t:
+                    t[key] += v[key]
+        c.close()
+
+    k = 0
+    for _ in range(args.warmup):
+        for _ in range(traj):
+            trajectory(k, False)
+            k += 1
+    torch.cuda.synchronize()
+    launches0 = capi.sv_launch_count()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for _ in range(traj):
+            trajectory(k, True)
+            k += 1
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    s.close()
+    col = prof_tot.get("collapse", {"launches": 0, "ms": float("nan"), "bytes": 0.0})
+    col_gbs = col["bytes"] / (col["ms"] * 1e-3) / 1e9 if col["launches"] else float("nan")
+    return {
+        "metric": "mid-circuit trajectories/s", "value": args.steps * traj / dt, "unit": "trajectories/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": f"n={n} random prefix depth 20 once; per trajectory: clone (2 GiB), measure 2 qubits, "
+                               f"reset 1, suffix depth 2, 1 shot; {traj} trajectories per step"},
+        "roofline": {"bound": "hbm", "kernel": "k_collapse", "achieved": round(col_gbs, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(col_gbs / peak, 4), "peak_source": peak_kind,
+                     "algorithmic_bytes_per_launch": 16 * (1 << n), "traffic": None},
+        "kernels": {k2: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k2, v in prof_tot.items()},
+        "gpu_launches": int(capi.sv_launch_count() - launches0),
+    }
+
+
 def run_serve_mode(args):
     """Config: Poisson stream of random layered circuits, n geometric-skewed on
     8..30 (mean ~16), depth ~ U{10..100}, 1000 shots or a Z-string mask; served
@@ -458,9 +523,10 @@ def main():
     ap.add_argument("--kernel-variant", type=int, default=0)
     ap.add_argument("--precision", type=int, default=OPTS["precision"],
                     help="0: FP32 CUDA cores; 1: 3xTF32 tensor-core stage products")
-    ap.add_argument("--workload", choices=["statevector", "large", "batch", "serve"], default="statevector",
+    ap.add_argument("--workload", choices=["statevector", "large", "batch", "serve", "dynamic"], default="statevector",
                     help="statevector: the bench line; large: the 34-qubit (128 GiB) single state, "
-                         "depth 30, 1e6 shots; batch / serve: the batched and serving patterns")
+                         "depth 30, 1e6 shots; batch / serve: the batched and serving patterns; "
+                         "dynamic: per-shot trajectories with mid-circuit measurement")
     ap.add_argument("--batch-circuits", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate-factors", default="0.5,1,2,4")
@@ -479,9 +545,9 @@ def main():
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
         return
-    if args.workload in ("batch", "serve"):
+    if args.workload in ("batch", "serve", "dynamic"):
         if rank == 0:
-            fn = run_batch_mode if args.workload == "batch" else run_serve_mode
+            fn = {"batch": run_batch_mode, "serve": run_serve_mode, "dynamic": run_dynamic_mode}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
 

@@ -56,6 +56,19 @@ __device__ __forceinline__ double cs_to_double(float s, float c) {
   return double(s) + double(c);
 }
 
+// Warp sum of compensated pairs (s, c), result in lane 0: the pairs' partial
+// sums stay compensated float32 (relative error ~2^-44 for 32 terms); GB300
+// runs float64 at a small fraction of the float32 rate, so only lane 0
+// converts to double.
+__device__ __forceinline__ void warp_acc_pair(float &s, float &c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_down_sync(0xffffffffu, s, o);
+    const float c2 = __shfl_down_sync(0xffffffffu, c, o);
+    acc_pair(s, c, s2, c2);
+  }
+}
+
 // ---- staged load of a CTA's 4096 amplitudes ------------------------------
 __device__ __forceinline__ void cp_async16m(void *smem_dst, const void *gsrc) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
@@ -118,16 +131,12 @@ __global__ void __launch_bounds__(kRT) k_reduce_pz(const float2 *__restrict__ am
   stage_load(tile, amp, start, cnt);
   float ps, pc, zs, zc;
   thread_sums(tile, cnt, start, zmask, ps, pc, zs, zc);
-  double p = cs_to_double(ps, pc), z = cs_to_double(zs, zc);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    p += __shfl_down_sync(0xffffffffu, p, o);
-    z += __shfl_down_sync(0xffffffffu, z, o);
-  }
+  warp_acc_pair(ps, pc);
+  warp_acc_pair(zs, zc);
   const int w = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
-    red[0][w] = p;
-    red[1][w] = z;
+    red[0][w] = cs_to_double(ps, pc);
+    red[1][w] = cs_to_double(zs, zc);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -456,30 +465,47 @@ cudaError_t launch_probabilities(const float2 *amp, uint64_t offset, uint64_t co
 // whose outcome was 1) the kept half moves to bit q = 0.
 __global__ void k_collapse(float2 *__restrict__ amp, int n, int q, int outcome, int to_zero, float scale) {
   const uint64_t half = uint64_t(1) << (n - 1);
-  const uint64_t low = (uint64_t(1) << q) - 1;
-  for (uint64_t k = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < half;
-       k += uint64_t(gridDim.x) * blockDim.x) {
-    const uint64_t i0 = ((k & ~low) << 1) | (k & low), i1 = i0 | (low + 1);
-    const float2 a = amp[i0], b = amp[i1];
-    const float2 z = make_float2(0.f, 0.f);
-    if (outcome == 0) {
-      amp[i0] = make_float2(a.x * scale, a.y * scale);
-      amp[i1] = z;
-    } else if (to_zero) {
-      amp[i0] = make_float2(b.x * scale, b.y * scale);
-      amp[i1] = z;
-    } else {
-      amp[i0] = z;
-      amp[i1] = make_float2(b.x * scale, b.y * scale);
+  const float2 z = make_float2(0.f, 0.f);
+  auto keep = [&](float2 a) { return make_float2(a.x * scale, a.y * scale); };
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  if (q == 0) {
+    // i0 and i1 are adjacent: one 16-byte access per pair
+    float4 *a4 = reinterpret_cast<float4 *>(amp);
+    for (uint64_t k = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < half; k += stride) {
+      const float4 v = a4[k];
+      const float2 a = make_float2(v.x, v.y), b = make_float2(v.z, v.w);
+      float2 r0, r1;
+      if (outcome == 0) { r0 = keep(a); r1 = z; }
+      else if (to_zero) { r0 = keep(b); r1 = z; }
+      else { r0 = z; r1 = keep(b); }
+      a4[k] = make_float4(r0.x, r0.y, r1.x, r1.y);
     }
+    return;
+  }
+  // q >= 1: two consecutive pairs (i0, i0 + 1) and (i1, i1 + 1), 16 bytes each
+  const uint64_t low = (uint64_t(1) << q) - 1;
+  for (uint64_t k2 = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; k2 < (half >> 1); k2 += stride) {
+    const uint64_t k = k2 << 1;
+    const uint64_t i0 = ((k & ~low) << 1) | (k & low), i1 = i0 | (low + 1);
+    float4 *p0 = reinterpret_cast<float4 *>(amp + i0), *p1 = reinterpret_cast<float4 *>(amp + i1);
+    const float4 A = *p0, B = *p1;
+    const float2 a0 = make_float2(A.x, A.y), a1 = make_float2(A.z, A.w);
+    const float2 b0 = make_float2(B.x, B.y), b1 = make_float2(B.z, B.w);
+    float2 r00, r01, r10, r11;
+    if (outcome == 0) { r00 = keep(a0); r01 = keep(a1); r10 = z; r11 = z; }
+    else if (to_zero) { r00 = keep(b0); r01 = keep(b1); r10 = z; r11 = z; }
+    else { r00 = z; r01 = z; r10 = keep(b0); r11 = keep(b1); }
+    *p0 = make_float4(r00.x, r00.y, r01.x, r01.y);
+    *p1 = make_float4(r10.x, r10.y, r11.x, r11.y);
   }
 }
 
 cudaError_t launch_collapse(float2 *amp, int n, int q, int outcome, int to_zero, float scale,
                             cudaStream_t st) {
   if (n < 1 || q < 0 || q >= n) return cudaErrorInvalidValue;
-  const uint64_t half = uint64_t(1) << (n - 1);
-  const uint64_t g = umin64((half + 255) / 256, 152ull * 16);
+  const uint64_t units = (uint64_t(1) << (n - 1)) >> (q == 0 ? 0 : 1);
+  const uint64_t g = umin64((units + 255) / 256, 152ull * 16);
+  if (units == 0) return cudaSuccess;
   k_collapse<<<unsigned(g), 256, 0, st>>>(amp, n, q, outcome, to_zero, scale);
   count_launch();
   return cudaGetLastError();
