@@ -80,6 +80,10 @@ class Oracle:
         L.orc_measure.restype = ctypes.c_int
         L.orc_reset_qubit.argtypes = [P, u64, ctypes.c_int, ctypes.c_double]
         L.orc_reset_qubit.restype = ctypes.c_int
+        L.orc_kron.argtypes = [P, ctypes.c_int, P, ctypes.c_int, P]
+        L.orc_kron.restype = None
+        L.orc_take_qubit.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+        L.orc_take_qubit.restype = None
         L.orc_expect_z.restype = ctypes.c_double
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_set_threads.restype = None
@@ -167,6 +171,24 @@ class Oracle:
         return int(out), psi
 
 
+    def kron(self, a, b):
+        """Merged register a (x) b, a on the low qubits."""
+        a = np.ascontiguousarray(a, dtype=np.complex128)
+        b = np.ascontiguousarray(b, dtype=np.complex128)
+        na, nb = a.shape[0].bit_length() - 1, b.shape[0].bit_length() - 1
+        out = np.empty(a.shape[0] * b.shape[0], dtype=np.complex128)
+        self.L.orc_kron(a.ctypes.data, na, b.ctypes.data, nb, out.ctypes.data)
+        return out
+
+    def take_qubit(self, psi, q: int, v: int):
+        """Register without qubit q, which must be in the basis state |v>."""
+        psi = np.ascontiguousarray(psi, dtype=np.complex128)
+        n = psi.shape[0].bit_length() - 1
+        out = np.empty(psi.shape[0] // 2, dtype=np.complex128)
+        self.L.orc_take_qubit(psi.ctypes.data, n, int(q), int(v), out.ctypes.data)
+        return out
+
+
 def basis(n: int, index: int = 0) -> np.ndarray:
     psi = np.zeros(1 << n, dtype=np.complex128)
     psi[index] = 1.0
@@ -196,6 +218,8 @@ def sample_cdf(C, uniforms, eps=1e-9): return default().sample_cdf(C, uniforms, 
 def expect_z(psi, zmask): return default().expect_z(psi, zmask)
 def measure(psi, q, u): return default().measure(psi, q, u)
 def reset_qubit(psi, q, u): return default().reset_qubit(psi, q, u)
+def kron(a, b): return default().kron(a, b)
+def take_qubit(psi, q, v): return default().take_qubit(psi, q, v)
 
 
 def fidelity(a, b) -> float:

@@ -40,6 +40,13 @@
  *     are multiplied by 1 / sqrt(m_outcome);
  *   - a reset is that measurement followed by X on q when the outcome is 1.
  *
+ * Partitioned blocks (§II p-block simulation; §III-E: registers merge when
+ * they first interact and communication qubits leave after measurement):
+ *   - merging registers A (n_a qubits) and B (n_b qubits) gives A (x) B with A
+ *     on the low qubits: out[i_b * 2^n_a + i_a] = b[i_b] * a[i_a];
+ *   - a qubit q known to be in the basis state |v> (e.g. just measured) leaves
+ *     the register: out[j] = psi[j with bit v inserted at position q].
+ *
  * Parity pinning: see tests/test_oracle_pins.py (closed forms for GHZ and QFT,
  * an explicit DFT matrix, Kronecker-product brute force for n <= 8, textbook
  * gate identities, norm preservation, circuit * inverse = |0...0>, sampler and
@@ -312,4 +319,21 @@ int orc_reset_qubit(cplx *psi, uint64_t N, int q, double u) {
       }
   }
   return outcome;
+}
+
+/* Merge of two registers: out (2^(na+nb) entries) = a (x) b, a on the low qubits. */
+void orc_kron(const cplx *a, int na, const cplx *b, int nb, cplx *out) {
+  const uint64_t Na = (uint64_t)1 << na, Nb = (uint64_t)1 << nb;
+  for (uint64_t ib = 0; ib < Nb; ib++)
+    for (uint64_t ia = 0; ia < Na; ia++) out[ib * Na + ia] = b[ib] * a[ia];
+}
+
+/* Qubit q in the basis state |v> leaves the n-qubit register: out has 2^(n-1) entries. */
+void orc_take_qubit(const cplx *psi, int n, int q, int v, cplx *out) {
+  const uint64_t half = (uint64_t)1 << (n - 1);
+  const uint64_t low = ((uint64_t)1 << q) - 1;
+  for (uint64_t j = 0; j < half; j++) {
+    const uint64_t i = ((j & ~low) << 1) | (j & low) | ((uint64_t)v << q);
+    out[j] = psi[i];
+  }
 }

@@ -414,6 +414,33 @@ def pin_measure(o):
     _close(out, _basis(5, 0b11011), what="reset on GHZ")
 
 
+def pin_pblock(o):
+    """Register merge against numpy's Kronecker product (b on the high qubits is
+    np.kron(b, a) in little-endian order) and against running the gates of both
+    registers on the merged state; taking a basis-state qubit out undoes a merge
+    with |v> and matches a measured register's nonzero half."""
+    rng = np.random.default_rng(31)
+    for na, nb in ((1, 1), (2, 3), (4, 2)):
+        a, b = random_state(na, rng), random_state(nb, rng)
+        _close(o.kron(a, b), np.kron(b, a), what="kron vs numpy")
+    ca = W.random_layered(3, 3, 1)
+    cb = W.random_layered(2, 3, 2)
+    merged = o.kron(o.run(3, ca), o.run(2, cb))
+    shifted = [(g, tuple(q + 3 for q in qs), p) for g, qs, p in cb]
+    _close(merged, o.run(5, ca + shifted), what="merged registers = monolithic run")
+    for n, q, v in ((4, 0, 1), (4, 2, 0), (5, 4, 1)):
+        rest = random_state(n - 1, rng)
+        # insert qubit q in |v>: merge with the one-qubit state, then move it to position q
+        full = np.zeros(1 << n, dtype=np.complex128)
+        for j in range(1 << (n - 1)):
+            low = j & ((1 << q) - 1)
+            full[((j >> q) << (q + 1)) | (v << q) | low] = rest[j]
+        _close(o.take_qubit(full, q, v), rest, what="take a basis-state qubit")
+    g = o.run(4, W.ghz(4))
+    b, _, post = o.measure(g, 1, 0.8)
+    _close(o.take_qubit(post, 1, b), _basis(3, 0b111), what="take a measured GHZ qubit")
+
+
 ALL_PINS = [pin_gate_identities, pin_kron_bruteforce, pin_apply_matrix_k5, pin_ghz, pin_qft,
             pin_norm_and_mirror, pin_norm_sum, pin_sampler, pin_expectation, pin_validate,
-            pin_measure]
+            pin_measure, pin_pblock]

@@ -37,6 +37,8 @@ MUTANTS = {
     "measure_wrong_qubit": ("int orc_measure(cplx *psi, uint64_t N, int q, double u, double *prob) {\n  const uint64_t bit = (uint64_t)1 << q;",
                             "int orc_measure(cplx *psi, uint64_t N, int q, double u, double *prob) {\n  const uint64_t bit = (uint64_t)1 << (q ^ 1);"),
     "reset_no_flip": ("  if (outcome) {\n    const uint64_t bit", "  if (0) {\n    const uint64_t bit"),
+    "kron_operands_swapped": ("out[ib * Na + ia] = b[ib] * a[ia];", "out[ia * Nb + ib] = b[ib] * a[ia];"),
+    "take_wrong_half": ("| ((uint64_t)v << q);", "| ((uint64_t)(1 - v) << q);"),
 }
 
 
