@@ -224,6 +224,27 @@ int sv_reset_qubit(sv_state *s, int qubit, double u, int *outcome);
 int sv_clone(sv_state *src, void *cuda_stream, sv_state **out);
 
 /*
+ * Partitioned blocks (§II p-block simulation; §III-E: registers merge when
+ * their qubits first interact, communication qubits leave once measured).
+ *
+ * sv_merge creates a new (n_a + n_b)-qubit state a (x) b: a's qubits become
+ * qubits 0..n_a-1 and b's become n_a..n_a+n_b-1, out[i_b * 2^n_a + i_a] =
+ * b[i_b] * a[i_a].  Queued on `cuda_stream` after all work queued on a's and
+ * b's streams; a and b are unchanged and stay valid.  SV_ERR_ARG past 36
+ * qubits or across devices, SV_ERR_OOM without room for the result.
+ *
+ * sv_take_qubit removes `qubit` from a register in which it is in a basis
+ * state |v> (e.g. right after sv_measure_qubit / sv_reset_qubit): the new
+ * (n-1)-qubit state holds psi[j with bit v inserted at `qubit`], the remaining
+ * qubits renumbered downwards.  *value receives v.  The masses of both halves
+ * are computed first (synchronises); if the smaller one exceeds tol times the
+ * total (tol in [0, 0.5)) the qubit is entangled or in superposition and
+ * SV_ERR_ARG is returned.  s is unchanged.
+ */
+int sv_merge(sv_state *a, sv_state *b, void *cuda_stream, sv_state **out);
+int sv_take_qubit(sv_state *s, int qubit, double tol, int *value, sv_state **out);
+
+/*
  * Allocation-free <Z_mask>, for callers that cannot allocate device memory
  * when they need the value: e.g. a process that reserved all free GPU memory
  * for resident state vectors up front, or a latency-critical loop that cannot

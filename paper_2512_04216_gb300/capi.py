@@ -100,6 +100,8 @@ _SIGS = {
     "sv_measure_qubit": ([_P, _i, ctypes.c_double, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_double)], _i),
     "sv_reset_qubit": ([_P, _i, ctypes.c_double, ctypes.POINTER(_i)], _i),
     "sv_clone": ([_P, _P, ctypes.POINTER(_P)], _i),
+    "sv_merge": ([_P, _P, _P, ctypes.POINTER(_P)], _i),
+    "sv_take_qubit": ([_P, _i, ctypes.c_double, ctypes.POINTER(_i), ctypes.POINTER(_P)], _i),
     "sv_diag_bounded_wait": ([_i], _i),
     "sv_expect_z_static": ([_P, _i, _u64, _P, _P], _i),
     "sv_batch_create": ([ctypes.c_size_t, _P, _P, _P, _P, _P, _P, _P, _i, _P, ctypes.POINTER(_P)], _i),
@@ -306,6 +308,20 @@ def sv_clone(h, stream=None):
     out = _P()
     _check(_L.sv_clone(h, _stream_ptr(stream), ctypes.byref(out)))
     return out
+
+
+def sv_merge(a, b, stream=None):
+    out = _P()
+    _check(_L.sv_merge(a, b, _stream_ptr(stream), ctypes.byref(out)))
+    return out
+
+
+def sv_take_qubit(h, qubit: int, tol: float = 1e-6):
+    """Removes a basis-state qubit: returns (new handle, its value)."""
+    out = _P()
+    v = _i()
+    _check(_L.sv_take_qubit(h, int(qubit), float(tol), ctypes.byref(v), ctypes.byref(out)))
+    return out, int(v.value)
 
 
 def sv_diag_bounded_wait(limit_ms: int) -> int:

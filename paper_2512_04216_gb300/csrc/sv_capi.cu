@@ -494,6 +494,17 @@ int sv_reset_qubit(sv_state *s, int qubit, double u, int *outcome) {
   return measure_common(s, qubit, u, 1, outcome, nullptr);
 }
 
+// Orders `dst`'s stream after all work queued on `src`'s stream.
+static cudaError_t stream_after(cudaStream_t dst, cudaStream_t src) {
+  if (dst == src) return cudaSuccess;
+  cudaEvent_t ev = nullptr;
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev, src);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(dst, ev, 0);
+  if (ev) cudaEventDestroy(ev);
+  return e;
+}
+
 int sv_clone(sv_state *src, void *cuda_stream, sv_state **out) {
   CHECK_STATE(src);
   if (!out) return fail(SV_ERR_ARG, "out is null");
@@ -502,17 +513,66 @@ int sv_clone(sv_state *src, void *cuda_stream, sv_state **out) {
   if (rc) return rc;
   sv_state *d = *out;
   const size_t bytes = (size_t(1) << src->n) * sizeof(float2);
-  cudaEvent_t ev = nullptr;
-  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventRecord(ev, src->stream);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(d->stream, ev, 0);
+  cudaError_t e = stream_after(d->stream, src->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d->amp, src->amp, bytes, cudaMemcpyDeviceToDevice, d->stream);
-  if (ev) cudaEventDestroy(ev);
   if (e != cudaSuccess) {
     free_state(d);
     *out = nullptr;
     return fail(SV_ERR_CUDA, "clone: %s", cudaGetErrorString(e));
   }
+  return SV_OK;
+}
+
+int sv_merge(sv_state *a, sv_state *b, void *cuda_stream, sv_state **out) {
+  CHECK_STATE(a);
+  CHECK_STATE(b);
+  if (!out) return fail(SV_ERR_ARG, "out is null");
+  if (a->device != b->device) return fail(SV_ERR_ARG, "registers live on different devices");
+  if (a->n + b->n > 36) return fail(SV_ERR_ARG, "merged register would exceed 36 qubits");
+  DeviceGuard g(a->device);
+  int rc = sv_create(a->n + b->n, SV_C64, cuda_stream, out);
+  if (rc) return rc;
+  sv_state *d = *out;
+  cudaError_t e = stream_after(d->stream, a->stream);
+  if (e == cudaSuccess) e = stream_after(d->stream, b->stream);
+  if (e == cudaSuccess)
+    e = timed(d, "merge", double(size_t(8) << d->n),
+              [&] { return launch_kron(a->amp, a->n, b->amp, b->n, d->amp, d->stream); });
+  if (e != cudaSuccess) {
+    free_state(d);
+    *out = nullptr;
+    return fail(SV_ERR_CUDA, "merge: %s", cudaGetErrorString(e));
+  }
+  return SV_OK;
+}
+
+int sv_take_qubit(sv_state *s, int qubit, double tol, int *value, sv_state **out) {
+  CHECK_STATE(s);
+  if (!out || !value) return fail(SV_ERR_ARG, "out/value is null");
+  if (s->n < 2) return fail(SV_ERR_ARG, "a register keeps at least one qubit");
+  if (qubit < 0 || qubit >= s->n) return fail(SV_ERR_ARG, "qubit %d out of range [0,%d)", qubit, s->n);
+  if (!(tol >= 0.0 && tol < 0.5)) return fail(SV_ERR_ARG, "tol must be in [0, 0.5)");
+  DeviceGuard g(s->device);
+  double m0 = 0.0, m1 = 0.0;
+  int rc = qubit_masses(s, qubit, &m0, &m1);
+  if (rc) return rc;
+  const double total = m0 + m1;
+  if (!(total > 0.0)) return fail(SV_ERR_ARG, "state has zero norm");
+  const int v = (m1 > m0) ? 1 : 0;
+  if ((v ? m0 : m1) > tol * total)
+    return fail(SV_ERR_ARG, "qubit %d is not in a basis state (minority mass %.3g of %.3g)", qubit,
+                v ? m0 : m1, total);
+  rc = sv_create(s->n - 1, SV_C64, s->stream, out);
+  if (rc) return rc;
+  sv_state *d = *out;
+  cudaError_t e = timed(d, "take", double(size_t(8) << s->n),
+                        [&] { return launch_take(s->amp, s->n, qubit, v, d->amp, d->stream); });
+  if (e != cudaSuccess) {
+    free_state(d);
+    *out = nullptr;
+    return fail(SV_ERR_CUDA, "take: %s", cudaGetErrorString(e));
+  }
+  *value = v;
   return SV_OK;
 }
 

@@ -176,6 +176,10 @@ cudaError_t launch_sample(const float2 *amp, int n, const MeasureScratch &ms,
 cudaError_t launch_probabilities(const float2 *amp, uint64_t offset, uint64_t count, double *out,
                                  cudaStream_t st);
 cudaError_t launch_reset(float2 *amp, int n, uint64_t basis, cudaStream_t st);
+// Partitioned blocks (sv_pblock.cu): out = a (x) b (a on the low qubits), and
+// removal of qubit q known to be in |v>.
+cudaError_t launch_kron(const float2 *a, int na, const float2 *b, int nb, float2 *out, cudaStream_t st);
+cudaError_t launch_take(const float2 *psi, int n, int q, int v, float2 *out, cudaStream_t st);
 // Collapse after a one-qubit measurement (see k_collapse).
 cudaError_t launch_collapse(float2 *amp, int n, int q, int outcome, int to_zero, float scale,
                             cudaStream_t st);

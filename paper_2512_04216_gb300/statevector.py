@@ -112,6 +112,16 @@ class StateVector:
         st = stream if stream is not None else self.stream
         return ClonedState(capi.sv_clone(self.h, st), self.n, st, self.device)
 
+    def merge(self, other: "StateVector", stream=None) -> "ClonedState":
+        """p-block merge: self (x) other, self on the low qubits."""
+        st = stream if stream is not None else self.stream
+        return ClonedState(capi.sv_merge(self.h, other.h, st), self.n + other.n, st, self.device)
+
+    def take_qubit(self, qubit: int, tol: float = 1e-6):
+        """Removes a qubit that is in a basis state: (new (n-1)-qubit state, its value)."""
+        h, v = capi.sv_take_qubit(self.h, qubit, tol)
+        return ClonedState(h, self.n - 1, self.stream, self.device), v
+
     def profile(self, on: bool = True):
         capi.sv_profile_enable(self.h, on)
 
