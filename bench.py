@@ -479,6 +479,72 @@ def run_dynamic_mode(args):
     }
 
 
+def run_pblock_mode(args):
+    """Distributed-register pattern (§III-E): two 14-qubit hosts, each with one
+    communication qubit, are simulated apart, merged into one 28-qubit register
+    (2 GiB), entangled through the communication pair, the communication qubits
+    measured and taken out (27 then 26 qubits).  Reports steps/s and the merge
+    and take kernels' HBM rates (CUDA events on the states' stream; the take
+    interval includes its mass reduction, 8 B per amplitude read)."""
+    import torch
+    from paper_2512_04216_gb300 import StateVector, capi
+    na = nb = 14
+    ca, cb = W.random_layered(na, 10, 41), W.random_layered(nb, 10, 42)
+    peak, peak_kind = peaks()
+    prof_tot = {}
+
+    def step(k, prof):
+        a, b = StateVector(na), StateVector(nb)
+        a.apply(ca)
+        b.apply(cb)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record()
+        m = a.merge(b)
+        ev[1].record()
+        m.apply([("h", (na - 1,), ()), ("cx", (na - 1, na + nb - 1), ()), ("cx", (0, na - 1), ())])
+        m.measure(na - 1, 0.25 + 0.5 * (k % 2))
+        m.measure(na + nb - 1, 0.6)
+        ev[2].record()
+        m2, _ = m.take_qubit(na + nb - 1)
+        ev[3].record()
+        m3, _ = m2.take_qubit(na - 1)
+        torch.cuda.synchronize()
+        if prof:
+            for name, (e0, e1, nbytes) in {"merge": (ev[0], ev[1], 8.0 * (1 << (na + nb))),
+                                           "take": (ev[2], ev[3], 8.0 * (1 << (na + nb)))}.items():
+                t = prof_tot.setdefault(name, {"launches": 0, "ms": 0.0, "bytes": 0.0})
+                t["launches"] += 1
+                t["ms"] += e0.elapsed_time(e1)
+                t["bytes"] += nbytes
+        for st in (a, b, m, m2, m3):
+            st.close()
+
+    for k in range(args.warmup):
+        step(k, False)
+    torch.cuda.synchronize()
+    launches0 = capi.sv_launch_count()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(k, True)
+    dt = time.perf_counter() - t0
+    rates = {k: (v["bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] > 0 and v["bytes"] else None)
+             for k, v in prof_tot.items()}
+    mg = rates.get("merge") or float("nan")
+    return {
+        "metric": "p-block steps/s", "value": args.steps / dt, "unit": "steps/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": "two 14-qubit hosts (depth 10) merged to 28 qubits, communication pair "
+                               "entangled, measured and taken out; state allocation inside the step"},
+        "roofline": {"bound": "hbm", "kernel": "k_kron", "achieved": round(mg, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(mg / peak, 4), "peak_source": peak_kind,
+                     "algorithmic_bytes_per_launch": 8 * (1 << (na + nb)), "traffic": None},
+        "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                        "GB/s": round(rates[k], 1) if rates[k] else None} for k, v in prof_tot.items()},
+        "gpu_launches": int(capi.sv_launch_count() - launches0),
+    }
+
+
 def run_serve_mode(args):
     """Config: Poisson stream of random layered circuits, n geometric-skewed on
     8..30 (mean ~16), depth ~ U{10..100}, 1000 shots or a Z-string mask; served
@@ -523,10 +589,12 @@ def main():
     ap.add_argument("--kernel-variant", type=int, default=0)
     ap.add_argument("--precision", type=int, default=OPTS["precision"],
                     help="0: FP32 CUDA cores; 1: 3xTF32 tensor-core stage products")
-    ap.add_argument("--workload", choices=["statevector", "large", "batch", "serve", "dynamic"], default="statevector",
+    ap.add_argument("--workload", choices=["statevector", "large", "batch", "serve", "dynamic", "pblock"],
+                    default="statevector",
                     help="statevector: the bench line; large: the 34-qubit (128 GiB) single state, "
                          "depth 30, 1e6 shots; batch / serve: the batched and serving patterns; "
-                         "dynamic: per-shot trajectories with mid-circuit measurement")
+                         "dynamic: per-shot trajectories with mid-circuit measurement; "
+                         "pblock: merged registers with communication qubits")
     ap.add_argument("--batch-circuits", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate-factors", default="0.5,1,2,4")
@@ -545,9 +613,10 @@ def main():
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
         return
-    if args.workload in ("batch", "serve", "dynamic"):
+    if args.workload in ("batch", "serve", "dynamic", "pblock"):
         if rank == 0:
-            fn = {"batch": run_batch_mode, "serve": run_serve_mode, "dynamic": run_dynamic_mode}[args.workload]
+            fn = {"batch": run_batch_mode, "serve": run_serve_mode, "dynamic": run_dynamic_mode,
+                  "pblock": run_pblock_mode}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
 

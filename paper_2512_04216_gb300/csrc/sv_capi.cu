@@ -280,7 +280,9 @@ const char *sv_version(void) { return "svgb 0.1 (sm_103a)"; }
 
 uint64_t sv_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
-int sv_create(int n_qubits, int dtype, void *cuda_stream, sv_state **out) {
+// A library-owned state whose buffer is left uninitialised when `reset` is
+// false (for results that overwrite every amplitude: clone, merge, take).
+static int create_state(int n_qubits, int dtype, void *cuda_stream, bool reset, sv_state **out) {
   int rc = new_state(n_qubits, dtype, cuda_stream, out);
   if (rc) return rc;
   sv_state *s = *out;
@@ -295,6 +297,7 @@ int sv_create(int n_qubits, int dtype, void *cuda_stream, sv_state **out) {
                 cudaGetErrorString(e));
   }
   s->owned = true;
+  if (!reset) return SV_OK;
   e = launch_reset(s->amp, n_qubits, 0, s->stream);
   if (e != cudaSuccess) {
     free_state(s);
@@ -302,6 +305,10 @@ int sv_create(int n_qubits, int dtype, void *cuda_stream, sv_state **out) {
     return fail(SV_ERR_CUDA, "reset: %s", cudaGetErrorString(e));
   }
   return SV_OK;
+}
+
+int sv_create(int n_qubits, int dtype, void *cuda_stream, sv_state **out) {
+  return create_state(n_qubits, dtype, cuda_stream, true, out);
 }
 
 int sv_wrap(void *dev_ptr, int n_qubits, int dtype, void *cuda_stream, sv_state **out) {
@@ -509,7 +516,7 @@ int sv_clone(sv_state *src, void *cuda_stream, sv_state **out) {
   CHECK_STATE(src);
   if (!out) return fail(SV_ERR_ARG, "out is null");
   DeviceGuard g(src->device);
-  int rc = sv_create(src->n, SV_C64, cuda_stream, out);
+  int rc = create_state(src->n, SV_C64, cuda_stream, false, out);
   if (rc) return rc;
   sv_state *d = *out;
   const size_t bytes = (size_t(1) << src->n) * sizeof(float2);
@@ -530,7 +537,7 @@ int sv_merge(sv_state *a, sv_state *b, void *cuda_stream, sv_state **out) {
   if (a->device != b->device) return fail(SV_ERR_ARG, "registers live on different devices");
   if (a->n + b->n > 36) return fail(SV_ERR_ARG, "merged register would exceed 36 qubits");
   DeviceGuard g(a->device);
-  int rc = sv_create(a->n + b->n, SV_C64, cuda_stream, out);
+  int rc = create_state(a->n + b->n, SV_C64, cuda_stream, false, out);
   if (rc) return rc;
   sv_state *d = *out;
   cudaError_t e = stream_after(d->stream, a->stream);
@@ -562,7 +569,7 @@ int sv_take_qubit(sv_state *s, int qubit, double tol, int *value, sv_state **out
   if ((v ? m0 : m1) > tol * total)
     return fail(SV_ERR_ARG, "qubit %d is not in a basis state (minority mass %.3g of %.3g)", qubit,
                 v ? m0 : m1, total);
-  rc = sv_create(s->n - 1, SV_C64, s->stream, out);
+  rc = create_state(s->n - 1, SV_C64, s->stream, false, out);
   if (rc) return rc;
   sv_state *d = *out;
   cudaError_t e = timed(d, "take", double(size_t(8) << s->n),
