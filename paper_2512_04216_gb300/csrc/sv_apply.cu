@@ -344,7 +344,7 @@ __host__ __device__ inline RegLayout reg_layout(uint32_t T, uint32_t c, uint32_t
 // of 256 threads per SM; 32 amplitudes per thread (blocks up to 2 qubits):
 // three CTAs of 128 threads per SM.
 template <int R, int NTMAX>
-__global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 4 : 1) : (NTMAX <= 256 ? 2 : 1))
+__global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 4 : 2) : (NTMAX <= 256 ? 2 : 1))
     k_pass_reg(float2 *__restrict__ amp, const uint8_t *__restrict__ plan, uint32_t pass_off,
                const __grid_constant__ RegPassParams prm) {
   constexpr int NR = 1 << R;

@@ -994,7 +994,7 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
     }
     // register stages hold 2^Rb amplitudes per thread (blocks up to 4
     // qubits); passes with 5-qubit blocks use the shared-memory kernel
-    const int Rb = (o_r5 && kmx <= 2 && T_ <= 12 && T_reg_ok(T_, c, 5)) ? 5 : 4;
+    const int Rb = (o_r5 && kmx <= 2 && T_reg_ok(T_, c, 5)) ? 5 : 4;
     const bool use_reg = !o_smem && kmx <= 4 && T_reg_ok(T_, c, Rb);
     std::vector<HStage> stages;
     std::vector<int> order;
