@@ -398,11 +398,15 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 4 : 2) : (NTMA
     t_gl = pdep_u64(LB >> c, hm) + (LB & lowmask);
   }
 
+  // 32-amplitude passes prefetch the next tile into the exchange buffer while
+  // their last stage computes (the buffer is free once the last exchange is read)
+  const uint32_t t_ldx = (tt[tid] & 0xffffu) * 8u;
   uint64_t tile = blockIdx.x;
   uint64_t base = tile < n_tiles ? pdep_u64(tile, outer_mask) : 0;
-  if (!kDirect && tile < n_tiles) {
+  if (tile < n_tiles) {
+    const uint32_t dst = kDirect ? sx : sin;
 #pragma unroll
-    for (int k = 0; k < NK; k++) cp_async16_s(sin + (tid + k * NT) * 16u, amp + base + t_cp + prm.ko[k]);
+    for (int k = 0; k < NK; k++) cp_async16_s(dst + (tid + k * NT) * 16u, amp + base + t_cp + prm.ko[k]);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
   __syncthreads();
@@ -412,10 +416,10 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 4 : 2) : (NTMA
     const uint64_t next = tile + gridDim.x;
     const uint64_t base_next = next < n_tiles ? pdep_u64(next, outer_mask) : 0;
     if constexpr (kDirect) {
-      // first stage straight from HBM: lanes hold consecutive amplitudes
-      const float2 *src = amp + base + t_gl;
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+      __syncthreads();
 #pragma unroll
-      for (int j = 0; j < NR; j++) v[j] = __ldcs(src + prm.gi[j]);
+      for (int j = 0; j < NR; j++) v[j] = lds64(sx + t_ldx + prm.lo[j]);
     } else {
       asm volatile("cp.async.wait_all;\n" ::: "memory");
       __syncthreads();
@@ -454,6 +458,14 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 4 : 2) : (NTMA
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < NR; j++) v[j] = lds64(sx + (xo[j] ^ PB));
+      }
+      if (kDirect && s + 1 == ns) {
+        __syncthreads();  // every thread has read the exchange buffer
+        if (next < n_tiles) {
+#pragma unroll
+          for (int k = 0; k < NK; k++) cp_async16_s(sx + (tid + k * NT) * 16u, amp + base_next + t_cp + prm.ko[k]);
+          asm volatile("cp.async.commit_group;\n" ::: "memory");
+        }
       }
       const uint32_t oe = st.op_end;
       for (uint32_t o = st.op_begin; o < oe; o++) {
