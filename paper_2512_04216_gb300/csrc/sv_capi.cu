@@ -55,6 +55,16 @@ int svgb::set_last_error(int code, const char *fmt, ...) {
   return code;
 }
 
+// Pinned host staging + device copy of one chunk of a plan; reusable once the
+// event recorded after the chunk's last kernel has completed.
+struct PlanSlab {
+  uint8_t *host = nullptr;
+  uint8_t *dev = nullptr;
+  size_t cap = 0;
+  cudaEvent_t done = nullptr;
+  bool live = false;
+};
+
 struct sv_state {
   int n = 0;
   int device = 0;
@@ -62,13 +72,6 @@ struct sv_state {
   bool owned = false;
   bool poisoned = false;
   cudaStream_t stream = nullptr;
-  // plan staging
-  uint8_t *plan_dev = nullptr;
-  size_t plan_cap = 0;
-  uint8_t *plan_host = nullptr;
-  size_t plan_host_cap = 0;
-  cudaEvent_t plan_evt = nullptr;
-  bool plan_evt_live = false;
   // measurement scratch
   MeasureScratch ms;
   double *dscal = nullptr;       // device scalars: [0] sum p, [1] sum pz, [2] total
@@ -77,6 +80,7 @@ struct sv_state {
   double *hscal = nullptr;       // pinned host scalars
   void *stage = nullptr;         // device staging for host in/out buffers
   size_t stage_cap = 0;
+  std::vector<PlanSlab> slabs;  // streamed plan chunks
   // profiling
   bool prof = false;
   std::vector<ProfRec> recs;
@@ -251,9 +255,6 @@ void free_state(sv_state *s) {
   DeviceGuard g(s->device);
   cudaStreamSynchronize(s->stream);
   if (s->owned && s->amp) cudaFree(s->amp);
-  if (s->plan_dev) cudaFree(s->plan_dev);
-  if (s->plan_host) cudaFreeHost(s->plan_host);
-  if (s->plan_evt) cudaEventDestroy(s->plan_evt);
   if (s->ms.chunk) cudaFree(s->ms.chunk);
   if (s->ms.block) cudaFree(s->ms.block);
   if (s->ms.part) cudaFree(s->ms.part);
@@ -267,6 +268,11 @@ void free_state(sv_state *s) {
     cudaEventDestroy(r.b);
   }
   for (auto e : s->evpool) cudaEventDestroy(e);
+  for (auto &sl : s->slabs) {
+    if (sl.host) cudaFreeHost(sl.host);
+    if (sl.dev) cudaFree(sl.dev);
+    if (sl.done) cudaEventDestroy(sl.done);
+  }
   delete s;
 }
 
@@ -364,49 +370,73 @@ int sv_plan_stats(int n_qubits, const sv_gate *ir, size_t n_gates, const sv_opts
   return SV_OK;
 }
 
+// A plan slab of at least `bytes` whose previous chunk has finished (index into s->slabs).
+static int acquire_slab(sv_state *s, size_t bytes, size_t *idx) {
+  for (size_t i = 0; i < s->slabs.size(); i++) {
+    PlanSlab &sl = s->slabs[i];
+    if (sl.cap < bytes) continue;
+    if (sl.live) {
+      const cudaError_t q = cudaEventQuery(sl.done);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) return cuda_fail(s, q, "plan slab event");
+      sl.live = false;
+    }
+    *idx = i;
+    return SV_OK;
+  }
+  PlanSlab sl;
+  sl.cap = std::max<size_t>(size_t(64) << 10, (bytes + 4095) & ~size_t(4095));
+  cudaError_t e = cudaMallocHost(&sl.host, sl.cap);
+  if (e == cudaSuccess) e = cudaMalloc(&sl.dev, sl.cap);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    if (sl.host) cudaFreeHost(sl.host);
+    if (sl.dev) cudaFree(sl.dev);
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? SV_ERR_OOM : SV_ERR_CUDA, "plan slab: %s", cudaGetErrorString(e));
+  }
+  s->slabs.push_back(sl);
+  *idx = s->slabs.size() - 1;
+  return SV_OK;
+}
+
+// Plans in chunks of 2, 4, 8, ... passes: each chunk is uploaded and its passes
+// launched before the next chunk is planned, so the GPU starts on the first
+// passes while the host plans the rest.
 int sv_apply_circuit(sv_state *s, const sv_gate *ir, size_t n_gates, const sv_opts *opts) {
   CHECK_STATE(s);
   if (n_gates == 0) return SV_OK;
   if (!ir) return fail(SV_ERR_ARG, "ir is null");
-  Plan plan;
+  PlanBuilder builder;
   std::string err;
-  if (!build_plan(s->n, ir, n_gates, opts, plan, err)) return fail(SV_ERR_ARG, "%s", err.c_str());
+  if (!builder.init(s->n, ir, n_gates, opts, err)) return fail(SV_ERR_ARG, "%s", err.c_str());
   DeviceGuard g(s->device);
   {
     int rc = ensure_scalars(s);
     if (rc) return rc;
   }
-  const size_t bytes = plan.bytes.size();
-  // host staging: wait until the previous upload has left the pinned buffer
-  if (s->plan_evt_live) {
-    CK(s, cudaEventSynchronize(s->plan_evt));
-    s->plan_evt_live = false;
-  }
-  if (s->plan_host_cap < bytes) {
-    if (s->plan_host) cudaFreeHost(s->plan_host);
-    s->plan_host = nullptr;
-    s->plan_host_cap = 0;
-    CK(s, cudaMallocHost(&s->plan_host, bytes * 2));
-    s->plan_host_cap = bytes * 2;
-  }
-  {
-    void *p = s->plan_dev;
-    int rc = ensure_dev(s, &p, &s->plan_cap, bytes * 2, "plan buffer");
-    s->plan_dev = static_cast<uint8_t *>(p);
-    if (rc) return rc;
-  }
-  if (!s->plan_evt) CK(s, cudaEventCreateWithFlags(&s->plan_evt, cudaEventDisableTiming));
-  std::memcpy(s->plan_host, plan.bytes.data(), bytes);
-  CK(s, cudaMemcpyAsync(s->plan_dev, s->plan_host, bytes, cudaMemcpyHostToDevice, s->stream));
-  CK(s, cudaEventRecord(s->plan_evt, s->stream));
-  s->plan_evt_live = true;
   const double pass_bytes = 16.0 * double(uint64_t(1) << s->n);
-  for (size_t p = 0; p < plan.passes.size(); p++) {
-    const char *kname = plan.passes[p].kind == KIND_TC ? "pass_tc" : "pass";
-    CK(s, timed(s, kname, pass_bytes, [&] {
-         return launch_pass(s->amp, s->plan_dev, plan.pass_offs[p], plan.passes[p], &plan.rparams[p], s->derr,
-                            s->stream);
-       }));
+  size_t chunk = 2;
+  while (!builder.done()) {
+    Plan plan;
+    if (!builder.next(plan, chunk, err)) return fail(SV_ERR_ARG, "%s", err.c_str());
+    chunk = std::min<size_t>(chunk * 2, 64);
+    const size_t bytes = plan.bytes.size();
+    size_t si = 0;
+    int rc = acquire_slab(s, bytes, &si);
+    if (rc) return rc;
+    PlanSlab &sl = s->slabs[si];
+    std::memcpy(sl.host, plan.bytes.data(), bytes);
+    CK(s, cudaMemcpyAsync(sl.dev, sl.host, bytes, cudaMemcpyHostToDevice, s->stream));
+    for (size_t p = 0; p < plan.passes.size(); p++) {
+      const char *kname = plan.passes[p].kind == KIND_TC ? "pass_tc" : "pass";
+      CK(s, timed(s, kname, pass_bytes, [&] {
+           return launch_pass(s->amp, sl.dev, plan.pass_offs[p], plan.passes[p], &plan.rparams[p], s->derr,
+                              s->stream);
+         }));
+    }
+    CK(s, cudaEventRecord(sl.done, s->stream));
+    sl.live = true;
   }
   return SV_OK;
 }

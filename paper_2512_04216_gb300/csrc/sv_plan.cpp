@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -805,8 +806,7 @@ static uint64_t lookahead_tile(const std::vector<GateM> &gates, const std::vecto
   return Q;
 }
 
-bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Plan &plan,
-                std::string &err) {
+bool PlanBuilder::init(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, std::string &err) {
   sv_opts o{};
   if (opts_in) o = *opts_in;
   int kmax = o.k_max ? o.k_max : 2;
@@ -837,7 +837,8 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
   if (c > T) c = T;
   // a pass must be able to take any single gate (up to 5 qubits) next to the c low qubits
   int widest = 1;
-  std::vector<GateM> gates;
+  std::vector<GateM> &gates = gates_;
+  gates.clear();
   if (!convert_ir(n, ir, ng, gates, err)) return false;
   for (auto &g : gates) widest = std::max(widest, g.k);
   if (T < n && T - c < widest) c = std::max(1, T - widest);
@@ -847,14 +848,34 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
   }
   kmax = std::min(kmax, T);  // a wider UNITARY still gets a block of its own
 
+  n_ = n;
+  kmax_ = kmax;
+  T_ = T;
+  c_ = c;
+  o_ = o;
+  o_smem_ = o_smem;
+  o_r5_ = o_r5;
+  ng_ = ng;
+  nmask_ = (n >= 64) ? ~uint64_t(0) : ((uint64_t(1) << n) - 1);
+  lowmask_ = (uint64_t(1) << c) - 1;
+  remaining_.resize(ng);
+  for (size_t i = 0; i < ng; i++) remaining_[i] = uint32_t(i);
+  return true;
+}
+
+bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
+  const int n = n_, T = T_, c = c_;
+  int kmax = kmax_;
+  const sv_opts &o = o_;
+  const bool o_smem = o_smem_, o_r5 = o_r5_;
+  const std::vector<GateM> &gates = gates_;
+  std::vector<uint32_t> &remaining = remaining_;
   plan = Plan();
   plan.n = n;
-  plan.info.n_gates = ng;
-  const uint64_t nmask = (n >= 64) ? ~uint64_t(0) : ((uint64_t(1) << n) - 1);
-  const uint64_t lowmask = (uint64_t(1) << c) - 1;
-
-  std::vector<uint32_t> remaining(ng);
-  for (size_t i = 0; i < ng; i++) remaining[i] = uint32_t(i);
+  plan.info.n_gates = first_ ? ng_ : 0;
+  first_ = false;
+  const uint64_t nmask = nmask_;
+  const uint64_t lowmask = lowmask_;
 
   struct PassH {
     uint64_t Q;
@@ -865,7 +886,7 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
   };
   std::vector<PassH> passes;
 
-  while (!remaining.empty()) {
+  while (!remaining.empty() && passes.size() < max_passes) {
     uint64_t Q = lowmask, blocked = 0;
     std::vector<uint32_t> acc, rest;
     acc.reserve(remaining.size());
@@ -1133,6 +1154,12 @@ bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_in, Pla
   plan.info.upload_bytes = buf.size();
   plan.precision = o.precision;
   return true;
+}
+
+bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts, Plan &plan, std::string &err) {
+  PlanBuilder b;
+  if (!b.init(n, ir, ng, opts, err)) return false;
+  return b.next(plan, SIZE_MAX, err);
 }
 
 }  // namespace svgb

@@ -33,4 +33,23 @@ bool convert_ir(int n, const sv_gate *ir, size_t ng, std::vector<GateM> &gates, 
 bool build_plan(int n, const sv_gate *ir, size_t ng, const sv_opts *opts, Plan &plan,
                 std::string &err);
 
+// Incremental planner: init() validates and converts the IR; each next() plans up
+// to max_passes further passes and packs them as a standalone Plan, so a caller
+// can launch the first passes while later ones are still being planned.
+class PlanBuilder {
+ public:
+  bool init(int n, const sv_gate *ir, size_t ng, const sv_opts *opts, std::string &err);
+  bool done() const { return remaining_.empty(); }
+  bool next(Plan &plan, size_t max_passes, std::string &err);
+
+ private:
+  int n_ = 0, kmax_ = 2, T_ = 12, c_ = 5;
+  sv_opts o_{};
+  bool o_smem_ = false, o_r5_ = false, first_ = true;
+  uint64_t nmask_ = 0, lowmask_ = 0;
+  size_t ng_ = 0;
+  std::vector<GateM> gates_;
+  std::vector<uint32_t> remaining_;
+};
+
 }  // namespace svgb
