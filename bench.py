@@ -42,7 +42,7 @@ DEPTH = 40
 SEED = 2
 SHOTS = 100_000
 ZMASK = 0b1011  # <Z_0 Z_1 Z_3>
-OPTS = dict(k_max=2, tile_qubits=12, low_qubits=5, precision=0, kernel_variant=0)
+OPTS = dict(k_max=5, tile_qubits=12, low_qubits=5, precision=0, kernel_variant=0)
 METRIC = "state-vector apply HBM GB/s vs peak"
 # FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12

@@ -79,7 +79,11 @@ typedef struct sv_gate {
 /* Options of sv_apply_circuit.  Zero fields take the library default. */
 typedef struct sv_opts {
   int32_t k_max;       /* fusion width: gates are fused into dense blocks of at most
-                          k_max qubits (1..5; default 2) */
+                          k_max qubits (1..5; default 2).  Per pass, blocks wider
+                          than 2 qubits are formed only when their estimated cost
+                          is lower (the register kernels run 1-2-qubit blocks
+                          fastest); with precision 1, up to min(k_max, 4).  A gate
+                          wider than the width keeps a block of its own. */
   int32_t tile_qubits; /* T: qubits held by one CTA tile in shared memory per HBM
                           pass (5..13; default 12; clamped to n) */
   int32_t low_qubits;  /* c: low qubits every tile contains, so each global access

@@ -81,18 +81,39 @@ __device__ __forceinline__ void apply_dense(float2 *__restrict__ tile, const flo
     float2 v[KK];
 #pragma unroll
     for (int j = 0; j < KK; j++) v[j] = tile[b + off[j]];
+    if constexpr (K <= 3) {
 #pragma unroll
-    for (int r = 0; r < KK; r++) {
-      float re = 0.f, im = 0.f;
+      for (int r = 0; r < KK; r++) {
+        float re = 0.f, im = 0.f;
 #pragma unroll
-      for (int j = 0; j < KK; j++) {
-        const float2 m = mat[r * KK + j];
-        re = fmaf(m.x, v[j].x, re);
-        re = fmaf(-m.y, v[j].y, re);
-        im = fmaf(m.x, v[j].y, im);
-        im = fmaf(m.y, v[j].x, im);
+        for (int j = 0; j < KK; j++) {
+          const float2 m = mat[r * KK + j];
+          re = fmaf(m.x, v[j].x, re);
+          re = fmaf(-m.y, v[j].y, re);
+          im = fmaf(m.x, v[j].y, im);
+          im = fmaf(m.y, v[j].x, im);
+        }
+        tile[b + off[r]] = make_float2(re, im);
       }
-      tile[b + off[r]] = make_float2(re, im);
+    } else {
+      // 16 / 32 outputs: one row at a time keeps the register footprint to the inputs
+#pragma unroll 1
+      for (int r = 0; r < KK; r++) {
+        float re = 0.f, im = 0.f;
+#pragma unroll
+        for (int j = 0; j < KK; j++) {
+          const float2 m = mat[r * KK + j];
+          re = fmaf(m.x, v[j].x, re);
+          re = fmaf(-m.y, v[j].y, re);
+          im = fmaf(m.x, v[j].y, im);
+          im = fmaf(m.y, v[j].x, im);
+        }
+        uint32_t o = 0;
+#pragma unroll
+        for (int m = 0; m < K; m++)
+          if ((r >> m) & 1) o |= 1u << lb[m];
+        tile[b + o] = make_float2(re, im);
+      }
     }
   }
 }

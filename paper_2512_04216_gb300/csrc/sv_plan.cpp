@@ -883,6 +883,7 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
     std::vector<uint32_t> acc;  // accepted gates (program order)
     int lq[32];
     bool pairs;                 // fused with two-local-qubit phase terms
+    int kfuse;                  // fusion width used
   };
   std::vector<PassH> passes;
 
@@ -949,8 +950,39 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
     // two-local-qubit phase terms only where the pass can run on register stages
     int wmax = 1;
     for (uint32_t gi : acc) wmax = std::max(wmax, gates[gi].k);
-    ph.pairs = !o_smem && kmax <= 4 && wmax <= 4 && T_reg_ok(popc(Q), c, 4);
-    fuse_pass(gates, acc, Q, lpos, kmax, ph.pairs, ph.ops);
+    auto pairs_ok = [&](int k) { return !o_smem && k <= 4 && wmax <= 4 && T_reg_ok(popc(Q), c, 4); };
+    // Fusion width: blocks of <= 2 qubits run on the 32-amplitude register
+    // kernel (paired FMAs, 4 * 2^k FMA per amplitude); wider blocks cost 2^k more
+    // each and run on slower kernels, so k_max > 2 is used for a pass only when
+    // the wider fusion's estimated cost is lower.  Tensor-core stages take up to
+    // 4 qubits at one cost.  A gate wider than the width keeps a block of its own.
+    auto est = [](const std::vector<HostOp> &ops) {
+      double w = 0.0;
+      int kx = 0;
+      for (const HostOp &op : ops) {
+        if (op.type == OP_DENSE) {
+          w += double(1 << op.blk.k());
+          kx = std::max(kx, op.blk.k());
+        } else {
+          w += 4.0;
+        }
+      }
+      return w * (kx <= 2 ? 1.0 : (kx <= 4 ? 1.3 : 4.0));
+    };
+    int kf = (o.precision == 1) ? std::min(kmax, 4) : std::min(kmax, 2);
+    ph.pairs = pairs_ok(kf);
+    fuse_pass(gates, acc, Q, lpos, kf, ph.pairs, ph.ops);
+    if (o.precision != 1 && kmax > kf) {
+      std::vector<HostOp> wide;
+      const bool pw = pairs_ok(kmax);
+      fuse_pass(gates, acc, Q, lpos, kmax, pw, wide);
+      if (est(wide) < est(ph.ops)) {
+        ph.ops.swap(wide);
+        ph.pairs = pw;
+        kf = kmax;
+      }
+    }
+    ph.kfuse = kf;
     ph.acc = std::move(acc);
     passes.push_back(std::move(ph));
     remaining.swap(rest);
@@ -1035,7 +1067,7 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
     if (!reg && ph.pairs) {
       // the shared-memory kernel takes phase terms with one tile qubit only
       ph.ops.clear();
-      fuse_pass(gates, ph.acc, ph.Q, lpos, kmax, false, ph.ops);
+      fuse_pass(gates, ph.acc, ph.Q, lpos, ph.kfuse, false, ph.ops);
       ph.pairs = false;
       op_masks();
       hp.n_ops = uint32_t(nops);

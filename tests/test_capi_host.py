@@ -53,8 +53,16 @@ def test_plan_stats_counts():
     assert info["bytes"] == 16 * (1 << 12)
     assert sum(info["hist_k"]) == info["n_blocks"]
     assert max(k for k in range(6) if info["hist_k"][k]) <= 2
+    # k_max is an upper bound: on U3 + CX layers, two-qubit blocks are cheaper
     info5 = capi.sv_plan_stats(12, c, capi.make_opts(5, 12, 5))
-    assert info5["n_blocks"] < info["n_blocks"]
+    assert info5["n_blocks"] <= info["n_blocks"]
+    assert max(k for k in range(6) if info5["hist_k"][k]) <= 5
+    # many gates on the same three qubits: one 3-qubit block beats many 2-qubit ones
+    rep = [("cx", (0, 1), ()), ("u3", (2,), (0.1, 0.2, 0.3)), ("cx", (1, 2), ()), ("u3", (0,), (0.3, 0.2, 0.1)),
+           ("cx", (2, 0), ())] * 8
+    w2 = capi.sv_plan_stats(6, rep, capi.make_opts(2, 6, 2))
+    w3 = capi.sv_plan_stats(6, rep, capi.make_opts(3, 6, 2))
+    assert w3["hist_k"][3] >= 1 and w3["flops"] < w2["flops"]
 
 
 def test_plan_passes_shrink_with_tile():
