@@ -386,10 +386,11 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 4 : 2) : (NTMA
   const uint32_t sx = static_cast<uint32_t>(__cvta_generic_to_shared(buf_x));
   // tile-invariant per-thread parts of the addresses
   const uint32_t t_ld = sin + (tt[tid] & 0xffffu) * 8u;
-  uint64_t t_st;
+  uint64_t t_st = 0;
   {
     const uint32_t LB = tt[(ns - 1) * NT + tid] & 0xffffu;
-    t_st = pdep_u64(LB >> c, hm) + (LB & lowmask);
+    for (uint32_t x = 0; x < T; x++)
+      if ((LB >> x) & 1u) t_st |= uint64_t(1) << prm.oq[x];
   }
   const uint64_t t_cp = pdep_u64(tid >> cs, hm) + (uint64_t(tid & cmask) << 1);
   uint64_t t_gl;

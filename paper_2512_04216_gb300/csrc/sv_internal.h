@@ -81,6 +81,7 @@ struct RegPassParams {
   uint64_t gi[32];      // first stage: amplitude offset of la[j] from the tile base in HBM
   uint64_t go[32];      // last stage: amplitude offset of la[j] from the tile base in HBM
   uint64_t ko[16];      // prefetch: amplitude offset of 16-byte chunk row k (chunks k*NT..)
+  uint8_t oq[16];       // store: physical qubit written from local bit x (SWAPs folded in)
 };
 
 // Columns of the shared-memory swizzle: local bit b < 4 maps to itself, local

@@ -102,6 +102,7 @@ static bool gate_matrix(const sv_gate &g, GateM &out, std::string &err) {
         at(0, 0) = 1.0; at(2, 2) = 1.0; at(1, 3) = 1.0; at(3, 1) = 1.0;
       } else if (g.kind == SV_GATE_SWAP) {
         at(0, 0) = 1.0; at(1, 2) = 1.0; at(2, 1) = 1.0; at(3, 3) = 1.0;
+        out.swap = true;
       } else {
         at(0, 0) = 1.0; at(1, 1) = 1.0; at(2, 2) = 1.0;
         at(3, 3) = (g.kind == SV_GATE_CZ) ? cd(-1.0) : std::polar(1.0, p[0]);
@@ -309,8 +310,13 @@ static void merge_terms(std::vector<HostTerm> &terms) {
 // planning
 // ---------------------------------------------------------------------------
 
+// With `rho` (relabeling), a SWAP of two tile qubits emits nothing: rho[q] is
+// the qubit whose loaded position now holds qubit q's data, and later gates act
+// on those positions; the caller stores qubit q's data from local bit
+// lpos[rho[q]].  Without it, SWAPs are ordinary 4x4 blocks.
 static void fuse_pass(const std::vector<GateM> &gates, const std::vector<uint32_t> &acc,
-                      uint64_t Q, const int *lpos, int kmax, bool pairs, std::vector<HostOp> &ops) {
+                      uint64_t Q, const int *lpos, int kmax, bool pairs, std::vector<HostOp> &ops,
+                      int *rho = nullptr) {
   std::vector<Block> open;
   std::vector<HostTerm> pending;
   uint64_t pending_local = 0;
@@ -347,8 +353,27 @@ static void fuse_pass(const std::vector<GateM> &gates, const std::vector<uint32_
     }
   };
 
+  GateM renamed;
   for (uint32_t gi : acc) {
-    const GateM &g = gates[gi];
+    const GateM *gp = &gates[gi];
+    if (rho) {
+      if (gp->swap) {
+        std::swap(rho[gp->q[0]], rho[gp->q[1]]);
+        continue;
+      }
+      bool moved = false;
+      for (int x = 0; x < gp->k; x++) moved |= rho[gp->q[x]] != gp->q[x];
+      if (moved) {
+        renamed = *gp;
+        renamed.mask = 0;
+        for (int x = 0; x < gp->k; x++) {
+          renamed.q[x] = rho[gp->q[x]];
+          renamed.mask |= uint64_t(1) << renamed.q[x];
+        }
+        gp = &renamed;
+      }
+    }
+    const GateM &g = *gp;
     const uint64_t local = g.mask & Q;
     const bool outer = (g.mask & ~Q) != 0;
     bool to_phase = false;
@@ -484,9 +509,15 @@ struct HStage {
 // the last stage holds a low bit.  With `tc` the dense ops of a stage become one
 // product applied before the stage's phase ops, so a dense op that touches a
 // bit of an accepted phase op waits for a later stage.
+// `store_low` (default: the c low bits) is the set of local bits that the store
+// puts on the lanes; it differs from the load's low bits when SWAPs relabel qubits
+// (`store_natural` false: the store lanes are not local bits 0..c-1 in order, so a
+// single stage cannot both load and store).
 static void assign_stages(const std::vector<HostOp> &ops, const std::vector<uint32_t> &omask, int T,
-                          int c, int Rb, std::vector<HStage> &st, bool tc = false) {
+                          int c, int Rb, std::vector<HStage> &st, bool tc = false, uint32_t store_low = 0,
+                          bool store_natural = true) {
   const uint32_t all = (T >= 32) ? ~0u : ((1u << T) - 1u), low = (1u << c) - 1u;
+  if (!store_low) store_low = low;
   std::vector<int> rem(ops.size());
   for (size_t i = 0; i < ops.size(); i++) rem[i] = int(i);
   bool first = true;
@@ -521,16 +552,20 @@ static void assign_stages(const std::vector<HostOp> &ops, const std::vector<uint
     first = false;
   }
   if (st.empty()) st.push_back(HStage{});
-  if (st.back().R & low) st.push_back(HStage{});
+  if ((st.back().R & store_low) || (st.size() == 1 && !store_natural)) st.push_back(HStage{});
   for (size_t i = 0; i < st.size(); i++) {
-    const bool io = (i == 0) || (i + 1 == st.size());
-    const uint32_t allowed = io ? (all & ~low) : all;
+    uint32_t allowed = all;
+    if (i == 0) allowed &= ~low;
+    if (i + 1 == st.size()) allowed &= ~store_low;
     for (int b = T - 1; b >= 0 && popc(uint64_t(st[i].R)) < Rb; b--)
       if (((allowed >> b) & 1u) && !((st[i].R >> b) & 1u)) st[i].R |= 1u << b;
   }
 }
 
-static StageRec make_stage(const HStage &hs, int T, int c, int Rb, bool load, bool store) {
+// `store_lanes` (store stages of relabeled passes): the local bits that hold
+// output qubits 0..c-1, in that order, to be put on the lanes.
+static StageRec make_stage(const HStage &hs, int T, int c, int Rb, bool load, bool store,
+                           const std::vector<int> *store_lanes = nullptr) {
   StageRec sr{};
   int nr = 0;
   for (int b = 0; b < T; b++)
@@ -539,7 +574,11 @@ static StageRec make_stage(const HStage &hs, int T, int c, int Rb, bool load, bo
   for (int b = 0; b < T; b++)
     if (!((hs.R >> b) & 1u)) rest.push_back(b);
   std::vector<int> tb;
-  if (load || store) {
+  if (store && !load && store_lanes) {
+    tb = *store_lanes;  // output qubits 0..c-1 on the lanes, then the rest ascending
+    for (int b : rest)
+      if (std::find(tb.begin(), tb.end(), b) == tb.end()) tb.push_back(b);
+  } else if (load || store) {
     tb = rest;  // ascending: the low tile bits sit on the lanes
   } else {
     // four lane bits whose swizzle images are independent (one half-warp of
@@ -718,15 +757,20 @@ static uint64_t pdep_host(uint64_t x, uint64_t mask) {
 }
 
 // Address tables of a KIND_REG pass (see RegPassParams).
-static RegPassParams reg_params(const PlanPass &hp, const StageRec &first, const StageRec &last) {
+static RegPassParams reg_params(const PlanPass &hp, const StageRec &first, const StageRec &last,
+                                const int *outq) {
   RegPassParams p{};
   const uint32_t c = hp.c, cs = c - 1u, lowmask = (1u << c) - 1u;
   const uint32_t NT = 1u << (hp.T - hp.R);
+  for (uint32_t x = 0; x < hp.T; x++) p.oq[x] = uint8_t(outq[x]);
   for (int j = 0; j < (1 << hp.R); j++) {
     p.lo[j] = uint32_t(first.la[j]) * 8u;
     const uint32_t f = first.la[j], l = last.la[j];
     p.gi[j] = pdep_host(f >> c, hp.high_mask) + (f & lowmask);
-    p.go[j] = pdep_host(l >> c, hp.high_mask) + (l & lowmask);
+    uint64_t g = 0;
+    for (uint32_t x = 0; x < hp.T; x++)
+      if ((l >> x) & 1u) g |= uint64_t(1) << outq[x];
+    p.go[j] = g;
   }
   for (uint32_t k = 0; k < (1u << (hp.R - 1)); k++) p.ko[k] = pdep_host(uint64_t(k) * (NT >> cs), hp.high_mask);
   return p;
@@ -884,6 +928,8 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
     int lq[32];
     bool pairs;                 // fused with two-local-qubit phase terms
     int kfuse;                  // fusion width used
+    bool relabeled;             // SWAPs folded into the store mapping
+    int rho[64];                // qubit q's data ends at the loaded position of rho[q]
   };
   std::vector<PassH> passes;
 
@@ -970,16 +1016,22 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
       return w * (kx <= 2 ? 1.0 : (kx <= 4 ? 1.3 : 4.0));
     };
     int kf = (o.precision == 1) ? std::min(kmax, 4) : std::min(kmax, 2);
+    // SWAPs of tile qubits become a relabeling of the store (register passes only)
+    ph.relabeled = !o_smem && o.precision == 0;
+    for (int q = 0; q < 64; q++) ph.rho[q] = q;
     ph.pairs = pairs_ok(kf);
-    fuse_pass(gates, acc, Q, lpos, kf, ph.pairs, ph.ops);
+    fuse_pass(gates, acc, Q, lpos, kf, ph.pairs, ph.ops, ph.relabeled ? ph.rho : nullptr);
     if (o.precision != 1 && kmax > kf) {
       std::vector<HostOp> wide;
       const bool pw = pairs_ok(kmax);
-      fuse_pass(gates, acc, Q, lpos, kmax, pw, wide);
+      int rho2[64];
+      for (int q = 0; q < 64; q++) rho2[q] = q;
+      fuse_pass(gates, acc, Q, lpos, kmax, pw, wide, ph.relabeled ? rho2 : nullptr);
       if (est(wide) < est(ph.ops)) {
         ph.ops.swap(wide);
         ph.pairs = pw;
         kf = kmax;
+        std::copy(rho2, rho2 + 64, ph.rho);
       }
     }
     ph.kfuse = kf;
@@ -1034,6 +1086,21 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
     op_masks();
     // register stages when every block fits the registers of one thread
     const int T_ = int(hp.T);
+    // store mapping: local bit x is written to physical qubit outq[x]; SWAPs folded
+    // into the pass leave qubit q's data at local bit lpos[rho[q]]
+    int outq[32];
+    for (int x = 0; x < 32; x++) outq[x] = x < T_ ? ph.lq[x] : -1;
+    if (ph.relabeled)
+      for (int x = 0; x < T_; x++) outq[lpos[ph.rho[ph.lq[x]]]] = ph.lq[x];
+    std::vector<int> store_lanes(size_t(c), 0);
+    uint32_t store_low = 0;
+    for (int x = 0; x < T_; x++)
+      if (outq[x] < c) {
+        store_lanes[size_t(outq[x])] = x;
+        store_low |= 1u << x;
+      }
+    bool store_natural = true;
+    for (int q = 0; q < c; q++) store_natural &= store_lanes[size_t(q)] == q;
     // tensor-core stages (precision 1) when the pass fits the TC kernel
     if (o.precision == 1 && kmx <= 4 &&
         pack_tc_pass(ph.ops, omask, lpos, int(hp.T), c, hp, buf, plan.info)) {
@@ -1053,7 +1120,7 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
     std::vector<int> order;
     bool reg = use_reg;
     if (reg) {
-      assign_stages(ph.ops, omask, T_, c, Rb, stages);
+      assign_stages(ph.ops, omask, T_, c, Rb, stages, false, store_low, store_natural);
       // bytes of this pass's records as packed below (16-byte aligned pieces)
       size_t est = nops * sizeof(OpRec) + stages.size() * sizeof(StageRec) + 16;
       for (auto &op : ph.ops)
@@ -1064,11 +1131,13 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
         stages.clear();
       }
     }
-    if (!reg && ph.pairs) {
-      // the shared-memory kernel takes phase terms with one tile qubit only
+    if (!reg && (ph.pairs || ph.relabeled)) {
+      // the shared-memory kernel takes phase terms with one tile qubit only and
+      // stores in the loaded order
       ph.ops.clear();
       fuse_pass(gates, ph.acc, ph.Q, lpos, ph.kfuse, false, ph.ops);
       ph.pairs = false;
+      ph.relabeled = false;
       op_masks();
       hp.n_ops = uint32_t(nops);
     }
@@ -1162,7 +1231,8 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
       uint32_t ob = 0;
       StageRec first{}, last{};
       for (size_t si = 0; si < stages.size(); si++) {
-        StageRec sr = make_stage(stages[si], T_, c, Rb, si == 0, si + 1 == stages.size());
+        StageRec sr = make_stage(stages[si], T_, c, Rb, si == 0, si + 1 == stages.size(),
+                                 store_natural ? nullptr : &store_lanes);
         sr.op_begin = ob;
         ob += uint32_t(stages[si].ops.size());
         sr.op_end = ob;
@@ -1170,7 +1240,7 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
         if (si == 0) first = sr;
         if (si + 1 == stages.size()) last = sr;
       }
-      plan.rparams[p] = reg_params(hp, first, last);
+      plan.rparams[p] = reg_params(hp, first, last, outq);
       plan.info.n_stages += stages.size();
     }
     align16(buf);

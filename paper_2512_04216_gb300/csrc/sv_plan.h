@@ -16,6 +16,7 @@ struct GateM {
   int q[5] = {0, 0, 0, 0, 0};
   uint64_t mask = 0;
   bool diag = false;
+  bool swap = false;  // SWAP gate (a pure exchange of two qubits)
   std::vector<std::complex<double>> m;  // 2^k x 2^k row-major
 };
 
