@@ -565,6 +565,33 @@ def run_serve_mode(args):
         pl = serve.summarize(serve.run_plain(reqs))
         out["points"].append({"rate_factor": f, "rate_hz": rate, "served": srv, "plain": pl,
                               "circuits_per_s_ratio": srv["circuits_per_s"] / pl["circuits_per_s"]})
+    # runtime model (Eq. 1) calibrated on this GPU: held-out accuracy, and the
+    # highest-rate point again with shortest-predicted-first admission
+    from paper_2512_04216_gb300 import costmodel
+    t0 = time.perf_counter()
+    model = costmodel.calibrate(ns=tuple(range(8, 31, 2)), reps=1)
+    cal_s = time.perf_counter() - t0
+    import torch
+    from paper_2512_04216_gb300 import StateVector, capi
+    errs = []
+    for n, d, sd in ((11, 40, 1), (15, 70, 2), (19, 30, 3), (23, 50, 4), (27, 20, 5)):
+        c = W.random_layered(n, d, 900 + sd)
+        s = StateVector(n)
+        ir, keep = capi.to_ir(c)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        capi.sv_apply_circuit(s.h, ir, len(c))
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        s.close()
+        errs.append(abs(model.predict_ms(n, c) - e0.elapsed_time(e1)) / e0.elapsed_time(e1))
+    f = float(args.rate_factors.split(",")[-1])
+    specs = W.serving_requests(count, 4, f * plain_cap)
+    reqs = serve.make_requests(specs, W.random_layered)
+    spt = serve.summarize(serve.Server(cost_model=model).run(reqs))
+    out["cost_model"] = {"calibration_s": cal_s, "held_out_abs_rel_err": [round(e, 3) for e in errs],
+                         "rate_factor": f, "served_shortest_predicted_first": spt}
     best = max(p["circuits_per_s_ratio"] for p in out["points"])
     return {"metric": "mixed-stream circuits/s & p99 vs plain path", "value": best,
             "unit": "x plain circuits/s", "n_gpus": 1, "higher_is_better": True, "vs_baseline": None,

@@ -13,7 +13,7 @@ __all__ = ["capi", "StateVector", "Batch", "build"]
 
 
 def __getattr__(name):
-    if name in ("capi", "build", "statevector", "batch", "serve"):
+    if name in ("capi", "build", "statevector", "batch", "serve", "costmodel"):
         return importlib.import_module(f".{name}", __name__)
     if name == "StateVector":
         return importlib.import_module(".statevector", __name__).StateVector

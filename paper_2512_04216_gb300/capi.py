@@ -244,6 +244,14 @@ def sv_plan_stats(n_qubits, circuit, opts=None) -> dict:
     return info.as_dict()
 
 
+def sv_plan_stats_ir(n_qubits, ir, n_gates, opts=None) -> dict:
+    """sv_plan_stats on an already marshalled IR."""
+    info = sv_plan_info()
+    _check(_L.sv_plan_stats(n_qubits, ir.ctypes.data, int(n_gates),
+                            ctypes.byref(opts) if opts is not None else None, ctypes.byref(info)))
+    return info.as_dict()
+
+
 def sv_norm(h) -> float:
     out = ctypes.c_double()
     _check(_L.sv_norm(h, ctypes.byref(out)))

@@ -1,0 +1,174 @@
+"""GPU-calibrated runtime model (Eq. 1: T_total ~ sum over operations of a
+hardware-calibrated coefficient times the operation's complexity term).
+
+For this state-vector backend the operations are the plan's HBM passes and
+its dense-block arithmetic, and the end-of-circuit sampling:
+
+    T_apply(n, circuit) ~ C_pass(n) * passes + C_flop(n) * flops
+    T_shots(n, S)       ~ c1(n) + c2 * S
+
+`passes` and `flops` come from the host planner (sv_plan_stats, no GPU work).
+The coefficients are measured once on the device by `calibrate` over a grid of
+qubit counts (synthetic circuits of different flop densities, least squares per
+n) and interpolated in n with a monotone piecewise cubic Hermite interpolant
+(Fritsch-Carlson slopes) on log coefficients, as the paper does for its
+C_op(n) curves; T_shots is a linear regression in S.  The serving loop uses the
+predictions to order waiting requests (shortest predicted first).
+"""
+from __future__ import annotations
+
+import json
+import math
+from dataclasses import asdict, dataclass, field
+
+import numpy as np
+
+
+# ---------------------------------------------------------------------------
+# monotone piecewise cubic Hermite interpolation (Fritsch & Carlson, 1980)
+# ---------------------------------------------------------------------------
+
+def _pchip_slopes(x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    h = np.diff(x)
+    delta = np.diff(y) / h
+    m = np.zeros_like(y)
+    if len(x) == 2:
+        m[:] = delta[0]
+        return m
+    for k in range(1, len(x) - 1):
+        if delta[k - 1] * delta[k] <= 0.0:
+            m[k] = 0.0
+        else:
+            w1 = 2.0 * h[k] + h[k - 1]
+            w2 = h[k] + 2.0 * h[k - 1]
+            m[k] = (w1 + w2) / (w1 / delta[k - 1] + w2 / delta[k])
+    # one-sided three-point end slopes, kept shape-preserving
+    for end, (h0, h1, d0, d1) in ((0, (h[0], h[1], delta[0], delta[1])),
+                                  (len(x) - 1, (h[-1], h[-2], delta[-1], delta[-2]))):
+        s = ((2.0 * h0 + h1) * d0 - h0 * d1) / (h0 + h1)
+        if s * d0 <= 0.0:
+            s = 0.0
+        elif d0 * d1 <= 0.0 and abs(s) > abs(3.0 * d0):
+            s = 3.0 * d0
+        m[end] = s
+    return m
+
+
+def pchip(x, y):
+    """Returns f(t): the monotone cubic Hermite interpolant through (x, y)
+    (x strictly increasing), constant-slope extrapolation outside."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    if x.ndim != 1 or x.shape != y.shape or x.shape[0] < 2 or np.any(np.diff(x) <= 0):
+        raise ValueError("pchip needs >= 2 strictly increasing knots")
+    m = _pchip_slopes(x, y)
+
+    def f(t):
+        t = np.asarray(t, dtype=np.float64)
+        k = np.clip(np.searchsorted(x, t, side="right") - 1, 0, len(x) - 2)
+        h = x[k + 1] - x[k]
+        s = (t - x[k]) / h
+        h00 = (1 + 2 * s) * (1 - s) ** 2
+        h10 = s * (1 - s) ** 2
+        h01 = s * s * (3 - 2 * s)
+        h11 = s * s * (s - 1)
+        inner = h00 * y[k] + h10 * h * m[k] + h01 * y[k + 1] + h11 * h * m[k + 1]
+        lo = y[0] + m[0] * (t - x[0])
+        hi = y[-1] + m[-1] * (t - x[-1])
+        return np.where(t < x[0], lo, np.where(t > x[-1], hi, inner))
+
+    return f
+
+
+def linear_fit(x, y):
+    """Least-squares (c1, c2) of y ~ c1 + c2 x."""
+    A = np.stack([np.ones(len(x)), np.asarray(x, dtype=np.float64)], axis=1)
+    (c1, c2), *_ = np.linalg.lstsq(A, np.asarray(y, dtype=np.float64), rcond=None)
+    return float(c1), float(c2)
+
+
+# ---------------------------------------------------------------------------
+# the model
+# ---------------------------------------------------------------------------
+
+@dataclass
+class CostModel:
+    ns: list = field(default_factory=list)        # calibrated qubit counts
+    c_pass: list = field(default_factory=list)    # ms per pass at each n
+    c_flop: list = field(default_factory=list)    # ms per dense-block flop at each n
+    c_shot1: list = field(default_factory=list)   # ms of CDF build + fixed sampling cost at each n
+    c_shot2: float = 0.0                          # ms per shot
+
+    def _curve(self, vals, n):
+        v = np.maximum(np.asarray(vals, dtype=np.float64), 1e-30)
+        return float(np.exp(pchip(self.ns, np.log(v))(float(n))))
+
+    def apply_ms(self, n: int, passes: int, flops: float) -> float:
+        return self._curve(self.c_pass, n) * passes + self._curve(self.c_flop, n) * flops
+
+    def shots_ms(self, n: int, shots: int) -> float:
+        return self._curve(self.c_shot1, n) + self.c_shot2 * shots
+
+    def predict_ms(self, n: int, circuit, shots: int = 0, opts=None) -> float:
+        from . import capi
+        st = capi.sv_plan_stats(n, circuit, opts)
+        return self.apply_ms(n, st["n_passes"], float(st["flops"])) + (self.shots_ms(n, shots) if shots else 0.0)
+
+    def to_json(self) -> str:
+        return json.dumps(asdict(self))
+
+    @staticmethod
+    def from_json(s: str) -> "CostModel":
+        return CostModel(**json.loads(s))
+
+
+def calibrate(ns=(10, 12, 14, 16, 18, 20, 22, 24, 26, 28), reps: int = 2, opts=None, seed: int = 7) -> CostModel:
+    """Measures the coefficient curves on the current device (a one-time routine)."""
+    import torch
+
+    import workloads as W
+    from . import capi
+    from .statevector import StateVector
+
+    model = CostModel(ns=[int(n) for n in ns])
+    shot_samples = []
+    for n in ns:
+        rows, times = [], []
+        circuits = [W.random_layered(n, 8, seed + n), W.random_layered(n, 2, seed + 2 * n), W.qft(n), W.ghz(n)]
+        s = StateVector(n)
+        for c in circuits:
+            st = capi.sv_plan_stats(n, c, opts)
+            ir, keep = capi.to_ir(c)
+            best = math.inf
+            for _ in range(reps + 1):
+                s.reset(0)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s.stream)
+                capi.sv_apply_circuit(s.h, ir, len(c), opts)
+                e1.record(s.stream)
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            rows.append([st["n_passes"], float(st["flops"])])
+            times.append(best)
+        A = np.asarray(rows, dtype=np.float64)
+        sol, *_ = np.linalg.lstsq(A, np.asarray(times), rcond=None)
+        model.c_pass.append(max(float(sol[0]), 1e-6))
+        model.c_flop.append(max(float(sol[1]), 1e-18))
+        # sampling: a few shot counts on the last state
+        for S in (1, 1000, 100000):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s.stream)
+            s.sample(S, 3)
+            e1.record(s.stream)
+            torch.cuda.synchronize()
+            shot_samples.append((n, S, e0.elapsed_time(e1)))
+        s.close()
+    _, c2 = linear_fit([S for _, S, _ in shot_samples], [t for _, _, t in shot_samples])
+    model.c_shot2 = max(c2, 0.0)
+    for n in ns:
+        pts = [(S, t) for m, S, t in shot_samples if m == n]
+        c1 = float(np.mean([t - model.c_shot2 * S for S, t in pts]))
+        model.c_shot1.append(max(c1, 1e-4))
+    return model

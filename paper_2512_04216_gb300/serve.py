@@ -14,7 +14,9 @@ either a shot count or a Z-string mask) arrive over time; the server
     streams, admitted only while the sum of admitted footprints
     (2^n * 8 bytes plus measurement scratch) stays within an HBM budget, so
     their passes interleave on the device;
-  * records arrival, start and finish times of every request.
+  * records arrival, start and finish times of every request;
+  * with a calibrated cost model (costmodel.py, Eq. 1), admits waiting large
+    requests shortest predicted runtime first instead of fewest qubits first.
 
 The plain path (``run_plain``) serves the same requests one at a time: create
 a state, apply, measure, destroy, on one stream.  Control is Python; every
@@ -101,7 +103,7 @@ def _run_single(req: Request, stream, opts, t0: float) -> Result:
 
 class Server:
     def __init__(self, small_max_qubits: int = 14, streams: int = 8, hbm_budget: int | None = None,
-                 batch_max: int = 1024, opts=None, batch_opts=None):
+                 batch_max: int = 1024, opts=None, batch_opts=None, cost_model=None):
         self.small_max = small_max_qubits
         self.n_streams = streams
         if hbm_budget is None:
@@ -115,6 +117,22 @@ class Server:
         for _ in range(streams):
             self.streams.put(torch.cuda.Stream())
         self.batch_stream = torch.cuda.Stream()
+        self.cost_model = cost_model
+        self._pred = {}
+
+    def predicted_ms(self, r: Request) -> float:
+        """Cost-model runtime of a request (cached; planning on the host only)."""
+        if r.id not in self._pred:
+            st = capi.sv_plan_stats_ir(r.n, r.ir, r.n_gates, self.opts)
+            ms = self.cost_model.apply_ms(r.n, st["n_passes"], float(st["flops"]))
+            ms += self.cost_model.shots_ms(r.n, r.shots) if r.shots else self.cost_model.shots_ms(r.n, 0)
+            self._pred[r.id] = ms
+        return self._pred[r.id]
+
+    def _order_key(self, r: Request):
+        if self.cost_model is None:
+            return (r.n, r.t)
+        return (self.predicted_ms(r), r.t)
 
     def _run_batch(self, reqs, t0):
         t_start = time.perf_counter() - t0
@@ -154,7 +172,7 @@ class Server:
                     nxt += 1
                 # admit large requests while slots and memory allow (smallest first
                 # among those that arrived, so small-footprint work is not starved)
-                waiting_large.sort(key=lambda r: (r.n, r.t))
+                waiting_large.sort(key=self._order_key)
                 i = 0
                 while i < len(waiting_large):
                     r = waiting_large[i]

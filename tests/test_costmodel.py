@@ -1,0 +1,50 @@
+"""The runtime model's interpolation and regression pieces against closed forms
+and scipy's monotone cubic interpolant (CPU only)."""
+import numpy as np
+import pytest
+
+from paper_2512_04216_gb300 import costmodel as CM
+
+
+def test_pchip_reproduces_knots_and_cubics_of_lines():
+    x = np.array([10.0, 12, 15, 16, 20])
+    y = 3.0 * x - 7.0
+    f = CM.pchip(x, y)
+    assert np.allclose(f(x), y, atol=1e-12)
+    t = np.linspace(10, 20, 57)
+    assert np.allclose(f(t), 3.0 * t - 7.0, atol=1e-12)  # a line is reproduced exactly
+
+
+def test_pchip_is_monotone_on_monotone_data():
+    rng = np.random.default_rng(3)
+    x = np.cumsum(rng.uniform(0.5, 2.0, 9))
+    y = np.cumsum(rng.uniform(0.0, 3.0, 9))
+    t = np.linspace(x[0], x[-1], 2001)
+    v = CM.pchip(x, y)(t)
+    assert np.all(np.diff(v) >= -1e-12)
+
+
+def test_pchip_matches_scipy():
+    interp = pytest.importorskip("scipy.interpolate")
+    rng = np.random.default_rng(5)
+    for _ in range(5):
+        x = np.cumsum(rng.uniform(0.3, 2.0, 8))
+        y = rng.normal(size=8)
+        t = np.linspace(x[0], x[-1], 501)
+        want = interp.PchipInterpolator(x, y)(t)
+        assert np.allclose(CM.pchip(x, y)(t), want, atol=1e-10)
+
+
+def test_linear_fit_recovers_coefficients():
+    S = np.array([1, 10, 100, 1000, 1e5])
+    c1, c2 = CM.linear_fit(S, 0.25 + 3e-6 * S)
+    assert abs(c1 - 0.25) < 1e-12 and abs(c2 - 3e-6) < 1e-15
+
+
+def test_model_curves_interpolate_in_log_space():
+    m = CM.CostModel(ns=[10, 20, 30], c_pass=[1e-3, 1e-3 * 2 ** 10, 1e-3 * 2 ** 20],
+                     c_flop=[1e-12, 1e-12, 1e-12], c_shot1=[0.1, 0.2, 0.4], c_shot2=1e-5)
+    # 2^n growth is exact in log space
+    assert abs(m.apply_ms(25, 1, 0.0) - 1e-3 * 2 ** 15) < 1e-9
+    assert abs(m.shots_ms(20, 1000) - (0.2 + 1e-2)) < 1e-12
+    assert CM.CostModel.from_json(m.to_json()) == m
