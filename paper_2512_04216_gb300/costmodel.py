@@ -4,15 +4,16 @@ hardware-calibrated coefficient times the operation's complexity term).
 For this state-vector backend the operations are the plan's HBM passes and
 its dense-block arithmetic, and the end-of-circuit sampling:
 
-    T_apply(n, circuit) ~ C_pass(n) * passes + C_flop(n) * flops
+    T_apply(n, circuit) ~ c_fix + C_pass(n) * passes + c_flop * flops_eff
     T_shots(n, S)       ~ c1(n) + c2 * S
 
-`passes` and `flops` come from the host planner (sv_plan_stats, no GPU work).
-The coefficients are measured once on the device by `calibrate` over a grid of
-qubit counts (synthetic circuits of different flop densities, least squares per
-n) and interpolated in n with a monotone piecewise cubic Hermite interpolant
-(Fritsch-Carlson slopes) on log coefficients, as the paper does for its
-C_op(n) curves; T_shots is a linear regression in S.  The serving loop uses the
+`passes`, dense-block flops and phase ops (flops_eff counts a phase op as 48
+flops per amplitude) come from the host planner (sv_plan_stats, no GPU work).
+The coefficients are measured once on the device by `calibrate` (synthetic
+circuits of different densities over a grid of qubit counts, one joint least
+squares fit) and C_pass is interpolated in n with a monotone piecewise cubic
+Hermite interpolant (Fritsch-Carlson slopes) on log coefficients, as the paper
+does for its C_op(n) curves; T_shots is a linear regression in S.  The serving loop uses the
 predictions to order waiting requests (shortest predicted first).
 """
 from __future__ import annotations
@@ -94,17 +95,25 @@ def linear_fit(x, y):
 @dataclass
 class CostModel:
     ns: list = field(default_factory=list)        # calibrated qubit counts
-    c_pass: list = field(default_factory=list)    # ms per pass at each n
-    c_flop: list = field(default_factory=list)    # ms per dense-block flop at each n
+    c_pass: list = field(default_factory=list)    # ms per HBM pass at each n
+    c_flop: float = 0.0                           # ms per effective dense-block flop
+    c_fix: float = 0.0                            # ms per apply call (planning, upload)
     c_shot1: list = field(default_factory=list)   # ms of CDF build + fixed sampling cost at each n
     c_shot2: float = 0.0                          # ms per shot
+
+    # a phase op costs about as much per amplitude as 48 flops of dense block
+    PHASE_FLOPS = 48.0
+
+    @staticmethod
+    def eff_flops(n: int, stats: dict) -> float:
+        return float(stats["flops"]) + CostModel.PHASE_FLOPS * float(stats["n_phase"]) * float(1 << n)
 
     def _curve(self, vals, n):
         v = np.maximum(np.asarray(vals, dtype=np.float64), 1e-30)
         return float(np.exp(pchip(self.ns, np.log(v))(float(n))))
 
-    def apply_ms(self, n: int, passes: int, flops: float) -> float:
-        return self._curve(self.c_pass, n) * passes + self._curve(self.c_flop, n) * flops
+    def apply_ms(self, n: int, passes: int, eff_flops: float) -> float:
+        return self.c_fix + self._curve(self.c_pass, n) * passes + self.c_flop * eff_flops
 
     def shots_ms(self, n: int, shots: int) -> float:
         return self._curve(self.c_shot1, n) + self.c_shot2 * shots
@@ -112,7 +121,7 @@ class CostModel:
     def predict_ms(self, n: int, circuit, shots: int = 0, opts=None) -> float:
         from . import capi
         st = capi.sv_plan_stats(n, circuit, opts)
-        return self.apply_ms(n, st["n_passes"], float(st["flops"])) + (self.shots_ms(n, shots) if shots else 0.0)
+        return self.apply_ms(n, st["n_passes"], self.eff_flops(n, st)) + (self.shots_ms(n, shots) if shots else 0.0)
 
     def to_json(self) -> str:
         return json.dumps(asdict(self))
@@ -123,7 +132,9 @@ class CostModel:
 
 
 def calibrate(ns=(10, 12, 14, 16, 18, 20, 22, 24, 26, 28), reps: int = 2, opts=None, seed: int = 7) -> CostModel:
-    """Measures the coefficient curves on the current device (a one-time routine)."""
+    """Measures the coefficients on the current device (a one-time routine):
+    one joint least-squares fit of T = c_fix + C_pass(n) * passes + c_flop *
+    effective flops over synthetic circuits at every n in `ns`."""
     import torch
 
     import workloads as W
@@ -131,10 +142,10 @@ def calibrate(ns=(10, 12, 14, 16, 18, 20, 22, 24, 26, 28), reps: int = 2, opts=N
     from .statevector import StateVector
 
     model = CostModel(ns=[int(n) for n in ns])
-    shot_samples = []
-    for n in ns:
-        rows, times = [], []
-        circuits = [W.random_layered(n, 8, seed + n), W.random_layered(n, 2, seed + 2 * n), W.qft(n), W.ghz(n)]
+    rows, times, shot_samples = [], [], []
+    for i, n in enumerate(ns):
+        circuits = [W.random_layered(n, 8, seed + n), W.random_layered(n, 2, seed + 2 * n),
+                    W.random_layered(n, 24, seed + 3 * n), W.qft(n), W.ghz(n), W.ghz(n)[:1]]
         s = StateVector(n)
         for c in circuits:
             st = capi.sv_plan_stats(n, c, opts)
@@ -149,13 +160,12 @@ def calibrate(ns=(10, 12, 14, 16, 18, 20, 22, 24, 26, 28), reps: int = 2, opts=N
                 e1.record(s.stream)
                 torch.cuda.synchronize()
                 best = min(best, e0.elapsed_time(e1))
-            rows.append([st["n_passes"], float(st["flops"])])
+            row = [0.0] * (len(ns) + 2)
+            row[i] = float(st["n_passes"])
+            row[len(ns)] = CostModel.eff_flops(n, st)
+            row[len(ns) + 1] = 1.0
+            rows.append(row)
             times.append(best)
-        A = np.asarray(rows, dtype=np.float64)
-        sol, *_ = np.linalg.lstsq(A, np.asarray(times), rcond=None)
-        model.c_pass.append(max(float(sol[0]), 1e-6))
-        model.c_flop.append(max(float(sol[1]), 1e-18))
-        # sampling: a few shot counts on the last state
         for S in (1, 1000, 100000):
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -165,6 +175,13 @@ def calibrate(ns=(10, 12, 14, 16, 18, 20, 22, 24, 26, 28), reps: int = 2, opts=N
             torch.cuda.synchronize()
             shot_samples.append((n, S, e0.elapsed_time(e1)))
         s.close()
+    A = np.asarray(rows, dtype=np.float64)
+    scale = np.maximum(np.abs(A).max(axis=0), 1e-30)
+    sol, *_ = np.linalg.lstsq(A / scale, np.asarray(times), rcond=None)
+    sol = sol / scale
+    model.c_pass = [max(float(v), 1e-6) for v in sol[:len(ns)]]
+    model.c_flop = max(float(sol[len(ns)]), 0.0)
+    model.c_fix = max(float(sol[len(ns) + 1]), 0.0)
     _, c2 = linear_fit([S for _, S, _ in shot_samples], [t for _, _, t in shot_samples])
     model.c_shot2 = max(c2, 0.0)
     for n in ns:

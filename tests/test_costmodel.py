@@ -42,9 +42,10 @@ def test_linear_fit_recovers_coefficients():
 
 
 def test_model_curves_interpolate_in_log_space():
-    m = CM.CostModel(ns=[10, 20, 30], c_pass=[1e-3, 1e-3 * 2 ** 10, 1e-3 * 2 ** 20],
-                     c_flop=[1e-12, 1e-12, 1e-12], c_shot1=[0.1, 0.2, 0.4], c_shot2=1e-5)
+    m = CM.CostModel(ns=[10, 20, 30], c_pass=[1e-3, 1e-3 * 2 ** 10, 1e-3 * 2 ** 20], c_flop=1e-12, c_fix=0.05,
+                     c_shot1=[0.1, 0.2, 0.4], c_shot2=1e-5)
     # 2^n growth is exact in log space
-    assert abs(m.apply_ms(25, 1, 0.0) - 1e-3 * 2 ** 15) < 1e-9
+    assert abs(m.apply_ms(25, 1, 0.0) - (0.05 + 1e-3 * 2 ** 15)) < 1e-9
+    assert abs(m.apply_ms(20, 2, 1e9) - (0.05 + 2 * 1e-3 * 2 ** 10 + 1e-3)) < 1e-9
     assert abs(m.shots_ms(20, 1000) - (0.2 + 1e-2)) < 1e-12
     assert CM.CostModel.from_json(m.to_json()) == m
