@@ -316,9 +316,10 @@ struct RegLayout {
   size_t off_in, off_x, off_seg, off_tt, off_data, total;
 };
 
-// KIND_REG passes with 32 amplitudes per thread load their first stage straight from
-// HBM (no prefetch buffer), so four CTAs fit an SM; register passes keep no segment table.
-__host__ __device__ constexpr bool reg_direct(uint32_t R) { return R == 5; }
+// KIND_REG passes with 32 amplitudes per thread keep no separate prefetch buffer:
+// the next tile is prefetched into the exchange buffer during the last stage, so
+// four CTAs fit an SM.  Register passes keep no segment table.
+__host__ __device__ constexpr bool reg_shared_prefetch(uint32_t R) { return R == 5; }
 
 __host__ __device__ inline RegLayout reg_layout(uint32_t T, uint32_t c, uint32_t ns, uint32_t data_bytes,
                                                 uint32_t R = 4, bool reg = false) {
@@ -329,7 +330,7 @@ __host__ __device__ inline RegLayout reg_layout(uint32_t T, uint32_t c, uint32_t
   r.ns = ns;
   size_t o = 0;
   r.off_in = o;
-  if (!(reg && reg_direct(R))) o += size_t(r.L) * 8;
+  if (!(reg && reg_shared_prefetch(R))) o += size_t(r.L) * 8;
   r.off_x = o; o += size_t(r.L) * 8;
   r.off_seg = o;
   if (!reg) o += size_t(r.nseg) * 8;
@@ -354,7 +355,7 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 4 : 2) : (NTMA
   const uint32_t ns = P->n_stages;
   const uint32_t data_off = P->ops_off, data_bytes = P->data_bytes;
   const uint64_t outer_mask = P->outer_mask, n_tiles = P->n_tiles;
-  constexpr bool kDirect = reg_direct(R);
+  constexpr bool kShared = reg_shared_prefetch(R);
   const RegLayout lay = reg_layout(T, c, ns, data_bytes, R, true);
   float2 *buf_in = reinterpret_cast<float2 *>(smem + lay.off_in);
   float2 *buf_x = reinterpret_cast<float2 *>(smem + lay.off_x);
@@ -379,7 +380,6 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 4 : 2) : (NTMA
       if ((tid >> i) & 1u) LB |= 1u << stages[s].tb[i];
     tt[s * NT + tid] = LB | (swz(LB) << 16);
   }
-  const uint32_t lowmask = (1u << c) - 1u;
   const uint32_t cs = c - 1u, cmask = (1u << cs) - 1u;
   constexpr int NK = NR / 2;  // 16-byte chunks per thread per tile
   const uint32_t sin = static_cast<uint32_t>(__cvta_generic_to_shared(buf_in));
@@ -393,11 +393,6 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 4 : 2) : (NTMA
       if ((LB >> x) & 1u) t_st |= uint64_t(1) << prm.oq[x];
   }
   const uint64_t t_cp = pdep_u64(tid >> cs, hm) + (uint64_t(tid & cmask) << 1);
-  uint64_t t_gl;
-  {
-    const uint32_t LB = tt[tid] & 0xffffu;
-    t_gl = pdep_u64(LB >> c, hm) + (LB & lowmask);
-  }
 
   // 32-amplitude passes prefetch the next tile into the exchange buffer while
   // their last stage computes (the buffer is free once the last exchange is read)
@@ -405,7 +400,7 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 4 : 2) : (NTMA
   uint64_t tile = blockIdx.x;
   uint64_t base = tile < n_tiles ? pdep_u64(tile, outer_mask) : 0;
   if (tile < n_tiles) {
-    const uint32_t dst = kDirect ? sx : sin;
+    const uint32_t dst = kShared ? sx : sin;
 #pragma unroll
     for (int k = 0; k < NK; k++) cp_async16_s(dst + (tid + k * NT) * 16u, amp + base + t_cp + prm.ko[k]);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -416,7 +411,7 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 4 : 2) : (NTMA
   while (tile < n_tiles) {
     const uint64_t next = tile + gridDim.x;
     const uint64_t base_next = next < n_tiles ? pdep_u64(next, outer_mask) : 0;
-    if constexpr (kDirect) {
+    if constexpr (kShared) {
       asm volatile("cp.async.wait_all;\n" ::: "memory");
       __syncthreads();
 #pragma unroll
@@ -460,7 +455,7 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 4 : 2) : (NTMA
 #pragma unroll
         for (int j = 0; j < NR; j++) v[j] = lds64(sx + (xo[j] ^ PB));
       }
-      if (kDirect && s + 1 == ns) {
+      if (kShared && s + 1 == ns) {
         __syncthreads();  // every thread has read the exchange buffer
         if (next < n_tiles) {
 #pragma unroll

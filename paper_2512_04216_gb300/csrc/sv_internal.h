@@ -78,7 +78,6 @@ struct alignas(16) StageRec {
 // constant-bank operand).  A thread adds its own part once per CTA.
 struct RegPassParams {
   uint32_t lo[32];      // first stage: la[j] * 8, byte offset in the natural-order tile
-  uint64_t gi[32];      // first stage: amplitude offset of la[j] from the tile base in HBM
   uint64_t go[32];      // last stage: amplitude offset of la[j] from the tile base in HBM
   uint64_t ko[16];      // prefetch: amplitude offset of 16-byte chunk row k (chunks k*NT..)
   uint8_t oq[16];       // store: physical qubit written from local bit x (SWAPs folded in)

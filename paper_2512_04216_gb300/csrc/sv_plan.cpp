@@ -760,13 +760,12 @@ static uint64_t pdep_host(uint64_t x, uint64_t mask) {
 static RegPassParams reg_params(const PlanPass &hp, const StageRec &first, const StageRec &last,
                                 const int *outq) {
   RegPassParams p{};
-  const uint32_t c = hp.c, cs = c - 1u, lowmask = (1u << c) - 1u;
+  const uint32_t c = hp.c, cs = c - 1u;
   const uint32_t NT = 1u << (hp.T - hp.R);
   for (uint32_t x = 0; x < hp.T; x++) p.oq[x] = uint8_t(outq[x]);
   for (int j = 0; j < (1 << hp.R); j++) {
     p.lo[j] = uint32_t(first.la[j]) * 8u;
-    const uint32_t f = first.la[j], l = last.la[j];
-    p.gi[j] = pdep_host(f >> c, hp.high_mask) + (f & lowmask);
+    const uint32_t l = last.la[j];
     uint64_t g = 0;
     for (uint32_t x = 0; x < hp.T; x++)
       if ((l >> x) & 1u) g |= uint64_t(1) << outq[x];
