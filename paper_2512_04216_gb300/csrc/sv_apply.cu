@@ -309,6 +309,7 @@ __device__ __forceinline__ void reg_rphase(float2 (&v)[1 << R], const uint8_t *_
 // (natural order: its lanes are the low tile bits), later stages exchange
 // through the swizzled `buf_x`, and the last stage stores straight to HBM.
 constexpr int kMaxStages = 64;     // stage tables kept in shared memory
+constexpr int kPlanMismatch = 2;   // error word bit: a pass's device records differ from the host's
 constexpr uint32_t kMaxPassData = 160 * 1024;
 
 struct RegLayout {
@@ -347,7 +348,7 @@ __host__ __device__ inline RegLayout reg_layout(uint32_t T, uint32_t c, uint32_t
 template <int R, int NTMAX>
 __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 4 : 2) : (NTMAX <= 256 ? 2 : 1))
     k_pass_reg(float2 *__restrict__ amp, const uint8_t *__restrict__ plan, uint32_t pass_off,
-               const __grid_constant__ RegPassParams prm) {
+               const __grid_constant__ RegPassParams prm, int *__restrict__ err) {
   constexpr int NR = 1 << R;
   extern __shared__ __align__(16) unsigned char smem[];
   const PlanPass *P = reinterpret_cast<const PlanPass *>(plan + pass_off);
@@ -355,6 +356,12 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 4 : 2) : (NTMA
   const uint32_t ns = P->n_stages;
   const uint32_t data_off = P->ops_off, data_bytes = P->data_bytes;
   const uint64_t outer_mask = P->outer_mask, n_tiles = P->n_tiles;
+  // the launch's shared memory was sized from the host's copy of these fields
+  if (T != prm.chk[0] || ns != prm.chk[1] || data_bytes != prm.chk[2] || data_off != prm.chk[3] ||
+      P->R != uint32_t(R) || ns == 0 || ns > uint32_t(kMaxStages)) {
+    if (threadIdx.x == 0) atomicOr(err, kPlanMismatch);
+    return;
+  }
   constexpr bool kShared = reg_shared_prefetch(R);
   const RegLayout lay = reg_layout(T, c, ns, data_bytes, R, true);
   float2 *buf_in = reinterpret_cast<float2 *>(smem + lay.off_in);
@@ -487,7 +494,7 @@ constexpr size_t kSmemOptIn = 232448;  // 227 KiB per CTA on sm_100-class parts
 
 template <int R, int NTMAX>
 static cudaError_t launch_reg(float2 *amp, const uint8_t *plan, uint32_t off, const PlanPass &hp,
-                              const RegPassParams &prm, cudaStream_t st) {
+                              const RegPassParams &prm, int *err, cudaStream_t st) {
   const RegLayout lay = reg_layout(hp.T, hp.c, hp.n_stages, hp.data_bytes, R, true);
   static unsigned long long configured = 0;
   static int sms[64] = {0};
@@ -509,7 +516,7 @@ static cudaError_t launch_reg(float2 *amp, const uint8_t *plan, uint32_t off, co
   if (per_sm < 1) per_sm = 1;
   const uint64_t want = uint64_t(sms[dev < 64 ? dev : 0] > 0 ? sms[dev < 64 ? dev : 0] : 1) * per_sm;
   const unsigned grid = unsigned(hp.n_tiles < want ? hp.n_tiles : want);
-  k_pass_reg<R, NTMAX><<<grid, nt, lay.total, st>>>(amp, plan, off, prm);
+  k_pass_reg<R, NTMAX><<<grid, nt, lay.total, st>>>(amp, plan, off, prm, err);
   count_launch();
   return cudaGetLastError();
 }
@@ -789,14 +796,14 @@ cudaError_t launch_pass(float2 *amp, const uint8_t *plan_dev, uint32_t pass_off,
     return launch_tc<512>(amp, plan_dev, pass_off, hp, err, stream);
   }
   if (hp.kind == KIND_REG) {
-    if (!prm) return cudaErrorInvalidValue;
+    if (!prm || !err) return cudaErrorInvalidValue;
     if (hp.R == 5) {
-      if (hp.T <= 12) return launch_reg<5, 128>(amp, plan_dev, pass_off, hp, *prm, stream);
-      return launch_reg<5, 256>(amp, plan_dev, pass_off, hp, *prm, stream);
+      if (hp.T <= 12) return launch_reg<5, 128>(amp, plan_dev, pass_off, hp, *prm, err, stream);
+      return launch_reg<5, 256>(amp, plan_dev, pass_off, hp, *prm, err, stream);
     }
     if (hp.R != 4) return cudaErrorInvalidValue;
-    if (hp.T <= 12) return launch_reg<4, 256>(amp, plan_dev, pass_off, hp, *prm, stream);
-    return launch_reg<4, 512>(amp, plan_dev, pass_off, hp, *prm, stream);
+    if (hp.T <= 12) return launch_reg<4, 256>(amp, plan_dev, pass_off, hp, *prm, err, stream);
+    return launch_reg<4, 512>(amp, plan_dev, pass_off, hp, *prm, err, stream);
   }
   switch (hp.kmax) {
     case 0:

@@ -164,6 +164,42 @@ __device__ void batch_expect(const float2 *amps, uint32_t n, uint64_t zmask, dou
   __syncthreads();
 }
 
+// Whether a circuit's pass records and their ops stay inside the plan buffer
+// and the kernel's shared-memory layout (the host builds them that way; this
+// guards the launch against a corrupted buffer: the circuit is skipped and the
+// error word set instead of indexing out of range).
+template <int KMAX>
+__device__ __forceinline__ bool batch_plan_ok(const uint8_t *plans, uint64_t plans_size, const BatchCirc &C) {
+  if (C.n < 1 || C.n > uint32_t(kBatchMaxQubits)) return false;
+  if (C.plan_off + uint64_t(C.n_passes) * sizeof(PlanPass) > plans_size) return false;
+  const uint8_t *plan = plans + C.plan_off;
+  for (uint32_t p = 0; p < C.n_passes; p++) {
+    const PlanPass P = reinterpret_cast<const PlanPass *>(plan)[p];
+    if (P.T < 1 || P.T > uint32_t(kBatchSmemQubits) || P.c < 1 || P.c > P.T || P.T > C.n) return false;
+    if (C.n <= uint32_t(kBatchSmemQubits) && P.T != C.n) return false;
+    if (P.n_tiles != (uint64_t(1) << (C.n - P.T))) return false;
+    if (C.plan_off + P.ops_off + uint64_t(P.n_ops) * sizeof(OpRec) > plans_size) return false;
+    const OpRec *ops = reinterpret_cast<const OpRec *>(plan + P.ops_off);
+    for (uint32_t o = 0; o < P.n_ops; o++) {
+      const OpRec op = ops[o];
+      if (op.type == OP_DENSE) {
+        if (op.k < 1 || op.k > KMAX) return false;
+        for (int m = 0; m < op.k; m++)
+          if (op.lb[m] >= P.T) return false;
+        if (C.plan_off + op.data_off + (uint64_t(8) << (2 * op.k)) > plans_size) return false;
+      } else if (op.type == OP_PHASE) {
+        if (C.plan_off + op.data_off + uint64_t(op.count) * sizeof(PhaseTerm) > plans_size) return false;
+        const PhaseTerm *t = reinterpret_cast<const PhaseTerm *>(plan + op.data_off);
+        for (uint32_t i = 0; i < op.count; i++)
+          if (t[i].la < -1 || t[i].la >= int32_t(P.T)) return false;
+      } else {
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
 template <int KMAX>
 __device__ __forceinline__ void batch_ops(float2 *tile, float2 *mat, uint32_t *acc, float2 *tab,
                                           const uint8_t *plan, const PlanPass &P, uint64_t base) {
@@ -193,7 +229,7 @@ __global__ void __launch_bounds__(kBatchNT) k_batch(const uint8_t *__restrict__ 
                                                    const BatchCirc *__restrict__ circs, uint32_t n_circ,
                                                    float2 *__restrict__ arena, double *__restrict__ scratch,
                                                    uint64_t *__restrict__ out, double *__restrict__ ex,
-                                                   uint32_t *__restrict__ counter) {
+                                                   uint32_t *__restrict__ counter, uint64_t plans_size) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_next;
   const BatchLayout L = batch_layout(KMAX);
@@ -211,6 +247,10 @@ __global__ void __launch_bounds__(kBatchNT) k_batch(const uint8_t *__restrict__ 
     __syncthreads();
     if (ci >= n_circ) break;
     const BatchCirc C = circs[ci];
+    if (!batch_plan_ok<KMAX>(plans, plans_size, C)) {
+      if (threadIdx.x == 0) atomicOr(counter + 1, 1u);
+      continue;
+    }
     const uint8_t *plan = plans + C.plan_off;
     const uint32_t n = C.n, N = 1u << n;
     if (n <= uint32_t(kBatchSmemQubits)) {
@@ -267,6 +307,7 @@ struct sv_batch {
   std::vector<size_t> order;         // order[i] = caller index of launch slot i
   std::vector<size_t> slot;          // slot[caller index] = launch slot
   uint8_t *plan_dev = nullptr;
+  uint64_t plans_size = 0;
   BatchCirc *circ_dev = nullptr;
   float2 *arena = nullptr;
   double *scratch = nullptr;
@@ -325,7 +366,7 @@ cudaError_t enqueue_batch(sv_batch *b, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   k_batch<KMAX><<<b->grid, kBatchNT, batch_layout(KMAX).total, st>>>(b->plan_dev, b->circ_dev, uint32_t(b->n_circ),
                                                                     b->arena, b->scratch, b->out, b->ex,
-                                                                    b->counter);
+                                                                    b->counter, b->plans_size);
   return cudaGetLastError();
 }
 
@@ -465,7 +506,9 @@ int sv_batch_create(size_t n_circ, const sv_gate *const *irs, const size_t *n_ga
   if (e == cudaSuccess) e = cudaMalloc(&b->out, std::max<uint64_t>(outs, 2) * sizeof(uint64_t));
   if (e == cudaSuccess) e = cudaMalloc(&b->ex, 2 * n_circ * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(b->ex, 0, 2 * n_circ * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&b->counter, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&b->counter, 2 * sizeof(uint32_t));  // work queue, error word
+  if (e == cudaSuccess) e = cudaMemset(b->counter, 0, 2 * sizeof(uint32_t));
+  b->plans_size = plans.size();
   if (e == cudaSuccess) e = cudaMemcpy(b->plan_dev, plans.data(), plans.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(b->circ_dev, b->circ.data(), n_circ * sizeof(BatchCirc), cudaMemcpyHostToDevice);
@@ -505,8 +548,12 @@ int sv_batch_launch(sv_batch *b) {
 
 int sv_batch_synchronize(sv_batch *b) {
   if (!b) return set_last_error(SV_ERR_ARG, "null batch");
-  const cudaError_t e = cudaStreamSynchronize(b->stream);
+  cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return set_last_error(SV_ERR_CUDA, "sv_batch_synchronize: %s", cudaGetErrorString(e));
+  uint32_t bad = 0;
+  e = cudaMemcpy(&bad, b->counter + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return set_last_error(SV_ERR_CUDA, "sv_batch_synchronize: %s", cudaGetErrorString(e));
+  if (bad) return set_last_error(SV_ERR_STATE, "batched launch skipped circuits whose plan records failed validation");
   return SV_OK;
 }
 

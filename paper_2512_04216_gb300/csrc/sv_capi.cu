@@ -185,6 +185,11 @@ int check_device_error(sv_state *s) {
   CK(s, cudaMemcpy(&e, s->derr, sizeof(int), cudaMemcpyDeviceToHost));
   if (e) {
     CK(s, cudaMemset(s->derr, 0, sizeof(int)));
+    if (e & 2) {
+      s->poisoned = true;
+      return fail(SV_ERR_STATE, "a pass found its device plan records different from the host's; the state is "
+                                "not updated by that pass");
+    }
     return fail(SV_ERR_TIMEOUT, "a bounded device-side wait gave up (tensor-core pass)");
   }
   return SV_OK;

@@ -81,6 +81,8 @@ struct RegPassParams {
   uint64_t go[32];      // last stage: amplitude offset of la[j] from the tile base in HBM
   uint64_t ko[16];      // prefetch: amplitude offset of 16-byte chunk row k (chunks k*NT..)
   uint8_t oq[16];       // store: physical qubit written from local bit x (SWAPs folded in)
+  uint32_t chk[4];      // the host's T, n_stages, data_bytes, ops_off of this pass: the kernel
+                        // compares them with the device copy before using the records
 };
 
 // Columns of the shared-memory swizzle: local bit b < 4 maps to itself, local

@@ -772,6 +772,10 @@ static RegPassParams reg_params(const PlanPass &hp, const StageRec &first, const
     p.go[j] = g;
   }
   for (uint32_t k = 0; k < (1u << (hp.R - 1)); k++) p.ko[k] = pdep_host(uint64_t(k) * (NT >> cs), hp.high_mask);
+  p.chk[0] = hp.T;
+  p.chk[1] = hp.n_stages;
+  p.chk[2] = hp.data_bytes;
+  p.chk[3] = hp.ops_off;
   return p;
 }
 
