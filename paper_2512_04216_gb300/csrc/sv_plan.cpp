@@ -772,10 +772,6 @@ static RegPassParams reg_params(const PlanPass &hp, const StageRec &first, const
     p.go[j] = g;
   }
   for (uint32_t k = 0; k < (1u << (hp.R - 1)); k++) p.ko[k] = pdep_host(uint64_t(k) * (NT >> cs), hp.high_mask);
-  p.chk[0] = hp.T;
-  p.chk[1] = hp.n_stages;
-  p.chk[2] = hp.data_bytes;
-  p.chk[3] = hp.ops_off;
   return p;
 }
 
@@ -1248,6 +1244,14 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
     }
     align16(buf);
     hp.data_bytes = uint32_t(buf.size() - hp.ops_off);
+    if (reg) {
+      // the kernel checks its device copy of the records against these
+      RegPassParams &rp = plan.rparams[p];
+      rp.chk[0] = hp.T;
+      rp.chk[1] = hp.n_stages;
+      rp.chk[2] = hp.data_bytes;
+      rp.chk[3] = hp.ops_off;
+    }
     std::memcpy(buf.data() + p * sizeof(PlanPass), &hp, sizeof(hp));
     plan.passes[p] = hp;
     plan.pass_offs[p] = uint32_t(p * sizeof(PlanPass));
