@@ -85,6 +85,10 @@ class Oracle:
         L.orc_take_qubit.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
         L.orc_take_qubit.restype = None
         L.orc_expect_z.restype = ctypes.c_double
+        L.orc_alias_build.argtypes = [P, u64, P, P, P]
+        L.orc_alias_build.restype = ctypes.c_int
+        L.orc_alias_sample.argtypes = [P, P, u64, P, u64, P]
+        L.orc_alias_sample.restype = None
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_set_threads.restype = None
         L.orc_max_threads.argtypes = []
@@ -189,6 +193,29 @@ class Oracle:
         return out
 
 
+    def alias_build(self, psi):
+        """Walker alias table of |psi|^2: (Q uint64[N], own uint32[N], alias uint32[N])."""
+        psi = np.ascontiguousarray(psi, dtype=np.complex128)
+        N = psi.shape[0]
+        Q = np.empty(N, dtype=np.uint64)
+        own = np.empty(N, dtype=np.uint32)
+        alias = np.empty(N, dtype=np.uint32)
+        rc = self.L.orc_alias_build(psi.ctypes.data, N, Q.ctypes.data, own.ctypes.data, alias.ctypes.data)
+        if rc != 0:
+            raise ValueError("state has no weight")
+        return Q, own, alias
+
+    def alias_sample(self, own, alias, uniforms):
+        """Draws from an alias table for the given uniforms (uint64[S])."""
+        own = np.ascontiguousarray(own, dtype=np.uint32)
+        alias = np.ascontiguousarray(alias, dtype=np.uint32)
+        u = np.ascontiguousarray(uniforms, dtype=np.float64)
+        out = np.empty(u.shape[0], dtype=np.uint64)
+        self.L.orc_alias_sample(own.ctypes.data, alias.ctypes.data, own.shape[0], u.ctypes.data,
+                                u.shape[0], out.ctypes.data)
+        return out
+
+
 def basis(n: int, index: int = 0) -> np.ndarray:
     psi = np.zeros(1 << n, dtype=np.complex128)
     psi[index] = 1.0
@@ -220,6 +247,8 @@ def measure(psi, q, u): return default().measure(psi, q, u)
 def reset_qubit(psi, q, u): return default().reset_qubit(psi, q, u)
 def kron(a, b): return default().kron(a, b)
 def take_qubit(psi, q, v): return default().take_qubit(psi, q, v)
+def alias_build(psi): return default().alias_build(psi)
+def alias_sample(own, alias, uniforms): return default().alias_sample(own, alias, uniforms)
 
 
 def fidelity(a, b) -> float:

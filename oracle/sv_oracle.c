@@ -47,6 +47,22 @@
  *   - a qubit q known to be in the basis state |v> (e.g. just measured) leaves
  *     the register: out[j] = psi[j with bit v inserted at position q].
  *
+ * Alias sampling (§III-C: shots are drawn by alias sampling, O(1) work per
+ * shot, after Walker 1974).  One bucket per basis state, capacity C = 2^31
+ * units; bucket i keeps own_i units for outcome i and gives the rest to
+ * alias_i:
+ *   - weights are quantised: q_i = p_i * (N / W) with W = sum_i p_i
+ *     (sequential double), Q_i = q_i * 2^31 rounded to the nearest integer;
+ *     everything after that is exact integer arithmetic;
+ *   - items with Q_i < C are light, the others heavy, each list in index
+ *     order; the light items are walked in order, each taking its deficit
+ *     C - Q_i from the current heavy item; a heavy item whose remainder drops
+ *     below C becomes a light bucket of that remainder, filled from the next
+ *     heavy item; the last heavy item, and any never reached, keep a full
+ *     bucket (own = C, alias = itself);
+ *   - a draw with uniform u in [0,1): x = u * N, i = floor(x), f = x - i; it
+ *     is i when f * 2^31 < own_i, else alias_i.
+ *
  * Parity pinning: see tests/test_oracle_pins.py (closed forms for GHZ and QFT,
  * an explicit DFT matrix, Kronecker-product brute force for n <= 8, textbook
  * gate identities, norm preservation, circuit * inverse = |0...0>, sampler and
@@ -335,5 +351,70 @@ void orc_take_qubit(const cplx *psi, int n, int q, int v, cplx *out) {
   for (uint64_t j = 0; j < half; j++) {
     const uint64_t i = ((j & ~low) << 1) | (j & low) | ((uint64_t)v << q);
     out[j] = psi[i];
+  }
+}
+
+/*
+ * Walker alias table of p_i = |psi_i|^2 (see the header): Q (quantised
+ * weights), own (units kept by bucket i) and alias (its other outcome).
+ * Returns 0, or -1 when the state has no weight.
+ */
+int orc_alias_build(const cplx *psi, uint64_t N, uint64_t *Q, uint32_t *own, uint32_t *alias) {
+  const uint64_t C = (uint64_t)1 << 31;
+  double W = 0.0;
+  for (uint64_t i = 0; i < N; i++) {
+    double re = creal(psi[i]), im = cimag(psi[i]);
+    W += re * re + im * im;
+  }
+  if (!(W > 0.0)) return -1;
+  const double scale = (double)N / W;
+  uint64_t *light = (uint64_t *)malloc(N * sizeof(uint64_t));
+  uint64_t *heavy = (uint64_t *)malloc(N * sizeof(uint64_t));
+  uint64_t nl = 0, nh = 0;
+  for (uint64_t i = 0; i < N; i++) {
+    double re = creal(psi[i]), im = cimag(psi[i]);
+    double p = re * re + im * im;
+    Q[i] = (uint64_t)nearbyint(p * scale * 2147483648.0);
+    if (Q[i] < C) light[nl++] = i;
+    else heavy[nh++] = i;
+  }
+  if (nh == 0) {
+    free(light);
+    free(heavy);
+    return -1;
+  }
+  uint64_t j = 0;
+  uint64_t r = Q[heavy[0]]; /* units the current heavy item still holds */
+  for (uint64_t k = 0; k < nl; k++) {
+    const uint64_t i = light[k];
+    own[i] = (uint32_t)Q[i];
+    alias[i] = (uint32_t)heavy[j];
+    r -= C - Q[i];
+    while (r < C && j + 1 < nh) {
+      /* heavy item j is used up: its bucket keeps r units, the next heavy fills the rest */
+      own[heavy[j]] = (uint32_t)r;
+      alias[heavy[j]] = (uint32_t)heavy[j + 1];
+      r = Q[heavy[j + 1]] - (C - r);
+      j++;
+    }
+  }
+  for (uint64_t m = j; m < nh; m++) {
+    own[heavy[m]] = (uint32_t)C;
+    alias[heavy[m]] = (uint32_t)heavy[m];
+  }
+  free(light);
+  free(heavy);
+  return 0;
+}
+
+/* Draws from an alias table: out[s] for uniform u[s] (see the header). */
+void orc_alias_sample(const uint32_t *own, const uint32_t *alias, uint64_t N, const double *u,
+                      uint64_t S, uint64_t *out) {
+  for (uint64_t s = 0; s < S; s++) {
+    const double x = u[s] * (double)N;
+    uint64_t i = (uint64_t)x;
+    if (i >= N) i = N - 1;
+    const double f = x - (double)i;
+    out[s] = (f * 2147483648.0 < (double)own[i]) ? i : alias[i];
   }
 }

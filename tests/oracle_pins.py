@@ -441,6 +441,100 @@ def pin_pblock(o):
     _close(o.take_qubit(post, 1, b), _basis(3, 0b111), what="take a measured GHZ qubit")
 
 
+def load_alias_golden():
+    rows, draws = {}, []
+    with open(os.path.join(GOLDEN, "alias_worked_example.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            parts = line.split()
+            if parts[0] == "draw":
+                draws.append((float(parts[1]), int(parts[2])))
+            else:
+                rows[parts[0]] = [int(v) for v in parts[1:]]
+    return rows, draws
+
+
+ALIAS_C = 1 << 31
+
+
+def alias_masses(own, alias):
+    """Units of bucket capacity that reach each outcome: own_i for i itself,
+    C - own_k for every bucket k aliasing i."""
+    N = own.shape[0]
+    own = own.astype(np.int64)
+    given = np.bincount(alias.astype(np.int64), weights=(ALIAS_C - own).astype(np.float64), minlength=N)
+    return own + given.astype(np.int64)
+
+
+def pin_alias(o):
+    """Alias table: a hand-worked example; on random states, every light item's
+    units reach it exactly and the table's only discrepancy from the quantised
+    weights is the quantisation residual |N*C - sum Q|; light items alias the
+    first heavy item whose excess prefix reaches their deficit prefix (a closed
+    form independent of the sweep); the draw rule over a fine grid of uniforms
+    reproduces the units; uniform and basis states; chi-square of draws."""
+    rows, draws = load_alias_golden()
+    psi = np.sqrt(np.array([0.1, 0.2, 0.3, 0.4])).astype(np.complex128)
+    Q, own, alias = o.alias_build(psi)
+    assert Q.tolist() == rows["Q"], f"golden Q {Q}"
+    assert own.tolist() == rows["own"], f"golden own {own}"
+    assert alias.tolist() == rows["alias"], f"golden alias {alias}"
+    got = o.alias_sample(own, alias, np.array([d[0] for d in draws]))
+    assert got.tolist() == [d[1] for d in draws], f"golden draws {got}"
+    rng = np.random.default_rng(41)
+    for n in (1, 2, 3, 6, 10):
+        N = 1 << n
+        v = random_state(n, rng)
+        v[rng.random(N) < 0.3] = 0.0
+        if not np.any(v):
+            v[N - 1] = 1.0
+        Q, own, alias = o.alias_build(v)
+        Q = Q.astype(np.int64)
+        p = np.abs(v) ** 2
+        assert np.all(np.abs(Q - p * N / p.sum() * ALIAS_C) <= 0.5 + 4e-15 * N * ALIAS_C), "quantised weights"
+        assert np.all(own.astype(np.int64) <= ALIAS_C) and np.all(alias < N), "table range"
+        M = alias_masses(own, alias)
+        assert int(M.sum()) == N * ALIAS_C, "units per bucket"
+        light = Q < ALIAS_C
+        assert np.array_equal(M[light], Q[light]), "light units"
+        resid = abs(N * ALIAS_C - int(Q.sum()))
+        assert int(np.abs(M - Q).sum()) == resid, f"discrepancy {np.abs(M - Q).sum()} vs residual {resid}"
+        assert resid <= N // 2 + 2, f"residual {resid}"
+        heavy_idx = np.nonzero(~light)[0]
+        if light.any():
+            d = ALIAS_C - Q[light]
+            Dex = np.concatenate(([0], np.cumsum(d)[:-1]))
+            E = np.cumsum(Q[~light] - ALIAS_C)
+            j = np.minimum(np.searchsorted(E, Dex, side="left"), len(E) - 1)
+            assert np.array_equal(alias[light].astype(np.int64), heavy_idx[j]), "closed-form alias of light items"
+        # the draw rule on a grid of G uniforms per bucket reproduces the units
+        G = 256
+        u = (np.arange(N * G) + 0.5) / (N * G)
+        cnt = np.bincount(o.alias_sample(own, alias, u).astype(np.int64), minlength=N)
+        refs = np.bincount(alias.astype(np.int64), minlength=N) + 1
+        assert np.all(np.abs(cnt - M * G / ALIAS_C) <= refs), "grid draws vs units"
+    # uniform superposition: every bucket full and its own alias
+    n = 5
+    v = np.full(1 << n, 2.0 ** (-n / 2), dtype=np.complex128)
+    Q, own, alias = o.alias_build(v)
+    assert np.all(own == ALIAS_C) and np.array_equal(alias, np.arange(1 << n)), "uniform state"
+    # basis state: every draw is the basis index
+    Q, own, alias = o.alias_build(_basis(6, 45))
+    assert np.all(o.alias_sample(own, alias, W.shot_uniforms(3, 2000)) == 45), "basis state"
+    # chi-square of draws against |psi|^2 on a random 5-qubit state
+    v = random_state(5, rng)
+    p = np.abs(v) ** 2
+    p = p / p.sum()
+    Q, own, alias = o.alias_build(v)
+    Sh = 40000
+    x = o.alias_sample(own, alias, W.shot_uniforms(6, Sh))
+    cnt = np.bincount(x.astype(np.int64), minlength=32)
+    chi2 = float(np.sum((cnt - Sh * p) ** 2 / (Sh * p)))
+    assert chi2 < 31 + 6 * math.sqrt(62), f"alias chi2 {chi2}"
+
+
 ALL_PINS = [pin_gate_identities, pin_kron_bruteforce, pin_apply_matrix_k5, pin_ghz, pin_qft,
             pin_norm_and_mirror, pin_norm_sum, pin_sampler, pin_expectation, pin_validate,
-            pin_measure, pin_pblock]
+            pin_measure, pin_pblock, pin_alias]

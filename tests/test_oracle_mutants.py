@@ -39,6 +39,13 @@ MUTANTS = {
     "reset_no_flip": ("  if (outcome) {\n    const uint64_t bit", "  if (0) {\n    const uint64_t bit"),
     "kron_operands_swapped": ("out[ib * Na + ia] = b[ib] * a[ia];", "out[ia * Nb + ib] = b[ib] * a[ia];"),
     "take_wrong_half": ("| ((uint64_t)v << q);", "| ((uint64_t)(1 - v) << q);"),
+    "alias_lights_to_last_heavy": ("alias[i] = (uint32_t)heavy[j];", "alias[i] = (uint32_t)heavy[nh - 1];"),
+    "alias_drops_carried_deficit": ("r = Q[heavy[j + 1]] - (C - r);", "r = Q[heavy[j + 1]];"),
+    "alias_light_threshold": ("if (Q[i] < C) light[nl++] = i;", "if (Q[i] <= C) light[nl++] = i;"),
+    "alias_unscaled": ("nearbyint(p * scale * 2147483648.0)", "nearbyint(p * 2147483648.0)"),
+    "alias_coin_flipped": ("(f * 2147483648.0 < (double)own[i]) ? i : alias[i]",
+                           "(f * 2147483648.0 < (double)own[i]) ? alias[i] : i"),
+    "alias_converted_keeps_full": ("own[heavy[j]] = (uint32_t)r;", "own[heavy[j]] = (uint32_t)C;"),
 }
 
 
@@ -61,6 +68,7 @@ def test_mutant_is_caught(tmp_path, name):
     for pin in P.ALL_PINS:
         try:
             pin(o)
-        except AssertionError as e:
+        except (AssertionError, ValueError) as e:
+            # a ValueError is the oracle rejecting a valid input: also a catch
             caught.append(f"{pin.__name__}: {str(e)[:60]}")
     assert caught, f"mutant {name} passed every pin"
