@@ -51,8 +51,10 @@
  * shot, after Walker 1974).  One bucket per basis state, capacity C = 2^31
  * units; bucket i keeps own_i units for outcome i and gives the rest to
  * alias_i:
- *   - weights are quantised: q_i = p_i * (N / W) with W = sum_i p_i
- *     (sequential double), Q_i = q_i * 2^31 rounded to the nearest integer;
+ *   - weights are quantised: q_i = p_i * (N / W) with W = sum_i p_i taken
+ *     with Neumaier's compensated summation (so that W, and with it every
+ *     Q_i, is fixed by the amplitudes to within a few ulps whatever their
+ *     number or order), Q_i = q_i * 2^31 rounded to the nearest integer;
  *     everything after that is exact integer arithmetic;
  *   - items with Q_i < C are light, the others heavy, each list in index
  *     order; the light items are walked in order, each taking its deficit
@@ -361,11 +363,16 @@ void orc_take_qubit(const cplx *psi, int n, int q, int v, cplx *out) {
  */
 int orc_alias_build(const cplx *psi, uint64_t N, uint64_t *Q, uint32_t *own, uint32_t *alias) {
   const uint64_t C = (uint64_t)1 << 31;
-  double W = 0.0;
+  double W = 0.0, comp = 0.0; /* Neumaier: comp collects the rounding error of each addition */
   for (uint64_t i = 0; i < N; i++) {
     double re = creal(psi[i]), im = cimag(psi[i]);
-    W += re * re + im * im;
+    double p = re * re + im * im;
+    double t = W + p;
+    if (fabs(W) >= fabs(p)) comp += (W - t) + p;
+    else comp += (p - t) + W;
+    W = t;
   }
+  W += comp;
   if (!(W > 0.0)) return -1;
   const double scale = (double)N / W;
   uint64_t *light = (uint64_t *)malloc(N * sizeof(uint64_t));

@@ -20,6 +20,7 @@ Sources of truth used here:
 from __future__ import annotations
 
 import math
+from fractions import Fraction
 import os
 
 import numpy as np
@@ -493,7 +494,7 @@ def pin_alias(o):
         Q, own, alias = o.alias_build(v)
         Q = Q.astype(np.int64)
         p = np.abs(v) ** 2
-        assert np.all(np.abs(Q - p * N / p.sum() * ALIAS_C) <= 0.5 + 4e-15 * N * ALIAS_C), "quantised weights"
+        assert np.all(np.abs(Q - p * N / math.fsum(p) * ALIAS_C) <= 0.5 + 4e-15 * N * ALIAS_C), "quantised weights"
         assert np.all(own.astype(np.int64) <= ALIAS_C) and np.all(alias < N), "table range"
         M = alias_masses(own, alias)
         assert int(M.sum()) == N * ALIAS_C, "units per bucket"
@@ -520,6 +521,16 @@ def pin_alias(o):
     v = np.full(1 << n, 2.0 ** (-n / 2), dtype=np.complex128)
     Q, own, alias = o.alias_build(v)
     assert np.all(own == ALIAS_C) and np.array_equal(alias, np.arange(1 << n)), "uniform state"
+    # a total of many equal small weights and a few large ones (where a plain
+    # running sum drifts): the heavy weights still round from the exact total
+    v = np.full(1 << 16, 0.01, dtype=np.complex128)
+    big = [5, 900, 30000]
+    v[big] = 10.0
+    Q, own, alias = o.alias_build(v)
+    p = np.abs(v) ** 2
+    total = math.fsum(p)  # correctly rounded
+    exact = [float(Fraction(float(p[i])) * (1 << 16) * ALIAS_C / Fraction(total)) for i in big]
+    assert all(abs(int(Q[i]) - e) <= 0.51 for i, e in zip(big, exact)), "heavy weights"
     # basis state: every draw is the basis index
     Q, own, alias = o.alias_build(_basis(6, 45))
     assert np.all(o.alias_sample(own, alias, W.shot_uniforms(3, 2000)) == 45), "basis state"

@@ -46,6 +46,7 @@ MUTANTS = {
     "alias_coin_flipped": ("(f * 2147483648.0 < (double)own[i]) ? i : alias[i]",
                            "(f * 2147483648.0 < (double)own[i]) ? alias[i] : i"),
     "alias_converted_keeps_full": ("own[heavy[j]] = (uint32_t)r;", "own[heavy[j]] = (uint32_t)C;"),
+    "alias_plain_running_sum": ("  W += comp;", "  (void)comp;"),
 }
 
 
