@@ -545,6 +545,71 @@ def run_pblock_mode(args):
     }
 
 
+def run_alias_mode(args):
+    """Alias sampling (§III-C) against the CDF sampler on the 28-qubit bench
+    state (random layered depth 40): per step, one alias-table build and S
+    draws, and one CDF build and S draws, for S in 1e4, 1e6, 1e8 (device output
+    buffers).  Kernel times from CUDA events on the state's stream; the
+    crossover is the shot count above which build + draws is cheaper with the
+    alias table."""
+    import torch
+    from paper_2512_04216_gb300 import StateVector, capi
+    n = N_QUBITS
+    N = 1 << n
+    s = StateVector(n)
+    s.apply(W.random_layered(n, DEPTH, 2))
+    shots_list = [10_000, 1_000_000, 100_000_000]
+    out = torch.empty(max(shots_list), dtype=torch.int64, device=s.device)
+    peak, peak_kind = peaks()
+
+    def one(prof_on, k):
+        s.profile(prof_on)
+        for S in shots_list:
+            s.alias_build()
+            capi.sv_alias_sample(s.h, S, 1000 + k, out, True)
+            capi.sv_sample(s.h, S, 2000 + k, out, True)
+        torch.cuda.synchronize()
+        s.profile(False)
+
+    for k in range(args.warmup):
+        one(False, k)
+    s.profile_read()
+    launches0 = capi.sv_launch_count()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        one(True, k)
+    dt = time.perf_counter() - t0
+    st = s.profile_read()
+    steps = args.steps
+    per = {k: v["ms"] / v["launches"] for k, v in st.items() if v["launches"]}
+    build_ms = per["alias_build"] + per["reduce"]
+    cdf_ms = per["cdf"]
+    # draws: three shot counts per step, separate launches; per-shot cost from the 1e8 launches
+    S_tot = sum(shots_list)
+    alias_ns = st["alias_sample"]["ms"] / steps / S_tot * 1e6
+    cdf_ns = st["sample"]["ms"] / steps / S_tot * 1e6
+    cross = (build_ms - cdf_ms) / ((cdf_ns - alias_ns) * 1e-6) if cdf_ns > alias_ns else None
+    build_bytes = st["alias_build"]["bytes"] / st["alias_build"]["launches"]
+    build_gbs = build_bytes / (per["alias_build"] * 1e-3) / 1e9
+    s.close()
+    return {
+        "metric": "alias vs CDF sampler, 28-qubit state", "value": alias_ns, "unit": "ns per shot (alias draws)",
+        "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / steps,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c64/f64/u64",
+        "data": "synthetic",
+        "config": {"workload": f"random layered n={n} depth={DEPTH}; per step an alias build and a CDF build, "
+                               f"each with 1e4, 1e6 and 1e8 draws (device output)"},
+        "alias": {"build_ms": round(build_ms, 3), "table_ms": round(per["alias_build"], 3),
+                  "norm_ms": round(per["reduce"], 3), "ns_per_shot": round(alias_ns, 4)},
+        "cdf": {"build_ms": round(cdf_ms, 3), "ns_per_shot": round(cdf_ns, 4)},
+        "crossover_shots": round(cross) if cross else None,
+        "roofline": {"bound": "hbm", "kernel": "alias table build (6 kernels)", "achieved": round(build_gbs, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(build_gbs / peak, 4), "peak_source": peak_kind,
+                     "algorithmic_bytes_per_launch": build_bytes, "traffic": None},
+        "gpu_launches": int(capi.sv_launch_count() - launches0),
+    }
+
+
 def run_serve_mode(args):
     """Config: Poisson stream of random layered circuits, n geometric-skewed on
     8..30 (mean ~16), depth ~ U{10..100}, 1000 shots or a Z-string mask; served
@@ -616,12 +681,13 @@ def main():
     ap.add_argument("--kernel-variant", type=int, default=0)
     ap.add_argument("--precision", type=int, default=OPTS["precision"],
                     help="0: FP32 CUDA cores; 1: 3xTF32 tensor-core stage products")
-    ap.add_argument("--workload", choices=["statevector", "large", "batch", "serve", "dynamic", "pblock"],
+    ap.add_argument("--workload", choices=["statevector", "large", "batch", "serve", "dynamic", "pblock", "alias"],
                     default="statevector",
                     help="statevector: the bench line; large: the 34-qubit (128 GiB) single state, "
                          "depth 30, 1e6 shots; batch / serve: the batched and serving patterns; "
                          "dynamic: per-shot trajectories with mid-circuit measurement; "
-                         "pblock: merged registers with communication qubits")
+                         "pblock: merged registers with communication qubits; "
+                         "alias: alias-table sampling against the CDF sampler")
     ap.add_argument("--batch-circuits", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate-factors", default="0.5,1,2,4")
@@ -640,10 +706,10 @@ def main():
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
         return
-    if args.workload in ("batch", "serve", "dynamic", "pblock"):
+    if args.workload in ("batch", "serve", "dynamic", "pblock", "alias"):
         if rank == 0:
             fn = {"batch": run_batch_mode, "serve": run_serve_mode, "dynamic": run_dynamic_mode,
-                  "pblock": run_pblock_mode}[args.workload]
+                  "pblock": run_pblock_mode, "alias": run_alias_mode}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
 

@@ -195,6 +195,39 @@ int sv_sample_uniforms(sv_state *s, const double *uniforms, uint64_t shots,
                        uint64_t *out_bitstrings, uint64_t *out_n_boundary, int on_device);
 
 /*
+ * Alias sampling (§III-C: shots drawn by alias sampling at O(1) work per shot;
+ * Walker 1974).  sv_alias_build snapshots the current state's outcome
+ * distribution into a Walker alias table held by the state (8 bytes per basis
+ * state; later changes to the state do not touch it until the next build).
+ * Every bucket holds C = 2^31 units; outcome i weighs
+ * Q_i = round(|a_i|^2 * N / W * 2^31) units (W = sum |a|^2); light outcomes
+ * (Q < C) are taken in index order, each filling its bucket from the current
+ * heavy outcome (Q >= C, index order); a heavy outcome left with fewer than C
+ * units keeps them and is filled by the next heavy one; the last heavy outcome
+ * keeps a full bucket.  The build synchronises the state's stream and returns
+ * SV_ERR_ARG when the state's total weight is zero or not finite,
+ * SV_ERR_UNSUPPORTED past 32 qubits, SV_ERR_OOM without room for the table
+ * (8 B per amplitude) and the build's scratch (16 B per amplitude, freed
+ * before return).
+ *
+ * sv_alias_sample / sv_alias_sample_uniforms draw from the last table built
+ * (SV_ERR_ARG if none): with uniform u in [0,1), x = u * N, i = floor(x),
+ * f = x - i, the draw is i when f * 2^31 < own_i, else alias_i.  Uniforms come
+ * from `seed` by the SplitMix64 rule of sv_sample, or from the caller.
+ * out_bitstrings[s] receives draw s; device pointers if on_device, else host
+ * memory.
+ *
+ * sv_alias_table copies entries [offset, offset+count) of the table; entry i
+ * packs (own_i << 32) | alias_i.  sv_alias_release frees the table.
+ */
+int sv_alias_build(sv_state *s);
+int sv_alias_sample(sv_state *s, uint64_t shots, uint64_t seed, uint64_t *out_bitstrings, int on_device);
+int sv_alias_sample_uniforms(sv_state *s, const double *uniforms, uint64_t shots,
+                             uint64_t *out_bitstrings, int on_device);
+int sv_alias_table(sv_state *s, uint64_t *out, uint64_t offset, uint64_t count, int on_device);
+int sv_alias_release(sv_state *s);
+
+/*
  * Expectation of the Pauli string X^x_mask Z^z_mask (cached-state expectation
  * values, §III-B): <Z_mask> = sum_i |a_i|^2 (-1)^popcount(i & z_mask) / ||psi||^2.
  * x_mask != 0 returns SV_ERR_UNSUPPORTED.

@@ -91,6 +91,11 @@ _SIGS = {
     "sv_sample": ([_P, _u64, _u64, _P, _i], _i),
     "sv_sample_uniforms": ([_P, _P, _u64, _P, _P, _i], _i),
     "sv_expect_pauli": ([_P, _u64, _u64, _P], _i),
+    "sv_alias_build": ([_P], _i),
+    "sv_alias_sample": ([_P, _u64, _u64, _P, _i], _i),
+    "sv_alias_sample_uniforms": ([_P, _P, _u64, _P, _i], _i),
+    "sv_alias_table": ([_P, _P, _u64, _u64, _i], _i),
+    "sv_alias_release": ([_P], _i),
     "sv_profile_enable": ([_P, _i], _i),
     "sv_profile_read": ([_P, _P, _i, _P], _i),
     "sv_last_error": ([], ctypes.c_char_p),
@@ -279,6 +284,26 @@ def sv_sample_uniforms(h, uniforms, shots: int, out, on_device: bool) -> int:
     _check(_L.sv_sample_uniforms(h, _ptr(uniforms), int(shots), _ptr(out), ctypes.byref(nb),
                                  int(bool(on_device))))
     return int(nb.value)
+
+
+def sv_alias_build(h):
+    _check(_L.sv_alias_build(h))
+
+
+def sv_alias_sample(h, shots: int, seed: int, out, on_device: bool):
+    _check(_L.sv_alias_sample(h, int(shots), int(seed) & (2**64 - 1), _ptr(out), int(bool(on_device))))
+
+
+def sv_alias_sample_uniforms(h, uniforms, shots: int, out, on_device: bool):
+    _check(_L.sv_alias_sample_uniforms(h, _ptr(uniforms), int(shots), _ptr(out), int(bool(on_device))))
+
+
+def sv_alias_table(h, out, offset: int, count: int, on_device: bool):
+    _check(_L.sv_alias_table(h, _ptr(out), int(offset), int(count), int(bool(on_device))))
+
+
+def sv_alias_release(h):
+    _check(_L.sv_alias_release(h))
 
 
 def sv_expect_pauli(h, x_mask: int, z_mask: int) -> float:

@@ -62,14 +62,6 @@ __host__ __device__ inline BatchLayout batch_layout(int kmax) {
   return L;
 }
 
-__device__ __forceinline__ double batch_uniform(uint64_t seed, uint64_t s) {
-  uint64_t z = seed + (s + 1) * 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  z ^= z >> 31;
-  return double(z >> 11) * (1.0 / 9007199254740992.0);
-}
-
 __device__ __forceinline__ double p_of(float2 a) {
   const double re = a.x, im = a.y;
   return fma(re, re, im * im);
@@ -111,7 +103,7 @@ __device__ void batch_measure(const float2 *amps, uint32_t n, uint64_t seed, uin
   __syncthreads();
   const double total = chunk[nch - 1];
   for (uint32_t s = threadIdx.x; s < shots; s += blockDim.x) {
-    const double t = batch_uniform(seed, s) * total;
+    const double t = splitmix_uniform(seed, s) * total;
     uint32_t lo = 0, hi = nch;
     while (lo < hi) {
       const uint32_t mid = (lo + hi) >> 1;

@@ -81,6 +81,9 @@ struct sv_state {
   void *stage = nullptr;         // device staging for host in/out buffers
   size_t stage_cap = 0;
   std::vector<PlanSlab> slabs;  // streamed plan chunks
+  uint64_t *alias_table = nullptr;  // Walker alias table of the last sv_alias_build
+  uint64_t *alias_tot = nullptr;    // build totals and error word (AliasScratch::tot)
+  int alias_n = 0;
   // profiling
   bool prof = false;
   std::vector<ProfRec> recs;
@@ -268,6 +271,8 @@ void free_state(sv_state *s) {
   if (s->derr) cudaFree(s->derr);
   if (s->hscal) cudaFreeHost(s->hscal);
   if (s->stage) cudaFree(s->stage);
+  if (s->alias_table) cudaFree(s->alias_table);
+  if (s->alias_tot) cudaFree(s->alias_tot);
   for (auto &r : s->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -723,6 +728,134 @@ int sv_sample(sv_state *s, uint64_t shots, uint64_t seed, uint64_t *out_bitstrin
 int sv_sample_uniforms(sv_state *s, const double *uniforms, uint64_t shots, uint64_t *out_bitstrings,
                        uint64_t *out_n_boundary, int on_device) {
   return sample_impl(s, uniforms, 0, 0, shots, out_bitstrings, out_n_boundary, on_device);
+}
+
+int sv_alias_release(sv_state *s) {
+  if (!s) return fail(SV_ERR_ARG, "null state");
+  DeviceGuard g(s->device);
+  if (s->alias_table) {
+    CK(s, cudaStreamSynchronize(s->stream));
+    cudaFree(s->alias_table);
+    s->alias_table = nullptr;
+  }
+  s->alias_n = 0;
+  return SV_OK;
+}
+
+int sv_alias_build(sv_state *s) {
+  CHECK_STATE(s);
+  if (s->n > 32) return fail(SV_ERR_UNSUPPORTED, "alias tables hold 32-bit outcomes: n <= 32, got %d", s->n);
+  DeviceGuard g(s->device);
+  int rc = ensure_reduce(s);
+  if (rc) return rc;
+  const uint64_t N = uint64_t(1) << s->n;
+  CK(s, timed(s, "reduce", double(N * 8), [&] {
+       return launch_reduce_pz(s->amp, s->n, 0, s->ms.part, s->ms.n_part, s->dscal, s->stream);
+     }));
+  CK(s, cudaMemcpyAsync(s->hscal, s->dscal, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  rc = check_device_error(s);
+  if (rc) return rc;
+  const double W = s->hscal[0];
+  if (!(W > 0.0) || !std::isfinite(W)) return fail(SV_ERR_ARG, "state weight %g: nothing to sample", W);
+  const double scale = double(N) / W;
+  const float s_hi = float(scale), s_lo = float(scale - double(s_hi));
+  if (s->alias_table && s->alias_n != s->n) {
+    cudaFree(s->alias_table);
+    s->alias_table = nullptr;
+  }
+  if (!s->alias_table) CK(s, cudaMalloc(&s->alias_table, N * sizeof(uint64_t)));
+  s->alias_n = 0;
+  if (!s->alias_tot) CK(s, cudaMalloc(&s->alias_tot, 4 * sizeof(uint64_t)));
+  AliasScratch sc;
+  sc.tot = s->alias_tot;
+  const size_t nblk = alias_blocks(s->n), nseg = alias_segments(s->n), nsplit = alias_splits(s->n);
+  void *mem = nullptr;
+  const size_t off_seg = 3 * nblk * sizeof(uint64_t);
+  const size_t off_split = off_seg + 3 * nseg * sizeof(uint64_t);
+  const size_t off_keys = (off_split + nsplit * sizeof(uint64_t) + 255) & ~size_t(255);
+  const size_t off_qv = off_keys + N * sizeof(uint64_t);
+  const size_t off_idx = off_qv + N * sizeof(uint32_t);
+  const size_t bytes = off_idx + N * sizeof(uint32_t);
+  CK(s, cudaMallocAsync(&mem, bytes, s->stream));
+  uint8_t *base = static_cast<uint8_t *>(mem);
+  sc.blk = reinterpret_cast<uint64_t *>(base);
+  sc.seg = reinterpret_cast<uint64_t *>(base + off_seg);
+  sc.splits = reinterpret_cast<uint64_t *>(base + off_split);
+  sc.keys = reinterpret_cast<uint64_t *>(base + off_keys);
+  sc.qv = reinterpret_cast<uint32_t *>(base + off_qv);
+  sc.idx = reinterpret_cast<uint32_t *>(base + off_idx);
+  cudaError_t e = timed(s, "alias_build", double(N) * 60.0,
+                        [&] { return launch_alias_build(s->amp, s->n, s_hi, s_lo, sc, s->alias_table, s->stream); });
+  cudaError_t e2 = cudaFreeAsync(mem, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "alias table build");
+  if (e2 != cudaSuccess) return cuda_fail(s, e2, "alias scratch release");
+  uint64_t tot[4];
+  CK(s, cudaMemcpyAsync(s->hscal, s->alias_tot, 4 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  std::memcpy(tot, s->hscal, sizeof(tot));
+  if (tot[3] || tot[0] >= N) return fail(SV_ERR_ARG, "no outcome reaches a full bucket: state weight too small");
+  if (s->prof && !s->recs.empty() && std::strcmp(s->recs.back().name, "alias_build") == 0)
+    // two state reads, list records written and read (12 B, +4 B of weight for light
+    // outcomes), one table entry
+    s->recs.back().bytes = double(N) * (16 + 24 + 8) + double(tot[0]) * 8;
+  s->alias_n = s->n;
+  return SV_OK;
+}
+
+static int alias_sample_impl(sv_state *s, const double *u, uint64_t seed, int use_seed, uint64_t shots,
+                             uint64_t *out, int on_device) {
+  CHECK_STATE(s);
+  if (!s->alias_table || s->alias_n != s->n) return fail(SV_ERR_ARG, "no alias table: call sv_alias_build first");
+  if (shots == 0) return SV_OK;
+  if (!out) return fail(SV_ERR_ARG, "out is null");
+  if (!use_seed && !u) return fail(SV_ERR_ARG, "uniforms is null");
+  DeviceGuard g(s->device);
+  const double *u_dev = u;
+  uint64_t *out_dev = out;
+  if (!on_device) {
+    const size_t need = shots * (sizeof(uint64_t) + (use_seed ? 0 : sizeof(double)));
+    int rc = ensure_dev(s, &s->stage, &s->stage_cap, need, "staging buffer");
+    if (rc) return rc;
+    out_dev = static_cast<uint64_t *>(s->stage);
+    if (!use_seed) {
+      double *ud = reinterpret_cast<double *>(out_dev + shots);
+      CK(s, cudaMemcpyAsync(ud, u, shots * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+      u_dev = ud;
+    }
+  }
+  CK(s, timed(s, "alias_sample", double(shots) * 16.0, [&] {
+       return launch_alias_sample(s->alias_table, s->n, u_dev, seed, use_seed, shots, out_dev, s->stream);
+     }));
+  if (!on_device) {
+    CK(s, cudaMemcpyAsync(out, out_dev, shots * sizeof(uint64_t), cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    return check_device_error(s);
+  }
+  return SV_OK;
+}
+
+int sv_alias_sample(sv_state *s, uint64_t shots, uint64_t seed, uint64_t *out_bitstrings, int on_device) {
+  return alias_sample_impl(s, nullptr, seed, 1, shots, out_bitstrings, on_device);
+}
+
+int sv_alias_sample_uniforms(sv_state *s, const double *uniforms, uint64_t shots, uint64_t *out_bitstrings,
+                             int on_device) {
+  return alias_sample_impl(s, uniforms, 0, 0, shots, out_bitstrings, on_device);
+}
+
+int sv_alias_table(sv_state *s, uint64_t *out, uint64_t offset, uint64_t count, int on_device) {
+  CHECK_STATE(s);
+  if (!s->alias_table || s->alias_n != s->n) return fail(SV_ERR_ARG, "no alias table: call sv_alias_build first");
+  const uint64_t N = uint64_t(1) << s->n;
+  if (offset > N || count > N - offset) return fail(SV_ERR_ARG, "range beyond the table");
+  if (count == 0) return SV_OK;
+  if (!out) return fail(SV_ERR_ARG, "out is null");
+  DeviceGuard g(s->device);
+  CK(s, cudaMemcpyAsync(out, s->alias_table + offset, count * sizeof(uint64_t),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
+  if (!on_device) CK(s, cudaStreamSynchronize(s->stream));
+  return SV_OK;
 }
 
 int sv_tc_selftest(const float *a, const double *b, float *d) {

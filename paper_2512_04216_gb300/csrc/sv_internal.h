@@ -188,6 +188,40 @@ cudaError_t launch_collapse(float2 *amp, int n, int q, int outcome, int to_zero,
 
 size_t reduce_parts(int n);
 
+// Walker alias table (sv_alias.cu).  Entry i of the table packs
+// (own_i << 32) | alias_i: bucket i keeps own_i of its 2^31 units for outcome
+// i and gives the rest to outcome alias_i.
+constexpr uint64_t kAliasUnits = uint64_t(1) << 31;
+struct AliasScratch {
+  uint64_t *blk = nullptr;   // 3 per 4096-item block: light count, deficit sum, excess sum
+  uint64_t *seg = nullptr;   // 3 per scan segment
+  uint64_t *tot = nullptr;   // [0] light items, [1] total deficit, [2] total excess, [3] error
+  uint64_t *keys = nullptr;  // N: deficit prefixes of light items, then excess prefixes of heavy ones
+  uint32_t *qv = nullptr;    // N: Q of light items, by light rank
+  uint32_t *idx = nullptr;   // N: item index of light items, then of heavy items
+  uint64_t *splits = nullptr;  // merge-path split per merge CTA boundary (alias_splits(n))
+};
+size_t alias_blocks(int n);
+size_t alias_segments(int n);
+size_t alias_splits(int n);
+// Queues the table build for weights |a_i|^2 * (s_hi + s_lo) (s = N / sum |a|^2).
+cudaError_t launch_alias_build(const float2 *amp, int n, float s_hi, float s_lo, const AliasScratch &sc,
+                               uint64_t *table, cudaStream_t st);
+// Draws with uniforms u (or counter-based SplitMix64 from seed when use_seed).
+cudaError_t launch_alias_sample(const uint64_t *table, int n, const double *u, uint64_t seed, int use_seed,
+                                uint64_t shots, uint64_t *out, cudaStream_t st);
+
+#ifdef __CUDACC__
+// Counter-based SplitMix64 uniform for draw s of `seed`: 53 bits in [0, 1).
+__device__ __forceinline__ double splitmix_uniform(uint64_t seed, uint64_t s) {
+  uint64_t z = seed + (s + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return double(z >> 11) * (1.0 / 9007199254740992.0);
+}
+#endif
+
 // Records the calling thread's sv_last_error() message (sv_capi.cu); returns code.
 int set_last_error(int code, const char *fmt, ...);
 

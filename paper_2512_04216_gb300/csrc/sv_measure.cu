@@ -336,14 +336,6 @@ cudaError_t launch_build_cdf(const float2 *amp, int n, MeasureScratch &ms, doubl
 }
 
 // ---- sampling -----------------------------------------------------------------
-__device__ __forceinline__ double splitmix_uniform(uint64_t seed, uint64_t s) {
-  uint64_t z = seed + (s + 1) * 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  z ^= z >> 31;
-  return double(z >> 11) * (1.0 / 9007199254740992.0);
-}
-
 __device__ __forceinline__ double amp_p(float2 a) {
   const double re = a.x, im = a.y;
   return fma(re, re, im * im);

@@ -81,6 +81,39 @@ class StateVector:
         nb = capi.sv_sample_uniforms(self.h, u, u.shape[0], out, on_device)
         return out, nb
 
+    def alias_build(self):
+        """Snapshot the outcome distribution into a Walker alias table (synchronises)."""
+        capi.sv_alias_build(self.h)
+
+    def sample_alias(self, shots: int, seed: int, on_device: bool = False):
+        """Draws from the last alias table, uniforms from seed (SplitMix64, as sample())."""
+        if on_device:
+            out = torch.empty(shots, dtype=torch.int64, device=self.device)
+        else:
+            out = np.empty(shots, dtype=np.uint64)
+        capi.sv_alias_sample(self.h, shots, seed, out, on_device)
+        return out
+
+    def sample_alias_uniforms(self, uniforms, on_device: bool = False):
+        if on_device:
+            u = uniforms if torch.is_tensor(uniforms) else torch.as_tensor(uniforms, device=self.device)
+            out = torch.empty(u.shape[0], dtype=torch.int64, device=self.device)
+        else:
+            u = np.ascontiguousarray(uniforms, dtype=np.float64)
+            out = np.empty(u.shape[0], dtype=np.uint64)
+        capi.sv_alias_sample_uniforms(self.h, u, u.shape[0], out, on_device)
+        return out
+
+    def alias_table(self, offset: int = 0, count: int | None = None):
+        """(own uint32[count], alias uint32[count]) of the last alias table."""
+        count = (1 << self.n) - offset if count is None else count
+        raw = np.empty(count, dtype=np.uint64)
+        capi.sv_alias_table(self.h, raw, offset, count, False)
+        return (raw >> np.uint64(32)).astype(np.uint32), (raw & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+
+    def alias_release(self):
+        capi.sv_alias_release(self.h)
+
     def probabilities(self, offset: int = 0, count: int | None = None, on_device: bool = False):
         count = (1 << self.n) - offset if count is None else count
         if on_device:
