@@ -643,14 +643,19 @@ def run_serve_mode(args):
         c = W.random_layered(n, d, 900 + sd)
         s = StateVector(n)
         ir, keep = capi.to_ir(c)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(s.stream)
-        capi.sv_apply_circuit(s.h, ir, len(c))
-        e1.record(s.stream)
-        torch.cuda.synchronize()
+        capi.sv_apply_circuit(s.h, ir, len(c))  # warm, as in the calibration
+        best = math.inf
+        for _ in range(2):
+            s.reset(0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s.stream)
+            capi.sv_apply_circuit(s.h, ir, len(c))
+            e1.record(s.stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
         s.close()
-        errs.append(abs(model.predict_ms(n, c) - e0.elapsed_time(e1)) / e0.elapsed_time(e1))
+        errs.append(abs(model.predict_ms(n, c) - best) / best)
     f = float(args.rate_factors.split(",")[-1])
     specs = W.serving_requests(count, 4, f * plain_cap)
     reqs = serve.make_requests(specs, W.random_layered)

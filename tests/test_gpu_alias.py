@@ -212,3 +212,40 @@ def test_alias_errors(P):
     with pytest.raises(P.capi.SvError):
         s.sample_alias(10, 1)
     s.close()
+
+
+def test_alias_maximum_size_ghz32(P):
+    """n = 32, the largest table (32-bit outcomes): GHZ has two heavy outcomes,
+    0 and N-1, of N/2 buckets each, and N-2 empty light ones.  Light outcomes
+    1..N/2 fill from outcome 0, which is then used up exactly (its excess is
+    N/2 - 1 buckets) and keeps (almost) nothing, aliasing N-1; lights N/2+1..N-2
+    fill from N-1, the last heavy outcome, which keeps a full bucket.  The
+    weights come from float32 pairs, so the switch may move by one bucket and
+    outcome 0 keeps either a sliver of units or all but a sliver."""
+    n = 32
+    N = 1 << n
+    s = P.StateVector(n)
+    s.apply(W.ghz(n))
+    s.alias_build()
+    own, alias = s.alias_table(0, 1000)
+    # Q_0 = N/2 buckets +- a float32-pair rounding: 0 is used up by light N/2 (keeping the
+    # excess over N/2 buckets) or one light earlier (keeping almost a full bucket)
+    assert (own[0] < 1 << 17 or own[0] > ALIAS_C - (1 << 17)) and alias[0] == N - 1, (own[0], alias[0])
+    assert np.all(own[1:] == 0) and np.all(alias[1:] == 0)
+    own, alias = s.alias_table(N - 1000, 1000)
+    assert np.all(own[:-1] == 0) and np.all(alias[:-1] == N - 1)
+    assert own[-1] == ALIAS_C and alias[-1] == N - 1
+    own, alias = s.alias_table((N >> 1) - 4, 9)
+    assert np.all(own == 0)
+    switch = int(np.argmax(alias == N - 1))
+    assert np.all(alias[:switch] == 0) and np.all(alias[switch:] == N - 1) and 3 <= switch <= 6, alias
+    x = s.sample_alias(1_000_000, 5).astype(np.int64)
+    assert set(np.unique(x).tolist()) <= {0, N - 1}
+    frac = float(np.mean(x == 0))
+    assert abs(frac - 0.5) < 5 * 0.0005, frac
+    s.close()
+    big = P.StateVector(33)
+    with pytest.raises(P.capi.SvError) as e:
+        big.alias_build()
+    assert e.value.code == P.capi.SV_ERR_UNSUPPORTED
+    big.close()
