@@ -4,11 +4,14 @@ hardware-calibrated coefficient times the operation's complexity term).
 For this state-vector backend the operations are the plan's HBM passes and
 its dense-block arithmetic, and the end-of-circuit sampling:
 
-    T_apply(n, circuit) ~ c_fix + C_pass(n) * passes + c_flop * flops_eff
+    T_apply(n, circuit) ~ c_fix + c_gate * dense_gates + C_pass(n) * passes + c_flop * flops_eff
     T_shots(n, S)       ~ c1(n) + c2 * S
 
-`passes`, dense-block flops and phase ops (flops_eff counts a phase op as 48
-flops per amplitude) come from the host planner (sv_plan_stats, no GPU work).
+`dense_gates` counts the non-diagonal gates, each of which the host planner
+multiplies into a fused block (this host work dominates small states;
+diagonal gates only add phase terms).  `passes`, dense-block flops and phase
+ops (flops_eff counts a phase op as 48 flops per amplitude) come from the host
+planner (sv_plan_stats, no GPU work).
 The coefficients are measured once on the device by `calibrate` (synthetic
 circuits of different densities over a grid of qubit counts, one joint least
 squares fit) and C_pass is interpolated in n with a monotone piecewise cubic
@@ -97,7 +100,8 @@ class CostModel:
     ns: list = field(default_factory=list)        # calibrated qubit counts
     c_pass: list = field(default_factory=list)    # ms per HBM pass at each n
     c_flop: float = 0.0                           # ms per effective dense-block flop
-    c_fix: float = 0.0                            # ms per apply call (planning, upload)
+    c_fix: float = 0.0                            # ms per apply call (upload, launches)
+    c_gate: float = 0.0                           # ms of host fusion per non-diagonal gate
     c_shot1: list = field(default_factory=list)   # ms of CDF build + fixed sampling cost at each n
     c_shot2: float = 0.0                          # ms per shot
 
@@ -112,8 +116,17 @@ class CostModel:
         v = np.maximum(np.asarray(vals, dtype=np.float64), 1e-30)
         return float(np.exp(pchip(self.ns, np.log(v))(float(n))))
 
-    def apply_ms(self, n: int, passes: int, eff_flops: float) -> float:
-        return self.c_fix + self._curve(self.c_pass, n) * passes + self.c_flop * eff_flops
+    # IR kinds of diagonal gates (z, s, sdg, t, tdg, rz, p, cz, cp)
+    DIAGONAL_KINDS = (5, 6, 7, 8, 9, 12, 13, 15, 16)
+
+    @staticmethod
+    def dense_gates(ir, n_gates: int) -> int:
+        kinds = np.asarray(ir["kind"][:n_gates])
+        return int(n_gates - np.isin(kinds, CostModel.DIAGONAL_KINDS).sum())
+
+    def apply_ms(self, n: int, passes: int, eff_flops: float, dense_gates: int = 0) -> float:
+        return (self.c_fix + self.c_gate * dense_gates + self._curve(self.c_pass, n) * passes
+                + self.c_flop * eff_flops)
 
     def shots_ms(self, n: int, shots: int) -> float:
         return self._curve(self.c_shot1, n) + self.c_shot2 * shots
@@ -121,7 +134,9 @@ class CostModel:
     def predict_ms(self, n: int, circuit, shots: int = 0, opts=None) -> float:
         from . import capi
         st = capi.sv_plan_stats(n, circuit, opts)
-        return self.apply_ms(n, st["n_passes"], self.eff_flops(n, st)) + (self.shots_ms(n, shots) if shots else 0.0)
+        ir, _keep = capi.to_ir(circuit)
+        return (self.apply_ms(n, st["n_passes"], self.eff_flops(n, st), self.dense_gates(ir, len(circuit)))
+                + (self.shots_ms(n, shots) if shots else 0.0))
 
     def to_json(self) -> str:
         return json.dumps(asdict(self))
@@ -133,8 +148,9 @@ class CostModel:
 
 def calibrate(ns=(10, 12, 14, 16, 18, 20, 22, 24, 26, 28), reps: int = 2, opts=None, seed: int = 7) -> CostModel:
     """Measures the coefficients on the current device (a one-time routine):
-    one joint least-squares fit of T = c_fix + C_pass(n) * passes + c_flop *
-    effective flops over synthetic circuits at every n in `ns`."""
+    one joint least-squares fit of T = c_fix + c_gate * dense gates + C_pass(n)
+    * passes + c_flop * effective flops over synthetic circuits at every n in
+    `ns` (each timed warm: best of reps + 1 runs on one state)."""
     import torch
 
     import workloads as W
@@ -145,7 +161,8 @@ def calibrate(ns=(10, 12, 14, 16, 18, 20, 22, 24, 26, 28), reps: int = 2, opts=N
     rows, times, shot_samples = [], [], []
     for i, n in enumerate(ns):
         circuits = [W.random_layered(n, 8, seed + n), W.random_layered(n, 2, seed + 2 * n),
-                    W.random_layered(n, 24, seed + 3 * n), W.qft(n), W.ghz(n), W.ghz(n)[:1]]
+                    W.random_layered(n, 24, seed + 3 * n), W.random_layered(n, 60, seed + 4 * n),
+                    W.qft(n), W.ghz(n), W.ghz(n)[:1]]
         s = StateVector(n)
         for c in circuits:
             st = capi.sv_plan_stats(n, c, opts)
@@ -160,10 +177,11 @@ def calibrate(ns=(10, 12, 14, 16, 18, 20, 22, 24, 26, 28), reps: int = 2, opts=N
                 e1.record(s.stream)
                 torch.cuda.synchronize()
                 best = min(best, e0.elapsed_time(e1))
-            row = [0.0] * (len(ns) + 2)
+            row = [0.0] * (len(ns) + 3)
             row[i] = float(st["n_passes"])
             row[len(ns)] = CostModel.eff_flops(n, st)
             row[len(ns) + 1] = 1.0
+            row[len(ns) + 2] = float(CostModel.dense_gates(ir, len(c)))
             rows.append(row)
             times.append(best)
         for S in (1, 1000, 100000):
@@ -182,6 +200,7 @@ def calibrate(ns=(10, 12, 14, 16, 18, 20, 22, 24, 26, 28), reps: int = 2, opts=N
     model.c_pass = [max(float(v), 1e-6) for v in sol[:len(ns)]]
     model.c_flop = max(float(sol[len(ns)]), 0.0)
     model.c_fix = max(float(sol[len(ns) + 1]), 0.0)
+    model.c_gate = max(float(sol[len(ns) + 2]), 0.0)
     _, c2 = linear_fit([S for _, S, _ in shot_samples], [t for _, _, t in shot_samples])
     model.c_shot2 = max(c2, 0.0)
     for n in ns:
