@@ -121,16 +121,39 @@ __device__ __forceinline__ void thread_sums(const float2 *tile, uint32_t cnt, ui
 
 // ---- norm / Z-expectation ------------------------------------------------
 // part[2*b] = sum p, part[2*b+1] = sum p*(-1)^popcount(i & zmask) over CTA b.
+// Totals only: a thread takes amplitude pairs j * 256 + t (coalesced 16-byte
+// loads, all eight issued before any is used) instead of a staged run.
 __global__ void __launch_bounds__(kRT) k_reduce_pz(const float2 *__restrict__ amp, int n,
                                                    uint64_t zmask, double *__restrict__ part) {
-  __shared__ __align__(16) float2 tile[kCtaAmps];
   __shared__ double red[2][kRT / 32];
   const uint64_t N = uint64_t(1) << n;
   const uint64_t start = uint64_t(blockIdx.x) * kCtaAmps;
-  const uint32_t cnt = uint32_t(umin64(kCtaAmps, N - start));
-  stage_load(tile, amp, start, cnt);
-  float ps, pc, zs, zc;
-  thread_sums(tile, cnt, start, zmask, ps, pc, zs, zc);
+  const uint32_t cnt = uint32_t(umin64(kCtaAmps, N - start));  // even: N >= 2
+  const float4 *a4 = reinterpret_cast<const float4 *>(amp + start);
+  constexpr int kPairs = kPerThread / 2;
+  float4 f[kPairs];
+#pragma unroll
+  for (int j = 0; j < kPairs; j++) {
+    const uint32_t pr = uint32_t(j) * kRT + threadIdx.x;
+    f[j] = 2 * pr < cnt ? a4[pr] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  float ps = 0.f, pc = 0.f, zs = 0.f, zc = 0.f;
+#pragma unroll
+  for (int j = 0; j < kPairs; j++) {
+    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+    acc_sq(s0, c0, f[j].x);
+    acc_sq(s0, c0, f[j].y);
+    acc_sq(s1, c1, f[j].z);
+    acc_sq(s1, c1, f[j].w);
+    acc_pair(ps, pc, s0, c0);
+    acc_pair(ps, pc, s1, c1);
+    if (zmask) {
+      const uint64_t i0 = start + 2 * (uint64_t(j) * kRT + threadIdx.x);
+      const bool n0 = __popcll(i0 & zmask) & 1, n1 = __popcll((i0 + 1) & zmask) & 1;
+      acc_pair(zs, zc, n0 ? -s0 : s0, n0 ? -c0 : c0);
+      acc_pair(zs, zc, n1 ? -s1 : s1, n1 ? -c1 : c1);
+    }
+  }
   warp_acc_pair(ps, pc);
   warp_acc_pair(zs, zc);
   const int w = threadIdx.x >> 5;
