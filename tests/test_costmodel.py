@@ -49,3 +49,24 @@ def test_model_curves_interpolate_in_log_space():
     assert abs(m.apply_ms(20, 2, 1e9) - (0.05 + 2 * 1e-3 * 2 ** 10 + 1e-3)) < 1e-9
     assert abs(m.shots_ms(20, 1000) - (0.2 + 1e-2)) < 1e-12
     assert CM.CostModel.from_json(m.to_json()) == m
+
+
+def test_dense_gate_count_skips_diagonal_gates():
+    """The host term counts the gates the planner multiplies into blocks: every
+    non-diagonal gate; z, s, sdg, t, tdg, rz, p, cz and cp only add phase terms."""
+    capi = pytest.importorskip("paper_2512_04216_gb300.capi")
+    import workloads as W
+    n = 10
+    qft = W.qft(n)
+    ir, keep = capi.to_ir(qft)
+    assert CM.CostModel.dense_gates(ir, len(qft)) == n + n // 2  # H on every qubit, the final SWAPs
+    rl = W.random_layered(n, 3, 1)
+    ir, keep = capi.to_ir(rl)
+    assert CM.CostModel.dense_gates(ir, len(rl)) == len(rl)
+    mixed = [("z", (0,), ()), ("s", (1,), ()), ("sdg", (2,), ()), ("t", (3,), ()), ("tdg", (4,), ()),
+             ("rz", (5,), (0.3,)), ("p", (6,), (0.2,)), ("cz", (0, 1), ()), ("cp", (2, 3), (0.1,)),
+             ("x", (0,), ()), ("y", (1,), ()), ("rx", (2,), (0.4,)), ("swap", (3, 4), ())]
+    ir, keep = capi.to_ir(mixed)
+    assert CM.CostModel.dense_gates(ir, len(mixed)) == 4
+    m = CM.CostModel(ns=[10, 20], c_pass=[1.0, 2.0], c_flop=0.0, c_fix=0.5, c_gate=0.01)
+    assert abs(m.apply_ms(10, 3, 0.0, 100) - (0.5 + 1.0 + 3 * 1.0)) < 1e-12
