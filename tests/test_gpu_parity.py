@@ -259,19 +259,21 @@ def test_many_states_on_streams(sv):
 
 
 def test_large_mirror_and_qft_28(sv):
-    """28 qubits (2 GiB): C.C^-1 returns |0> and the QFT of a basis state
-    matches its closed form on sampled indices."""
+    """28 qubits (2 GiB), in the plan options the benchmark times (k_max 5,
+    12 tile qubits, 5 low qubits, register kernels): C.C^-1 returns |0> and the
+    QFT of a basis state matches its closed form on sampled indices."""
     n = 28
+    opts = dict(k_max=5, tile_qubits=12, low_qubits=5, kernel_variant=0, precision=0)
     c = W.random_layered(n, 40, 2)
     s = sv.StateVector(n)
-    s.apply(c + W.inverse(c))
+    s.apply(c + W.inverse(c), **opts)
     a0 = s.amplitudes(0, 1)[0]
     norm2 = s.norm2()
     assert abs(a0) ** 2 / norm2 >= 1 - FID_TOL, (abs(a0) ** 2, norm2)
     assert abs(norm2 - 1) < 1e-5, norm2
     x = W.basis_index(n, 2)
     s.reset(x)
-    s.apply(W.qft(n))
+    s.apply(W.qft(n), **opts)
     rng = np.random.default_rng(0)
     idx = np.unique(rng.integers(0, 1 << n, 1 << 14))
     amps = s.amplitudes()
