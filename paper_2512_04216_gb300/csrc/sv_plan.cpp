@@ -327,21 +327,6 @@ static void fuse_pass(const std::vector<GateM> &gates, const std::vector<uint32_
     op.blk = std::move(b);
     ops.push_back(std::move(op));
   };
-  auto flush_phase = [&]() {
-    if (pending.empty()) {
-      pending_local = 0;
-      return;
-    }
-    merge_terms(pending);
-    if (!pending.empty()) {
-      HostOp op;
-      op.type = OP_PHASE;
-      op.terms.swap(pending);
-      ops.push_back(std::move(op));
-    }
-    pending.clear();
-    pending_local = 0;
-  };
   auto close_touching = [&](uint64_t m) {
     for (size_t i = 0; i < open.size();) {
       if (open[i].mask & m) {
@@ -351,6 +336,24 @@ static void fuse_pass(const std::vector<GateM> &gates, const std::vector<uint32_
         i++;
       }
     }
+  };
+  auto flush_phase = [&]() {
+    if (pending.empty()) {
+      pending_local = 0;
+      return;
+    }
+    // register passes leave blocks open past the diagonal gates they queue:
+    // the blocks holding the phase's qubits come first
+    if (pairs) close_touching(pending_local);
+    merge_terms(pending);
+    if (!pending.empty()) {
+      HostOp op;
+      op.type = OP_PHASE;
+      op.terms.swap(pending);
+      ops.push_back(std::move(op));
+    }
+    pending.clear();
+    pending_local = 0;
   };
 
   GateM renamed;
@@ -382,18 +385,26 @@ static void fuse_pass(const std::vector<GateM> &gates, const std::vector<uint32_
       if (!outer) {
         // a local diagonal gate: absorb it into an open block that holds its
         // qubits; with no phase op being collected, also into open blocks that
-        // can take it within k_max (a new phase op costs more than a wider block)
+        // can take it within k_max (a new phase op costs more than a wider
+        // block) -- in register passes even when that only adds its other
+        // qubit to a block (e.g. a controlled phase next to a Hadamard)
         uint64_t U = local;
         for (auto &b : open)
           if (b.mask & local) U |= b.mask;
         bool inside = false;
         for (auto &b : open)
           if ((b.mask & local) == local) inside = true;
-        if (inside || (pending.empty() && (U & ~local) && popc(U) <= kmax)) to_phase = false;
+        const bool grows = pairs ? (U != local || std::any_of(open.begin(), open.end(), [&](const Block &b) {
+                                     return (b.mask & local) != 0;
+                                   }))
+                                 : (U & ~local) != 0;
+        if (inside || (pending.empty() && grows && popc(U) <= kmax)) to_phase = false;
       }
     }
     if (to_phase) {
-      close_touching(local);
+      // register passes keep the touching blocks open (a later gate may still
+      // join them; the flush emits them before the phase op)
+      if (!pairs) close_touching(local);
       diag_terms(g, lpos, pending);
       pending_local |= local;
       continue;
@@ -431,6 +442,7 @@ static void fuse_pass(const std::vector<GateM> &gates, const std::vector<uint32_
     open.push_back(std::move(nb));
   }
   for (auto &b : open) emit_block(std::move(b));
+  open.clear();
   flush_phase();
 }
 
