@@ -1,0 +1,88 @@
+"""The host planner's fusion against gate-by-gate application (CPU only).
+
+tests/plan_semantics/plan_check.cpp compiles the planner source with the host
+compiler, fuses a whole circuit into one pass (all qubits in the tile), applies
+the resulting dense blocks and phase terms -- and the SWAP relabeling of
+register passes -- to a random complex128 state, and compares with applying the
+circuit's gates one at a time.  Covers register-pass fusion (two-qubit phase
+terms, relabeling, blocks kept open past queued diagonal gates) and the
+shared-memory pass's fusion, at fusion widths 2 and 5."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_2512_04216_gb300", "csrc")
+
+
+def _cuda_include():
+    for base in (os.environ.get("CUDA_HOME"), "/usr/local/cuda"):
+        if base and os.path.exists(os.path.join(base, "include", "cuda_runtime.h")):
+            return os.path.join(base, "include")
+    nvcc = shutil.which("nvcc")
+    if nvcc:
+        inc = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "include")
+        if os.path.exists(os.path.join(inc, "cuda_runtime.h")):
+            return inc
+    return None
+
+
+@pytest.fixture(scope="module")
+def checker(tmp_path_factory):
+    inc = _cuda_include()
+    if inc is None or shutil.which("g++") is None:
+        pytest.skip("needs g++ and the CUDA headers")
+    exe = str(tmp_path_factory.mktemp("plan") / "plan_check")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-w", f"-I{inc}", f"-I{CSRC}", "-o", exe,
+                    os.path.join(HERE, "plan_semantics", "plan_check.cpp")], check=True)
+    return exe
+
+
+def _encode(n, circuit):
+    from paper_2512_04216_gb300 import capi  # gate kind numbers only (no library call)
+    lines = [f"{n} {len(circuit)}"]
+    for name, qs, ps in circuit:
+        ps = list(ps) + [0.0] * (3 - len(ps))
+        lines.append(" ".join(map(str, [capi.GATE_KIND[name], len(qs), *qs, *ps[:3]])))
+    return "\n".join(lines) + "\n"
+
+
+def _interleaved(n, seed):
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    c = []
+    for _ in range(60):
+        a, b = (int(x) for x in rng.choice(n, 2, replace=False))
+        kind = rng.integers(0, 5)
+        if kind == 0:
+            c.append(("h", (a,), ()))
+        elif kind == 1:
+            c.append(("cp", (a, b), (float(rng.uniform(0, 6.3)),)))
+        elif kind == 2:
+            c.append(("cx", (a, b), ()))
+        elif kind == 3:
+            c.append(("rz", (a,), (float(rng.uniform(0, 6.3)),)))
+        else:
+            c.append(("u3", (a,), tuple(float(x) for x in rng.uniform(0, 6.3, 3))))
+    return c
+
+
+CASES = ([("qft", 8, W.qft(8)), ("qft", 10, W.qft(10)), ("ghz", 9, W.ghz(9)),
+          ("random_layered", 8, W.random_layered(8, 6, 1)), ("random_layered", 10, W.random_layered(10, 5, 2))]
+         + [("gate_soup", 8, W.random_gate_soup(8, 120, s)) for s in range(8)]
+         + [("interleaved", 7, _interleaved(7, s)) for s in range(6)])
+
+
+@pytest.mark.parametrize("pairs,kmax", [(1, 2), (1, 5), (0, 2), (0, 5)])
+def test_fused_pass_equals_gates(checker, pairs, kmax):
+    bad = []
+    for name, n, c in CASES:
+        r = subprocess.run([checker, str(pairs), str(kmax)], input=_encode(n, c), capture_output=True, text=True)
+        if r.returncode != 0:
+            bad.append(f"{name} n={n}: {r.stdout.strip()} {r.stderr.strip()[:200]}")
+    assert not bad, bad
