@@ -304,10 +304,12 @@ __device__ __forceinline__ void reg_rphase(float2 (&v)[1 << R], const uint8_t *_
 // Persistent register-stage kernel.  Every CTA copies its pass's records
 // (ops, matrices, phase terms, stages) into shared memory once, builds the
 // per-thread stage index tables once, then walks tiles blockIdx.x,
-// blockIdx.x + gridDim.x, ...  While a tile is computed, the next tile's
-// amplitudes stream into `buf_in` with cp.async; stage 0 reads `buf_in`
-// (natural order: its lanes are the low tile bits), later stages exchange
-// through the swizzled `buf_x`, and the last stage stores straight to HBM.
+// blockIdx.x + gridDim.x, ...  The next tile's amplitudes stream into shared
+// memory with cp.async while the current one is computed (into `buf_in` with
+// 16 amplitudes per thread; with 32, into the exchange buffer `buf_x` during the
+// last stage, which no longer needs it); stage 0 reads them in natural order
+// (its lanes are the low tile bits), later stages exchange through the
+// swizzled `buf_x`, and the last stage stores straight to HBM.
 constexpr int kMaxStages = 64;     // stage tables kept in shared memory
 constexpr int kPlanMismatch = 2;   // error word bit: a pass's device records differ from the host's
 constexpr uint32_t kMaxPassData = 160 * 1024;
@@ -342,9 +344,9 @@ __host__ __device__ inline RegLayout reg_layout(uint32_t T, uint32_t c, uint32_t
   return r;
 }
 
-// 16 amplitudes per thread (blocks up to 4 qubits): 128 registers, two CTAs
-// of 256 threads per SM; 32 amplitudes per thread (blocks up to 2 qubits):
-// three CTAs of 128 threads per SM.
+// 16 amplitudes per thread (blocks up to 4 qubits): two CTAs of 256 threads
+// per SM; 32 amplitudes per thread (blocks up to 2 qubits): four CTAs of 128
+// threads per SM (128 registers a thread).
 template <int R, int NTMAX>
 __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 4 : 2) : (NTMAX <= 256 ? 2 : 1))
     k_pass_reg(float2 *__restrict__ amp, const uint8_t *__restrict__ plan, uint32_t pass_off,
