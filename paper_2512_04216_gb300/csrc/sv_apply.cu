@@ -19,6 +19,7 @@
 //
 // Diagonal phase ops tabulate a per-tile phase table from 32-bit turn
 // fractions (exact modulo 2*pi) over the low and high halves of the tile index.
+#include <atomic>
 #include <cstdint>
 
 #include "sv_device.cuh"
@@ -494,29 +495,50 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 4 : 2) : (NTMA
 
 constexpr size_t kSmemOptIn = 232448;  // 227 KiB per CTA on sm_100-class parts
 
+// One-time per-device setup of a kernel (its shared-memory opt-in) and the
+// device's SM count.  Host threads may launch concurrently (the serving loop
+// does): the bit for a device is published with release order after its SM
+// count is stored, so a reader that sees the bit also sees the count.
+template <class F>
+static cudaError_t once_per_device(std::atomic<uint64_t> &done, std::atomic<int> *sms, int dev, F &&setup,
+                                   int *n_sms) {
+  if (dev >= 0 && dev < 64 && ((done.load(std::memory_order_acquire) >> dev) & 1ull)) {
+    *n_sms = sms[dev].load(std::memory_order_relaxed);
+    return cudaSuccess;
+  }
+  cudaError_t e = setup();
+  if (e != cudaSuccess) return e;
+  int v = 0;
+  e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64) {
+    sms[dev].store(v, std::memory_order_relaxed);
+    done.fetch_or(1ull << dev, std::memory_order_release);
+  }
+  *n_sms = v;
+  return cudaSuccess;
+}
+
 template <int R, int NTMAX>
 static cudaError_t launch_reg(float2 *amp, const uint8_t *plan, uint32_t off, const PlanPass &hp,
                               const RegPassParams &prm, int *err, cudaStream_t st) {
   const RegLayout lay = reg_layout(hp.T, hp.c, hp.n_stages, hp.data_bytes, R, true);
-  static unsigned long long configured = 0;
-  static int sms[64] = {0};
-  int dev = 0;
+  static std::atomic<uint64_t> configured{0};
+  static std::atomic<int> sms[64];
+  int dev = 0, nsm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 64 && !((configured >> dev) & 1ull)) {
-    e = cudaFuncSetAttribute(k_pass_reg<R, NTMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(kSmemOptIn));
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    configured |= 1ull << dev;
-  }
+  e = once_per_device(configured, sms, dev, [] {
+    return cudaFuncSetAttribute(k_pass_reg<R, NTMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(kSmemOptIn));
+  }, &nsm);
+  if (e != cudaSuccess) return e;
   const unsigned nt = 1u << (hp.T - R);
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass_reg<R, NTMAX>, int(nt), lay.total);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  const uint64_t want = uint64_t(sms[dev < 64 ? dev : 0] > 0 ? sms[dev < 64 ? dev : 0] : 1) * per_sm;
+  const uint64_t want = uint64_t(nsm > 0 ? nsm : 1) * per_sm;
   const unsigned grid = unsigned(hp.n_tiles < want ? hp.n_tiles : want);
   k_pass_reg<R, NTMAX><<<grid, nt, lay.total, st>>>(amp, plan, off, prm, err);
   count_launch();
@@ -723,27 +745,21 @@ static cudaError_t launch_tc(float2 *amp, const uint8_t *plan, uint32_t off, con
   const size_t floor_ = tc_smem_floor(nt >> 7);
   if (smem < floor_) smem = floor_;
   if (smem + kTcStaticSmem > kSmemOptIn) return cudaErrorInvalidValue;
-  static unsigned long long configured = 0;
-  static int sms[64] = {0};
-  int dev = 0;
+  static std::atomic<uint64_t> configured{0};
+  static std::atomic<int> sms[64];
+  int dev = 0, nsm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 64 && !((configured >> dev) & 1ull)) {
-    cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, k_pass_tc<NTMAX>);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_pass_tc<NTMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(kSmemOptIn - kTcStaticSmem));
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    configured |= 1ull << dev;
-  }
+  e = once_per_device(configured, sms, dev, [] {
+    return cudaFuncSetAttribute(k_pass_tc<NTMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(kSmemOptIn - kTcStaticSmem));
+  }, &nsm);
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass_tc<NTMAX>, int(nt), smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  const int nsm = (dev < 64 && sms[dev] > 0) ? sms[dev] : 1;
+  if (nsm < 1) nsm = 1;
   const uint64_t want = uint64_t(nsm) * per_sm;
   const unsigned grid = unsigned(hp.n_tiles < want ? hp.n_tiles : want);
   k_pass_tc<NTMAX><<<grid, nt, smem, st>>>(amp, plan, off, err);
@@ -768,16 +784,16 @@ template <int KMAX>
 static cudaError_t launch_k(float2 *amp, const uint8_t *plan, uint32_t off, const PlanPass &hp,
                             cudaStream_t st) {
   const size_t smem = pass_smem(hp.T, hp.c, KMAX);
-  static unsigned long long configured = 0;  // bit d: attribute set on device d
-  int dev = 0;
+  static std::atomic<uint64_t> configured{0};
+  static std::atomic<int> sms[64];
+  int dev = 0, nsm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 64 && !((configured >> dev) & 1ull)) {
-    e = cudaFuncSetAttribute(k_pass<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(pass_smem(kMaxTile, 1, KMAX)));
-    if (e != cudaSuccess) return e;
-    configured |= 1ull << dev;
-  }
+  e = once_per_device(configured, sms, dev, [] {
+    return cudaFuncSetAttribute(k_pass<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(pass_smem(kMaxTile, 1, KMAX)));
+  }, &nsm);
+  if (e != cudaSuccess) return e;
   const uint64_t tiles = hp.n_tiles;
   dim3 grid;
   if (tiles <= (uint64_t(1) << 30)) {
