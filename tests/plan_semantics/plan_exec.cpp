@@ -1,0 +1,232 @@
+// Host interpreter of packed register-stage plans (KIND_REG passes), for
+// tests/test_plan_semantics.py.  It plans a circuit with the library's planner
+// (build_plan), then executes every pass the way the register kernel reads its
+// records -- the load's chunk rows (RegPassParams.ko), stage 0's offsets
+// (lo), each stage's thread bits (tb) and swizzled exchange offsets (xo), the
+// dense ops on register positions (rmask, (re, re, -im, im) matrices), the
+// register phase ops (classes, D), and the store (oq, go) -- in complex
+// double, and compares the result with the circuit's gates applied one by one.
+// Exit status 0 when every amplitude agrees within 1e-5, 2 otherwise, 3 when a
+// pass is not a register pass.
+#include "sv_plan.cpp"
+
+#include <cstdio>
+#include <random>
+
+// device-side helpers the planner links against
+namespace svgb {
+bool tc_pass_fits(uint32_t, uint32_t, uint32_t, uint32_t) { return false; }
+void tc_b_image(const double *, uint8_t *) {}
+bool reg_pass_fits(uint32_t, uint32_t, uint32_t, uint32_t, uint32_t) { return true; }
+}  // namespace svgb
+
+using namespace svgb;
+using cdd = std::complex<double>;
+
+static void apply_gate(std::vector<cdd> &psi, int n, const GateM &g) {
+  const int K = 1 << g.k;
+  uint64_t gm = g.mask;
+  for (uint64_t i = 0; i < (uint64_t(1) << n); i++) {
+    if (i & gm) continue;
+    cdd v[32], w[32];
+    for (int j = 0; j < K; j++) {
+      uint64_t o = i;
+      for (int x = 0; x < g.k; x++)
+        if (j >> x & 1) o |= uint64_t(1) << g.q[x];
+      v[j] = psi[o];
+    }
+    for (int r = 0; r < K; r++) {
+      cdd a = 0;
+      for (int j = 0; j < K; j++) a += cdd(g.m[r * K + j]) * v[j];
+      w[r] = a;
+    }
+    for (int r = 0; r < K; r++) {
+      uint64_t o = i;
+      for (int x = 0; x < g.k; x++)
+        if (r >> x & 1) o |= uint64_t(1) << g.q[x];
+      psi[o] = w[r];
+    }
+  }
+}
+
+static uint32_t dep_bits(uint32_t j, uint32_t mask) {  // bit i of j -> i-th set bit of mask
+  uint32_t out = 0;
+  int i = 0;
+  for (int p = 0; p < 32; p++)
+    if (mask >> p & 1u) {
+      if (j >> i & 1u) out |= 1u << p;
+      i++;
+    }
+  return out;
+}
+
+static cdd turn_exp(uint32_t turn) {
+  const double a = 2.0 * M_PI * double(int32_t(turn)) / 4294967296.0;
+  return cdd(std::cos(a), std::sin(a));
+}
+
+static int exec_reg_pass(std::vector<cdd> &amp, const Plan &plan, size_t p) {
+  const PlanPass &hp = plan.passes[p];
+  if (hp.kind != KIND_REG) return 3;
+  const uint8_t *base_ptr = plan.bytes.data();
+  const RegPassParams &prm = plan.rparams[p];
+  const uint32_t T = hp.T, c = hp.c, R = hp.R, NR = 1u << R, NT = 1u << (T - R), ns = hp.n_stages;
+  const StageRec *stages = reinterpret_cast<const StageRec *>(base_ptr + hp.stages_off);
+  const OpRec *ops = reinterpret_cast<const OpRec *>(base_ptr + hp.ops_off);
+  const uint32_t cs = c - 1u, cmask = (1u << cs) - 1u;
+  std::vector<uint32_t> tt(size_t(ns) * NT);
+  for (uint32_t s = 0; s < ns; s++)
+    for (uint32_t tid = 0; tid < NT; tid++) {
+      uint32_t LB = 0;
+      for (uint32_t i = 0; i < T - R; i++)
+        if ((tid >> i) & 1u) LB |= 1u << stages[s].tb[i];
+      tt[s * NT + tid] = LB | (swz(LB) << 16);
+    }
+  const uint32_t L = 1u << T;
+  std::vector<cdd> buf(L), xbuf(L);
+  std::vector<std::vector<cdd>> v(NT, std::vector<cdd>(NR));
+  for (uint64_t tile = 0; tile < hp.n_tiles; tile++) {
+    const uint64_t base = pdep_host(tile, hp.outer_mask);
+    // load: 16-byte chunk rows into the natural-order tile
+    for (uint32_t tid = 0; tid < NT; tid++) {
+      const uint64_t t_cp = pdep_host(tid >> cs, hp.high_mask) + (uint64_t(tid & cmask) << 1);
+      for (uint32_t k = 0; k < NR / 2; k++) {
+        const uint64_t g = base + t_cp + prm.ko[k];
+        const uint32_t q = tid + k * NT;
+        if (g + 1 >= amp.size() || 2 * q + 1 >= L) return 4;
+        buf[2 * q] = amp[g];
+        buf[2 * q + 1] = amp[g + 1];
+      }
+    }
+    for (uint32_t tid = 0; tid < NT; tid++) {
+      const uint32_t LB0 = tt[tid] & 0xffffu;
+      for (uint32_t j = 0; j < NR; j++) v[tid][j] = buf[LB0 + prm.lo[j] / 8];
+    }
+    for (uint32_t s = 0; s < ns; s++) {
+      const StageRec &st = stages[s];
+      if (s > 0) {
+        const StageRec &pv = stages[s - 1];
+        for (uint32_t tid = 0; tid < NT; tid++) {
+          const uint32_t PBp = (tt[(s - 1) * NT + tid] >> 16) * 8u;
+          for (uint32_t j = 0; j < NR; j++) {
+            const uint32_t a = (pv.xo[j] ^ PBp) / 8u;
+            if (a >= L) return 4;
+            xbuf[a] = v[tid][j];
+          }
+        }
+        for (uint32_t tid = 0; tid < NT; tid++) {
+          const uint32_t PB = (tt[s * NT + tid] >> 16) * 8u;
+          for (uint32_t j = 0; j < NR; j++) v[tid][j] = xbuf[(st.xo[j] ^ PB) / 8u];
+        }
+      }
+      for (uint32_t o = st.op_begin; o < st.op_end; o++) {
+        const OpRec &op = ops[o];
+        const uint8_t *d = base_ptr + op.data_off;
+        for (uint32_t tid = 0; tid < NT; tid++) {
+          std::vector<cdd> &x = v[tid];
+          if (op.type == OP_DENSE) {
+            const uint32_t M = op.rmask, K = 1u << op.k;
+            const float *m = reinterpret_cast<const float *>(d);  // (re, re, -im, im) per element
+            for (uint32_t g = 0; g < NR; g++) {
+              if (g & M) continue;
+              cdd in[32], out[32];
+              for (uint32_t j = 0; j < K; j++) in[j] = x[g | dep_bits(j, M)];
+              for (uint32_t r = 0; r < K; r++) {
+                cdd acc = 0;
+                for (uint32_t j = 0; j < K; j++) {
+                  const float *e = m + 4 * (r * K + j);
+                  acc += cdd(e[0], e[3]) * in[j];
+                }
+                out[r] = acc;
+              }
+              for (uint32_t r = 0; r < K; r++) x[g | dep_bits(r, M)] = out[r];
+            }
+          } else {
+            const RegPhaseHdr *h = reinterpret_cast<const RegPhaseHdr *>(d);
+            const RegPhaseTerm *t = reinterpret_cast<const RegPhaseTerm *>(d + sizeof(RegPhaseHdr));
+            const uint32_t LB = tt[s * NT + tid] & 0xffffu;
+            cdd e[6];
+            for (uint32_t k = 0; k <= R; k++) {
+              uint32_t turn = 0;
+              for (uint32_t i = k ? h->end[k - 1] : 0u; i < h->end[k]; i++)
+                if ((base & t[i].outer_mask) == t[i].outer_mask && (LB & t[i].tmask) == t[i].tmask) turn += t[i].turn;
+              e[k] = turn_exp(turn);
+            }
+            for (uint32_t j = 0; j < NR; j++) {
+              cdd f = e[0];
+              for (uint32_t i = 0; i < R; i++)
+                if (j >> i & 1u) f *= e[1 + i];
+              if (h->has_d) f *= cdd(h->d[j].x, h->d[j].y);
+              x[j] *= f;
+            }
+          }
+        }
+      }
+    }
+    // store: local bit x of the last stage's thread part goes to qubit oq[x]
+    for (uint32_t tid = 0; tid < NT; tid++) {
+      const uint32_t LB = tt[(ns - 1) * NT + tid] & 0xffffu;
+      uint64_t t_st = 0;
+      for (uint32_t x = 0; x < T; x++)
+        if ((LB >> x) & 1u) t_st |= uint64_t(1) << prm.oq[x];
+      for (uint32_t j = 0; j < NR; j++) {
+        const uint64_t g = base + t_st + prm.go[j];
+        if (g >= amp.size()) return 4;
+        amp[g] = v[tid][j];
+      }
+    }
+  }
+  return 0;
+}
+
+int main(int argc, char **argv) {
+  int n, ng;
+  if (scanf("%d %d", &n, &ng) != 2) return 1;
+  std::vector<sv_gate> ir(static_cast<size_t>(ng));
+  for (int i = 0; i < ng; i++) {
+    sv_gate g{};
+    int kind, nq;
+    if (scanf("%d %d", &kind, &nq) != 2) return 1;
+    g.kind = uint8_t(kind);
+    g.nq = uint8_t(nq);
+    for (int x = 0; x < nq; x++)
+      if (scanf("%d", &g.q[x]) != 1) return 1;
+    if (scanf("%lf %lf %lf", &g.p[0], &g.p[1], &g.p[2]) != 3) return 1;
+    ir[size_t(i)] = g;
+  }
+  sv_opts o{};
+  o.k_max = argc > 1 ? atoi(argv[1]) : 2;
+  o.tile_qubits = argc > 2 ? atoi(argv[2]) : 12;
+  o.low_qubits = argc > 3 ? atoi(argv[3]) : 5;
+  o.kernel_variant = argc > 4 ? atoi(argv[4]) : 0;
+  Plan plan;
+  std::string err;
+  if (!build_plan(n, ir.data(), size_t(ng), &o, plan, err)) {
+    printf("plan error: %s\n", err.c_str());
+    return 1;
+  }
+  std::vector<GateM> gates;
+  if (!convert_ir(n, ir.data(), size_t(ng), gates, err)) return 1;
+  std::mt19937_64 rng(11);
+  std::normal_distribution<double> nd;
+  std::vector<cdd> a(size_t(1) << n), b;
+  double nrm = 0;
+  for (auto &x : a) {
+    x = cdd(nd(rng), nd(rng));
+    nrm += std::norm(x);
+  }
+  for (auto &x : a) x /= std::sqrt(nrm);
+  b = a;
+  for (auto &g : gates) apply_gate(a, n, g);
+  for (size_t p = 0; p < plan.passes.size(); p++) {
+    const int rc = exec_reg_pass(b, plan, p);
+    if (rc) {
+      printf("pass %zu: %s\n", p, rc == 3 ? "not a register pass" : "index out of range");
+      return rc;
+    }
+  }
+  double e = 0;
+  for (size_t i = 0; i < a.size(); i++) e = std::max(e, std::abs(a[i] - b[i]));
+  printf("passes %zu maxerr %.3e\n", plan.passes.size(), e);
+  return e <= 1e-5 ? 0 : 2;
+}

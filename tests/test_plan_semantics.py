@@ -1,4 +1,4 @@
-"""The host planner's fusion against gate-by-gate application (CPU only).
+"""The host planner against gate-by-gate application (CPU only).
 
 tests/plan_semantics/plan_check.cpp compiles the planner source with the host
 compiler, fuses a whole circuit into one pass (all qubits in the tile), applies
@@ -6,7 +6,13 @@ the resulting dense blocks and phase terms -- and the SWAP relabeling of
 register passes -- to a random complex128 state, and compares with applying the
 circuit's gates one at a time.  Covers register-pass fusion (two-qubit phase
 terms, relabeling, blocks kept open past queued diagonal gates) and the
-shared-memory pass's fusion, at fusion widths 2 and 5."""
+shared-memory pass's fusion, at fusion widths 2 and 5.
+
+tests/plan_semantics/plan_exec.cpp goes further: it plans with build_plan and
+executes the packed register-stage passes the way the register kernel reads
+their records (load rows, stage thread bits and swizzled exchange offsets,
+register-position matrices, phase classes, the store's qubit map), so the
+packing is checked on the host too."""
 import os
 import shutil
 import subprocess
@@ -32,15 +38,24 @@ def _cuda_include():
     return None
 
 
-@pytest.fixture(scope="module")
-def checker(tmp_path_factory):
+def _compile(tmp_path_factory, name):
     inc = _cuda_include()
     if inc is None or shutil.which("g++") is None:
         pytest.skip("needs g++ and the CUDA headers")
-    exe = str(tmp_path_factory.mktemp("plan") / "plan_check")
+    exe = str(tmp_path_factory.mktemp("plan") / name)
     subprocess.run(["g++", "-O2", "-std=c++17", "-w", f"-I{inc}", f"-I{CSRC}", "-o", exe,
-                    os.path.join(HERE, "plan_semantics", "plan_check.cpp")], check=True)
+                    os.path.join(HERE, "plan_semantics", name + ".cpp")], check=True)
     return exe
+
+
+@pytest.fixture(scope="module")
+def checker(tmp_path_factory):
+    return _compile(tmp_path_factory, "plan_check")
+
+
+@pytest.fixture(scope="module")
+def executor(tmp_path_factory):
+    return _compile(tmp_path_factory, "plan_exec")
 
 
 def _encode(n, circuit):
@@ -86,3 +101,25 @@ def test_fused_pass_equals_gates(checker, pairs, kmax):
         if r.returncode != 0:
             bad.append(f"{name} n={n}: {r.stdout.strip()} {r.stderr.strip()[:200]}")
     assert not bad, bad
+
+
+EXEC_CASES = ([("qft", 13, W.qft(13)), ("qft", 14, W.qft(14)), ("ghz", 14, W.ghz(14)),
+               ("random_layered", 14, W.random_layered(14, 12, 3)), ("random_layered", 12, W.random_layered(12, 8, 4))]
+              + [("gate_soup", 13, W.random_gate_soup(13, 160, s)) for s in range(4)]
+              + [("interleaved", 12, _interleaved(12, s)) for s in range(3)])
+
+
+@pytest.mark.parametrize("k_max,T,c,variant", [(2, 12, 5, 0), (5, 12, 5, 0), (4, 11, 5, 2), (2, 10, 5, 0),
+                                               (2, 12, 4, 0)])
+def test_packed_register_passes_equal_gates(executor, k_max, T, c, variant):
+    bad, ran = [], 0
+    for name, n, circ in EXEC_CASES:
+        r = subprocess.run([executor, str(k_max), str(T), str(c), str(variant)], input=_encode(n, circ),
+                           capture_output=True, text=True)
+        if r.returncode == 3 and k_max == 5:
+            continue  # a pass with a 5-qubit block runs on the shared-memory kernel
+        ran += 1
+        if r.returncode != 0:
+            bad.append(f"{name} n={n}: rc={r.returncode} {r.stdout.strip()}")
+    assert not bad, bad
+    assert ran >= len(EXEC_CASES) // 2
