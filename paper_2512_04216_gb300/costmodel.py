@@ -4,14 +4,16 @@ hardware-calibrated coefficient times the operation's complexity term).
 For this state-vector backend the operations are the plan's HBM passes and
 its dense-block arithmetic, and the end-of-circuit sampling:
 
-    T_apply(n, circuit) ~ c_fix + c_gate * dense_gates + C_pass(n) * passes + c_flop * flops_eff
+    T_apply(n, circuit) ~ c_fix + c_gate * dense_gates + C_pass(n) * passes
+                          + c_flop * flops + c_phase * phase_ops * 2^n
     T_shots(n, S)       ~ c1(n) + c2 * S
 
 `dense_gates` counts the non-diagonal gates, each of which the host planner
 multiplies into a fused block (this host work dominates small states;
 diagonal gates only add phase terms).  `passes`, dense-block flops and phase
-ops (flops_eff counts a phase op as 48 flops per amplitude) come from the host
-planner (sv_plan_stats, no GPU work).
+ops come from the host planner (sv_plan_stats, no GPU work); a phase op
+(per-thread phase sums, exponentials and a complex product per amplitude) has
+its own coefficient per amplitude, fitted like the others.
 The coefficients are measured once on the device by `calibrate` (synthetic
 circuits of different densities over a grid of qubit counts, one joint least
 squares fit) and C_pass is interpolated in n with a monotone piecewise cubic
@@ -99,18 +101,22 @@ def linear_fit(x, y):
 class CostModel:
     ns: list = field(default_factory=list)        # calibrated qubit counts
     c_pass: list = field(default_factory=list)    # ms per HBM pass at each n
-    c_flop: float = 0.0                           # ms per effective dense-block flop
+    c_flop: float = 0.0                           # ms per dense-block flop
+    c_phase: float = 0.0                          # ms per amplitude per phase op
     c_fix: float = 0.0                            # ms per apply call (upload, launches)
     c_gate: float = 0.0                           # ms of host fusion per non-diagonal gate
     c_shot1: list = field(default_factory=list)   # ms of CDF build + fixed sampling cost at each n
     c_shot2: float = 0.0                          # ms per shot
 
-    # a phase op costs about as much per amplitude as 48 flops of dense block
-    PHASE_FLOPS = 48.0
-
     @staticmethod
     def eff_flops(n: int, stats: dict) -> float:
-        return float(stats["flops"]) + CostModel.PHASE_FLOPS * float(stats["n_phase"]) * float(1 << n)
+        """Dense-block flops of a plan."""
+        return float(stats["flops"])
+
+    @staticmethod
+    def phase_amps(n: int, stats: dict) -> float:
+        """Phase ops times amplitudes."""
+        return float(stats["n_phase"]) * float(1 << n)
 
     def _curve(self, vals, n):
         v = np.maximum(np.asarray(vals, dtype=np.float64), 1e-30)
@@ -124,9 +130,10 @@ class CostModel:
         kinds = np.asarray(ir["kind"][:n_gates])
         return int(n_gates - np.isin(kinds, CostModel.DIAGONAL_KINDS).sum())
 
-    def apply_ms(self, n: int, passes: int, eff_flops: float, dense_gates: int = 0) -> float:
+    def apply_ms(self, n: int, passes: int, eff_flops: float, dense_gates: int = 0,
+                 phase_amps: float = 0.0) -> float:
         return (self.c_fix + self.c_gate * dense_gates + self._curve(self.c_pass, n) * passes
-                + self.c_flop * eff_flops)
+                + self.c_flop * eff_flops + self.c_phase * phase_amps)
 
     def shots_ms(self, n: int, shots: int) -> float:
         return self._curve(self.c_shot1, n) + self.c_shot2 * shots
@@ -135,7 +142,8 @@ class CostModel:
         from . import capi
         st = capi.sv_plan_stats(n, circuit, opts)
         ir, _keep = capi.to_ir(circuit)
-        return (self.apply_ms(n, st["n_passes"], self.eff_flops(n, st), self.dense_gates(ir, len(circuit)))
+        return (self.apply_ms(n, st["n_passes"], self.eff_flops(n, st), self.dense_gates(ir, len(circuit)),
+                              self.phase_amps(n, st))
                 + (self.shots_ms(n, shots) if shots else 0.0))
 
     def to_json(self) -> str:
@@ -177,11 +185,12 @@ def calibrate(ns=(10, 12, 14, 16, 18, 20, 22, 24, 26, 28), reps: int = 2, opts=N
                 e1.record(s.stream)
                 torch.cuda.synchronize()
                 best = min(best, e0.elapsed_time(e1))
-            row = [0.0] * (len(ns) + 3)
+            row = [0.0] * (len(ns) + 4)
             row[i] = float(st["n_passes"])
             row[len(ns)] = CostModel.eff_flops(n, st)
             row[len(ns) + 1] = 1.0
             row[len(ns) + 2] = float(CostModel.dense_gates(ir, len(c)))
+            row[len(ns) + 3] = CostModel.phase_amps(n, st)
             rows.append(row)
             times.append(best)
         for S in (1, 1000, 100000):
@@ -201,6 +210,7 @@ def calibrate(ns=(10, 12, 14, 16, 18, 20, 22, 24, 26, 28), reps: int = 2, opts=N
     model.c_flop = max(float(sol[len(ns)]), 0.0)
     model.c_fix = max(float(sol[len(ns) + 1]), 0.0)
     model.c_gate = max(float(sol[len(ns) + 2]), 0.0)
+    model.c_phase = max(float(sol[len(ns) + 3]), 0.0)
     _, c2 = linear_fit([S for _, S, _ in shot_samples], [t for _, _, t in shot_samples])
     model.c_shot2 = max(c2, 0.0)
     for n in ns:

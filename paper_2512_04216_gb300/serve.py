@@ -125,7 +125,8 @@ class Server:
         if r.id not in self._pred:
             st = capi.sv_plan_stats_ir(r.n, r.ir, r.n_gates, self.opts)
             ms = self.cost_model.apply_ms(r.n, st["n_passes"], self.cost_model.eff_flops(r.n, st),
-                                          self.cost_model.dense_gates(r.ir, r.n_gates))
+                                          self.cost_model.dense_gates(r.ir, r.n_gates),
+                                          self.cost_model.phase_amps(r.n, st))
             ms += self.cost_model.shots_ms(r.n, r.shots) if r.shots else self.cost_model.shots_ms(r.n, 0)
             self._pred[r.id] = ms
         return self._pred[r.id]

@@ -68,5 +68,8 @@ def test_dense_gate_count_skips_diagonal_gates():
              ("x", (0,), ()), ("y", (1,), ()), ("rx", (2,), (0.4,)), ("swap", (3, 4), ())]
     ir, keep = capi.to_ir(mixed)
     assert CM.CostModel.dense_gates(ir, len(mixed)) == 4
-    m = CM.CostModel(ns=[10, 20], c_pass=[1.0, 2.0], c_flop=0.0, c_fix=0.5, c_gate=0.01)
+    m = CM.CostModel(ns=[10, 20], c_pass=[1.0, 2.0], c_flop=0.0, c_fix=0.5, c_gate=0.01, c_phase=1e-6)
     assert abs(m.apply_ms(10, 3, 0.0, 100) - (0.5 + 1.0 + 3 * 1.0)) < 1e-12
+    assert abs(m.apply_ms(10, 3, 0.0, 100, 2.0 * 1024) - (0.5 + 1.0 + 3 * 1.0 + 1e-6 * 2048)) < 1e-12
+    st = {"flops": 123.0, "n_phase": 3}
+    assert CM.CostModel.eff_flops(10, st) == 123.0 and CM.CostModel.phase_amps(10, st) == 3 * 1024
