@@ -6,6 +6,8 @@
 // dense ops on register positions (rmask, (re, re, -im, im) matrices), the
 // register phase ops (classes, D), and the store (oq, go) -- in complex
 // double, and compares the result with the circuit's gates applied one by one.
+// With a chunk size it plans incrementally (PlanBuilder, as the library streams
+// its plans) and runs the chunks in order.
 // Exit status 0 when every amplitude agrees within 1e-5, 2 otherwise, 3 when a
 // pass is not a register pass.
 #include "sv_plan.cpp"
@@ -199,11 +201,30 @@ int main(int argc, char **argv) {
   o.tile_qubits = argc > 2 ? atoi(argv[2]) : 12;
   o.low_qubits = argc > 3 ? atoi(argv[3]) : 5;
   o.kernel_variant = argc > 4 ? atoi(argv[4]) : 0;
-  Plan plan;
+  // chunk > 0: plan incrementally, `chunk` passes at a time (as sv_apply_circuit
+  // streams its plan), and run the chunks' passes in order
+  const int chunk = argc > 5 ? atoi(argv[5]) : 0;
+  std::vector<Plan> plans;
   std::string err;
-  if (!build_plan(n, ir.data(), size_t(ng), &o, plan, err)) {
-    printf("plan error: %s\n", err.c_str());
-    return 1;
+  if (chunk <= 0) {
+    plans.emplace_back();
+    if (!build_plan(n, ir.data(), size_t(ng), &o, plans.back(), err)) {
+      printf("plan error: %s\n", err.c_str());
+      return 1;
+    }
+  } else {
+    PlanBuilder pb;
+    if (!pb.init(n, ir.data(), size_t(ng), &o, err)) {
+      printf("plan error: %s\n", err.c_str());
+      return 1;
+    }
+    while (!pb.done()) {
+      plans.emplace_back();
+      if (!pb.next(plans.back(), size_t(chunk), err)) {
+        printf("plan error: %s\n", err.c_str());
+        return 1;
+      }
+    }
   }
   std::vector<GateM> gates;
   if (!convert_ir(n, ir.data(), size_t(ng), gates, err)) return 1;
@@ -218,15 +239,17 @@ int main(int argc, char **argv) {
   for (auto &x : a) x /= std::sqrt(nrm);
   b = a;
   for (auto &g : gates) apply_gate(a, n, g);
-  for (size_t p = 0; p < plan.passes.size(); p++) {
-    const int rc = exec_reg_pass(b, plan, p);
-    if (rc) {
-      printf("pass %zu: %s\n", p, rc == 3 ? "not a register pass" : "index out of range");
-      return rc;
+  size_t total = 0;
+  for (const Plan &plan : plans)
+    for (size_t p = 0; p < plan.passes.size(); p++, total++) {
+      const int rc = exec_reg_pass(b, plan, p);
+      if (rc) {
+        printf("pass %zu: %s\n", total, rc == 3 ? "not a register pass" : "index out of range");
+        return rc;
+      }
     }
-  }
   double e = 0;
   for (size_t i = 0; i < a.size(); i++) e = std::max(e, std::abs(a[i] - b[i]));
-  printf("passes %zu maxerr %.3e\n", plan.passes.size(), e);
+  printf("plans %zu passes %zu maxerr %.3e\n", plans.size(), total, e);
   return e <= 1e-5 ? 0 : 2;
 }

@@ -123,3 +123,16 @@ def test_packed_register_passes_equal_gates(executor, k_max, T, c, variant):
             bad.append(f"{name} n={n}: rc={r.returncode} {r.stdout.strip()}")
     assert not bad, bad
     assert ran >= len(EXEC_CASES) // 2
+
+
+@pytest.mark.parametrize("chunk", [1, 2, 3])
+def test_streamed_plan_chunks_compose(executor, chunk):
+    """Planning a few passes at a time (as sv_apply_circuit streams its plan)
+    gives chunks whose passes, run in order, still equal the circuit."""
+    bad = []
+    for name, n, circ in EXEC_CASES[:6]:
+        r = subprocess.run([executor, "2", "12", "5", "0", str(chunk)], input=_encode(n, circ),
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            bad.append(f"{name} n={n}: rc={r.returncode} {r.stdout.strip()}")
+    assert not bad, bad
