@@ -1,4 +1,4 @@
-// Host interpreter of packed register-stage plans (KIND_REG passes), for
+// Host interpreter of packed plans (register-stage and shared-memory passes), for
 // tests/test_plan_semantics.py.  It plans a circuit with the library's planner
 // (build_plan), then executes every pass the way the register kernel reads its
 // records -- the load's chunk rows (RegPassParams.ko), stage 0's offsets
@@ -8,8 +8,8 @@
 // double, and compares the result with the circuit's gates applied one by one.
 // With a chunk size it plans incrementally (PlanBuilder, as the library streams
 // its plans) and runs the chunks in order.
-// Exit status 0 when every amplitude agrees within 1e-5, 2 otherwise, 3 when a
-// pass is not a register pass.
+// Shared-memory passes run the way k_pass reads theirs.  Exit status 0 when
+// every amplitude agrees within 1e-5, 2 otherwise, 3 on a tensor-core pass.
 #include "sv_plan.cpp"
 
 #include <cstdio>
@@ -181,6 +181,67 @@ static int exec_reg_pass(std::vector<cdd> &amp, const Plan &plan, size_t p) {
   return 0;
 }
 
+// KIND_SMEM passes (k_pass): the tile in natural order (local index l <-> HBM
+// base + segoff(l >> c) + (l & low)), each op one sweep over it -- dense blocks
+// on local bits lb with float2 (re, im) matrices, phase ops as per-tile sums of
+// single-local-bit terms -- then stored back the same way.
+static int exec_smem_pass(std::vector<cdd> &amp, const Plan &plan, size_t p) {
+  const PlanPass &hp = plan.passes[p];
+  const uint8_t *base_ptr = plan.bytes.data();
+  const uint32_t T = hp.T, c = hp.c, L = 1u << T;
+  const OpRec *ops = reinterpret_cast<const OpRec *>(base_ptr + hp.ops_off);
+  std::vector<cdd> tile(L);
+  for (uint64_t tid = 0; tid < hp.n_tiles; tid++) {
+    const uint64_t base = pdep_host(tid, hp.outer_mask);
+    auto gaddr = [&](uint32_t l) { return base + pdep_host(l >> c, hp.high_mask) + (l & ((1u << c) - 1u)); };
+    for (uint32_t l = 0; l < L; l++) {
+      if (gaddr(l) >= amp.size()) return 4;
+      tile[l] = amp[gaddr(l)];
+    }
+    for (uint32_t o = 0; o < hp.n_ops; o++) {
+      const OpRec &op = ops[o];
+      if (op.type == OP_DENSE) {
+        const float *m = reinterpret_cast<const float *>(base_ptr + op.data_off);  // (re, im) per element
+        const uint32_t K = 1u << op.k;
+        uint32_t gm = 0;
+        for (uint32_t x = 0; x < op.k; x++) gm |= 1u << op.lb[x];
+        for (uint32_t b = 0; b < L; b++) {
+          if (b & gm) continue;
+          cdd in[32], out[32];
+          auto at = [&](uint32_t j) {
+            uint32_t off = 0;
+            for (uint32_t x = 0; x < op.k; x++)
+              if (j >> x & 1u) off |= 1u << op.lb[x];
+            return b | off;
+          };
+          for (uint32_t j = 0; j < K; j++) in[j] = tile[at(j)];
+          for (uint32_t r = 0; r < K; r++) {
+            cdd a = 0;
+            for (uint32_t j = 0; j < K; j++) a += cdd(m[2 * (r * K + j)], m[2 * (r * K + j) + 1]) * in[j];
+            out[r] = a;
+          }
+          for (uint32_t r = 0; r < K; r++) tile[at(r)] = out[r];
+        }
+      } else if (op.type == OP_PHASE) {
+        const PhaseTerm *t = reinterpret_cast<const PhaseTerm *>(base_ptr + op.data_off);
+        uint32_t acc[33] = {0};
+        for (uint32_t i = 0; i < op.count; i++)
+          if ((base & t[i].outer_mask) == t[i].outer_mask) acc[t[i].la + 1] += t[i].turn;
+        for (uint32_t l = 0; l < L; l++) {
+          uint32_t turn = acc[0];
+          for (uint32_t j = 0; j < T; j++)
+            if (l >> j & 1u) turn += acc[1 + j];
+          tile[l] *= turn_exp(turn);
+        }
+      } else {
+        return 5;
+      }
+    }
+    for (uint32_t l = 0; l < L; l++) amp[gaddr(l)] = tile[l];
+  }
+  return 0;
+}
+
 int main(int argc, char **argv) {
   int n, ng;
   if (scanf("%d %d", &n, &ng) != 2) return 1;
@@ -242,9 +303,9 @@ int main(int argc, char **argv) {
   size_t total = 0;
   for (const Plan &plan : plans)
     for (size_t p = 0; p < plan.passes.size(); p++, total++) {
-      const int rc = exec_reg_pass(b, plan, p);
+      const int rc = plan.passes[p].kind == KIND_SMEM ? exec_smem_pass(b, plan, p) : exec_reg_pass(b, plan, p);
       if (rc) {
-        printf("pass %zu: %s\n", total, rc == 3 ? "not a register pass" : "index out of range");
+        printf("pass %zu: %s\n", total, rc == 3 ? "tensor-core pass" : rc == 5 ? "unknown op" : "index out of range");
         return rc;
       }
     }

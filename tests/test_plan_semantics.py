@@ -110,19 +110,17 @@ EXEC_CASES = ([("qft", 13, W.qft(13)), ("qft", 14, W.qft(14)), ("ghz", 14, W.ghz
 
 
 @pytest.mark.parametrize("k_max,T,c,variant", [(2, 12, 5, 0), (5, 12, 5, 0), (4, 11, 5, 2), (2, 10, 5, 0),
-                                               (2, 12, 4, 0)])
-def test_packed_register_passes_equal_gates(executor, k_max, T, c, variant):
-    bad, ran = [], 0
+                                               (2, 12, 4, 0), (3, 12, 5, 1), (5, 10, 3, 1)])
+def test_packed_passes_equal_gates(executor, k_max, T, c, variant):
+    """Register passes (variants 0 and 2; k_max 5 mixes in shared-memory passes
+    for 5-qubit blocks) and shared-memory passes (variant 1)."""
+    bad = []
     for name, n, circ in EXEC_CASES:
         r = subprocess.run([executor, str(k_max), str(T), str(c), str(variant)], input=_encode(n, circ),
                            capture_output=True, text=True)
-        if r.returncode == 3 and k_max == 5:
-            continue  # a pass with a 5-qubit block runs on the shared-memory kernel
-        ran += 1
         if r.returncode != 0:
             bad.append(f"{name} n={n}: rc={r.returncode} {r.stdout.strip()}")
     assert not bad, bad
-    assert ran >= len(EXEC_CASES) // 2
 
 
 @pytest.mark.parametrize("chunk", [1, 2, 3])
