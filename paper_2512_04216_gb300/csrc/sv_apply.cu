@@ -19,6 +19,7 @@
 //
 // Diagonal phase ops tabulate a per-tile phase table from 32-bit turn
 // fractions (exact modulo 2*pi) over the low and high halves of the tile index.
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 
@@ -553,154 +554,208 @@ bool reg_pass_fits(uint32_t T, uint32_t c, uint32_t R, uint32_t n_stages, uint32
 
 
 // ---------------------------------------------------------------------------
-// tensor-core stages (KIND_TC): the persistent register-stage skeleton, with
-// each stage's dense blocks applied as one 3xTF32 tcgen05 GEMM (sv_tc.cu).
+// tensor-core stages (KIND_TC): the register-stage skeleton with 16 amplitudes
+// per thread (R = 4) and each stage's dense blocks applied as one 3xTF32
+// tcgen05 product (sv_tc.cu).  Per stage and 128-row group, the threads split
+// their rows into A_hi / A_lo in tensor memory, one thread of the group issues
+// the stage's 8 MMAs and commits them to the group's mbarrier, and the group
+// reads D back.  Between stages the tile moves through one swizzled exchange
+// buffer with one CTA barrier per exchange: a thread writes its amplitudes back
+// to exactly the positions it read them from at the previous stage, which no
+// other thread reads, so no barrier is needed before the writes.  The next tile
+// is prefetched (16-byte cp.async, natural order) into a separate load buffer as
+// soon as every thread has read the current tile from it (the first exchange's
+// barrier), so the load overlaps most of the tile's stages.  Passes of unitary ops (kPassUnitary) restore each
+// tile's norm before the store: the exact pass keeps it, and the tensor cores'
+// float32 accumulation rounds toward zero, which would otherwise shrink the
+// state by ~1e-7 per stage.
 // ---------------------------------------------------------------------------
 
 constexpr int kTcErrTimeout = 1;
-constexpr size_t kTcStaticSmem = 1024;  // bar, tbase, abort flag (aligned with the dynamic region)
+constexpr size_t kTcStaticSmem = 1024;  // mbarriers and the TMEM base (the static region's size)
 
-template <int NTMAX>
-__global__ void __launch_bounds__(NTMAX, NTMAX <= 128 ? 4 : (NTMAX <= 256 ? 2 : 1)) k_pass_tc(float2 *__restrict__ amp, const uint8_t *__restrict__ plan,
-                                                      uint32_t pass_off, int *__restrict__ err) {
+struct TcLayout {
+  uint32_t L, NT;
+  size_t off_in, off_x, off_red, off_tt, off_data, total;
+};
+
+__host__ __device__ inline TcLayout tc_layout(uint32_t T, uint32_t ns, uint32_t data_bytes) {
+  TcLayout r;
+  r.L = 1u << T;
+  r.NT = 1u << (T - 4);
+  size_t o = 0;
+  r.off_in = o; o += size_t(r.L) * 8;  // load buffer (natural order)
+  r.off_x = o; o += size_t(r.L) * 8;   // exchange buffer (swizzled)
+  r.off_red = o; o += size_t(r.NT / 32) * 8;  // per warp: the tile-norm partials
+  r.off_tt = o; o += size_t(ns) * r.NT * 4;
+  o = (o + 15) & ~size_t(15);
+  r.off_data = o; o += data_bytes;
+  r.total = (o + 15) & ~size_t(15);
+  return r;
+}
+
+// Barrier 1 + g over the 128 threads of row group g (literal ids, so ptxas
+// reserves only the barriers used).
+__device__ __forceinline__ void group_bar_sync(uint32_t g) {
+  switch (g) {
+    case 0: asm volatile("bar.sync 1, 128;\n" ::: "memory"); break;
+    case 1: asm volatile("bar.sync 2, 128;\n" ::: "memory"); break;
+    case 2: asm volatile("bar.sync 3, 128;\n" ::: "memory"); break;
+    default: asm volatile("bar.sync 4, 128;\n" ::: "memory"); break;
+  }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
+    k_pass_tc(float2 *__restrict__ amp, const uint8_t *__restrict__ plan, uint32_t pass_off,
+              const __grid_constant__ RegPassParams prm, int *__restrict__ err) {
   constexpr int NR = 16;  // R = 4 register qubits
+  constexpr uint32_t kT = NT == 128 ? 11u : (NT == 256 ? 12u : 13u);
+  constexpr uint32_t NW = NT / 32, NG = NT / 128;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar[8];  // one per issuing warp (<= 4 groups x 2)
+  __shared__ __align__(8) uint64_t bar[NG];
   __shared__ uint32_t tbase_s;
-  __shared__ int abort_s;
   const PlanPass *P = reinterpret_cast<const PlanPass *>(plan + pass_off);
-  const uint32_t T = P->T, c = P->c;
-  const uint32_t ns = P->n_stages;
+  const uint32_t T = P->T, c = P->c, ns = P->n_stages;
   const uint32_t data_off = P->ops_off, data_bytes = P->data_bytes;
   const uint64_t outer_mask = P->outer_mask, n_tiles = P->n_tiles;
-  const RegLayout lay = reg_layout(T, c, ns, data_bytes);
-  float2 *buf_in = reinterpret_cast<float2 *>(smem + lay.off_in);
-  float2 *buf_x = reinterpret_cast<float2 *>(smem + lay.off_x);
-  uint64_t *segoff = reinterpret_cast<uint64_t *>(smem + lay.off_seg);
+  const bool unitary = (P->flags & kPassUnitary) != 0u;
+  // the launch's shared memory was sized from the host's copy of these fields
+  if (T != kT || T != prm.chk[0] || ns != prm.chk[1] || data_bytes != prm.chk[2] || data_off != prm.chk[3] ||
+      P->R != 4u || P->kind != KIND_TC || ns == 0 || ns > uint32_t(kMaxStages)) {
+    if (threadIdx.x == 0) atomicOr(err, kPlanMismatch);
+    return;
+  }
+  const TcLayout lay = tc_layout(T, ns, data_bytes);
   uint32_t *tt = reinterpret_cast<uint32_t *>(smem + lay.off_tt);
+  float2 *red = reinterpret_cast<float2 *>(smem + lay.off_red);
   uint8_t *data = smem + lay.off_data;
-  const uint32_t tid = threadIdx.x, NT = blockDim.x, warp = tid >> 5;
-  const uint32_t groups = NT >> 7;
-  const uint32_t ncols = groups <= 1 ? 128u : (groups == 2 ? 256u : 512u);
+  const uint32_t tid = threadIdx.x, warp = tid >> 5, g = tid >> 7;
 
   {
     const uint4 *src = reinterpret_cast<const uint4 *>(plan + data_off);
     uint4 *dst = reinterpret_cast<uint4 *>(data);
     for (uint32_t i = tid; i < data_bytes / 16; i += NT) dst[i] = src[i];
   }
-  const uint64_t hm = P->high_mask;
-  for (uint32_t s = tid; s < lay.nseg; s += NT) segoff[s] = pdep_u64(s, hm);
-  fence_proxy_async_smem();  // stage matrices are read by the tensor cores
+  fence_proxy_async_smem();  // stage images are read by the tensor cores
   if (warp == 0) {
-    tmem_alloc(&tbase_s, ncols);
+    tmem_alloc(&tbase_s, NT);  // 128 columns per row group
     tmem_relinquish();
   }
-  if (tid < 8) mbar_init(&bar[tid], 1);
-  if (tid == 0) abort_s = 0;
+  if (tid < NG) mbar_init(&bar[tid], 1);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const StageRec *stages = reinterpret_cast<const StageRec *>(data + (P->stages_off - data_off));
   const OpRec *ops = reinterpret_cast<const OpRec *>(data);
+  // per-thread stage tables (own entries only): low 16 bits local index part, high 16 swizzled
   for (uint32_t s = 0; s < ns; s++) {
     uint32_t LB = 0;
     for (uint32_t i = 0; i < T - 4; i++)
       if ((tid >> i) & 1u) LB |= 1u << stages[s].tb[i];
     tt[s * NT + tid] = LB | (swz(LB) << 16);
   }
-  const uint32_t tbase = tbase_s;
-  const uint32_t tq = tbase + (((warp & 3u) * 32u) << 16) + (tid >> 7) * kTcColsPerGroup;
-  const uint32_t lowmask = (1u << c) - 1u;
+  const uint64_t hm = P->high_mask;
   const uint32_t cs = c - 1u, cmask = (1u << cs) - 1u;
-  const uint32_t nchunk = lay.L >> 1;
-  uint32_t parity = 0;
+  constexpr int NK = NR / 2;  // 16-byte chunks per thread per tile
+  const uint32_t sin = smem_u32(smem + lay.off_in), sx = smem_u32(smem + lay.off_x);
+  const uint32_t tbase = tbase_s;
+  const uint32_t gcols = tbase + g * kTcColsPerGroup;
+  const uint32_t tq = gcols + (((warp & 3u) * 32u) << 16);  // this thread's lane
+  const uint32_t t_ldx = (tt[tid] & 0xffffu) * 8u;
+  uint64_t t_st = 0;
+  {
+    const uint32_t LB = tt[(ns - 1) * NT + tid] & 0xffffu;
+    for (uint32_t x = 0; x < T; x++)
+      if ((LB >> x) & 1u) t_st |= uint64_t(1) << prm.oq[x];
+  }
+  const uint64_t t_cp = pdep_u64(tid >> cs, hm) + (uint64_t(tid & cmask) << 1);
 
   uint64_t tile = blockIdx.x;
   uint64_t base = tile < n_tiles ? pdep_u64(tile, outer_mask) : 0;
   if (tile < n_tiles) {
-    for (uint32_t i = tid; i < nchunk; i += NT)
-      cp_async16(buf_in + 2 * i, amp + base + segoff[i >> cs] + (uint64_t(i & cmask) << 1));
+#pragma unroll
+    for (int k = 0; k < NK; k++) cp_async16_s(sin + (tid + k * NT) * 16u, amp + base + t_cp + prm.ko[k]);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
-  __syncthreads();
-
+  uint32_t parity = 0;
+  bool bad = false, aborted = false;
   float2 v[NR];
-  bool aborted = false;
-  while (tile < n_tiles && !aborted) {
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
-    __syncthreads();
-    {
-      const StageRec &st = stages[0];
-      const uint32_t LB = tt[tid] & 0xffffu;
-#pragma unroll
-      for (int j = 0; j < NR; j++) v[j] = buf_in[uint32_t(st.la[j]) | LB];
-    }
-    __syncthreads();
+  while (tile < n_tiles) {
     const uint64_t next = tile + gridDim.x;
     const uint64_t base_next = next < n_tiles ? pdep_u64(next, outer_mask) : 0;
-    if (next < n_tiles) {
-      for (uint32_t i = tid; i < nchunk; i += NT)
-        cp_async16(buf_in + 2 * i, amp + base_next + segoff[i >> cs] + (uint64_t(i & cmask) << 1));
-      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    if (__syncthreads_or(bad)) {  // the tile has landed; the previous tile is done
+      aborted = true;
+      break;
+    }
+#pragma unroll
+    for (int j = 0; j < NR; j++) v[j] = lds64(sin + t_ldx + prm.lo[j]);
+    float2 nin = make_float2(0.f, 0.f);
+    if (unitary) {
+#pragma unroll
+      for (int j = 0; j < NR; j++) nin = __ffma2_rn(v[j], v[j], nin);
+    }
+    if (ns == 1) {  // no exchange barrier: make sure every thread has read the load buffer
+      if (__syncthreads_or(bad)) {
+        aborted = true;
+        break;
+      }
+      if (next < n_tiles) {
+#pragma unroll
+        for (int k = 0; k < NK; k++) cp_async16_s(sin + (tid + k * NT) * 16u, amp + base_next + t_cp + prm.ko[k]);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+      }
     }
     for (uint32_t s = 0; s < ns; s++) {
       const StageRec &st = stages[s];
       const uint32_t w = tt[s * NT + tid];
-      const uint32_t LB = w & 0xffffu, PB = w >> 16;
+      const uint32_t LB = w & 0xffffu;
       if (s > 0) {
-        const StageRec &pv = stages[s - 1];
-        const uint32_t PBp = tt[(s - 1) * NT + tid] >> 16;
-        __syncthreads();
+        const uint32_t PBp = (tt[(s - 1) * NT + tid] >> 16) * 8u, PB = (w >> 16) * 8u;
+        uint32_t xo[NR];
+        const uint4 *q = reinterpret_cast<const uint4 *>(stages[s - 1].xo);
 #pragma unroll
-        for (int j = 0; j < NR; j++) buf_x[uint32_t(pv.pa[j]) ^ PBp] = v[j];
-        __syncthreads();
+        for (int j = 0; j < NR / 4; j++) {
+          const uint4 t4 = q[j];
+          xo[4 * j] = t4.x; xo[4 * j + 1] = t4.y; xo[4 * j + 2] = t4.z; xo[4 * j + 3] = t4.w;
+        }
 #pragma unroll
-        for (int j = 0; j < NR; j++) v[j] = buf_x[uint32_t(st.pa[j]) ^ PB];
-      }
-      if (st.flags & 4u) {
-        uint32_t r[32];
-#pragma unroll
-        for (int j = 0; j < NR; j++) {
-          r[2 * j] = tf32_hi_bits(v[j].x);
-          r[2 * j + 1] = tf32_hi_bits(v[j].y);
-        }
-        tmem_st32(tq, r);
-#pragma unroll
-        for (int j = 0; j < NR; j++) {
-          r[2 * j] = __float_as_uint(__fsub_rn(v[j].x, __uint_as_float(tf32_hi_bits(v[j].x))));
-          r[2 * j + 1] = __float_as_uint(__fsub_rn(v[j].y, __uint_as_float(tf32_hi_bits(v[j].y))));
-        }
-        tmem_st32(tq + 32, r);
-        tmem_wait_st();
-        tc_fence_before();
-        __syncthreads();
-        // issuers: lane 0 of warp 2g + h issues half h of group g's product
-        if ((tid & 31) == 0 && warp < kTcIssuersPerGroup * groups) {
-          tc_fence_after();
-          issue_stage_mma_half(tbase, warp / kTcIssuersPerGroup, warp % kTcIssuersPerGroup,
-                               smem_u32(data + (st.b_off - data_off)));
-          mma_commit(&bar[warp]);
-        }
-        {
-          const uint32_t g = tid >> 7;
-          if (!mbar_wait_bounded(&bar[2 * g], parity) || !mbar_wait_bounded(&bar[2 * g + 1], parity))
-            abort_s = 1;
-        }
-        parity ^= 1u;
-        __syncthreads();
-        if (abort_s) {
+        for (int j = 0; j < NR; j++) sts64(sx + (xo[j] ^ PBp), v[j]);
+        if (__syncthreads_or(bad)) {
           aborted = true;
           break;
         }
-        tc_fence_after();
-        tmem_ld32(tq + 64, r);
-        uint32_t r1[32];
-        tmem_ld32(tq + 96, r1);
-        tmem_wait_ld();
+        if (s == 1 && next < n_tiles) {  // every thread has read the load buffer at stage 0
 #pragma unroll
-        for (int j = 0; j < NR; j++)
-          v[j] = make_float2(__fadd_rn(__uint_as_float(r[2 * j]), __uint_as_float(r1[2 * j])),
-                             __fadd_rn(__uint_as_float(r[2 * j + 1]), __uint_as_float(r1[2 * j + 1])));
+          for (int k = 0; k < NK; k++)
+            cp_async16_s(sin + (tid + k * NT) * 16u, amp + base_next + t_cp + prm.ko[k]);
+          asm volatile("cp.async.commit_group;\n" ::: "memory");
+        }
+        q = reinterpret_cast<const uint4 *>(st.xo);
+#pragma unroll
+        for (int j = 0; j < NR / 4; j++) {
+          const uint4 t4 = q[j];
+          xo[4 * j] = t4.x; xo[4 * j + 1] = t4.y; xo[4 * j + 2] = t4.z; xo[4 * j + 3] = t4.w;
+        }
+#pragma unroll
+        for (int j = 0; j < NR; j++) v[j] = lds64(sx + (xo[j] ^ PB));
+      }
+      if (st.flags & 4u) {
+        store_row_split(tq, v);
+        tmem_wait_st();
+        tc_fence_before();
+        group_bar_sync(g);  // the group's rows are in tensor memory
+        if ((tid & 127u) == 0) {  // one thread issues, commits and waits; the others block
+          tc_fence_after();
+          issue_stage_mma(gcols, smem_u32(data + (st.b_off - data_off)));
+          mma_commit(&bar[g]);
+          if (!mbar_wait_bounded(&bar[g], parity)) bad = true;
+        }
+        parity ^= 1u;
+        group_bar_sync(g);  // the product is in tensor memory
+        tc_fence_after();
+        load_row_sum(tq, v);
       }
       const uint32_t oe = st.op_end;
       for (uint32_t o = st.op_begin; o < oe; o++) {
@@ -709,14 +764,39 @@ __global__ void __launch_bounds__(NTMAX, NTMAX <= 128 ? 4 : (NTMAX <= 256 ? 2 : 
       }
     }
     if (aborted) break;
-    {
-      const StageRec &st = stages[ns - 1];
-      const uint32_t LB = tt[(ns - 1) * NT + tid] & 0xffffu;
+    if (unitary) {
+      float2 nout = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int j = 0; j < NR; j++) {
-        const uint32_t l = uint32_t(st.la[j]) | LB;
-        __stcs(amp + base + segoff[l >> c] + (l & lowmask), v[j]);
+      for (int j = 0; j < NR; j++) nout = __ffma2_rn(v[j], v[j], nout);
+      float a = nin.x + nin.y, b = nout.x + nout.y;
+#pragma unroll
+      for (int m = 16; m > 0; m >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, m);
+        b += __shfl_xor_sync(0xffffffffu, b, m);
       }
+      if ((tid & 31u) == 0) red[warp] = make_float2(a, b);
+      if (__syncthreads_or(bad)) {
+        aborted = true;
+        break;
+      }
+      float si = 0.f, so = 0.f;
+#pragma unroll
+      for (uint32_t x = 0; x < NW; x++) {
+        const float2 r = red[x];
+        si += r.x;
+        so += r.y;
+      }
+      if (si > 0.f && so > 0.f) {
+        const float sc = sqrtf(__fdiv_rn(si, so));
+        const float2 s2 = make_float2(sc, sc);
+#pragma unroll
+        for (int j = 0; j < NR; j++) v[j] = __fmul2_rn(v[j], s2);
+      }
+    }
+    {
+      float2 *dst = amp + base + t_st;
+#pragma unroll
+      for (int j = 0; j < NR; j++) __stcs(dst + prm.go[j], v[j]);
     }
     tile = next;
     base = base_next;
@@ -724,25 +804,24 @@ __global__ void __launch_bounds__(NTMAX, NTMAX <= 128 ? 4 : (NTMAX <= 256 ? 2 : 
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tbase, ncols);
-  if (tid == 0 && abort_s) atomicExch(err, kTcErrTimeout);
+  if (warp == 0) tmem_dealloc(tbase, NT);
+  if (tid == 0 && aborted) atomicOr(err, kTcErrTimeout);
 }
 
 // Smallest dynamic shared memory that keeps (512 / TMEM columns) CTAs per SM at
 // most, so tcgen05.alloc never waits for a CTA that only finishes at the end.
-static size_t tc_smem_floor(uint32_t groups) {
+static size_t tc_smem_floor(uint32_t nt) {
   const size_t per_sm = 233472;  // 228 KiB of shared memory per SM
-  const uint32_t ctas = groups <= 1 ? 4u : (groups == 2 ? 2u : 1u);
+  const uint32_t ctas = 512u / nt;  // TMEM columns per CTA = nt
   return per_sm / (ctas + 1) + 1024;
 }
 
-template <int NTMAX>
-static cudaError_t launch_tc(float2 *amp, const uint8_t *plan, uint32_t off, const PlanPass &hp, int *err,
-                             cudaStream_t st) {
-  const RegLayout lay = reg_layout(hp.T, hp.c, hp.n_stages, hp.data_bytes);
-  const uint32_t nt = 1u << (hp.T - 4);
+template <int NT>
+static cudaError_t launch_tc(float2 *amp, const uint8_t *plan, uint32_t off, const PlanPass &hp,
+                             const RegPassParams &prm, int *err, cudaStream_t st) {
+  const TcLayout lay = tc_layout(hp.T, hp.n_stages, hp.data_bytes);
   size_t smem = lay.total;
-  const size_t floor_ = tc_smem_floor(nt >> 7);
+  const size_t floor_ = tc_smem_floor(NT);
   if (smem < floor_) smem = floor_;
   if (smem + kTcStaticSmem > kSmemOptIn) return cudaErrorInvalidValue;
   static std::atomic<uint64_t> configured{0};
@@ -751,28 +830,37 @@ static cudaError_t launch_tc(float2 *amp, const uint8_t *plan, uint32_t off, con
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = once_per_device(configured, sms, dev, [] {
-    return cudaFuncSetAttribute(k_pass_tc<NTMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(kSmemOptIn - kTcStaticSmem));
+    cudaError_t r = cudaFuncSetAttribute(k_pass_tc<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(kSmemOptIn - kTcStaticSmem));
+    // all of the SM's unified memory as shared memory, so the occupancy below
+    // (and the launch) can place two ~110 KB CTAs per SM
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(k_pass_tc<NT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               int(cudaSharedmemCarveoutMaxShared));
+    return r;
   }, &nsm);
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass_tc<NTMAX>, int(nt), smem);
-  if (e != cudaSuccess) return e;
+  // CTAs per SM: shared memory (228 KiB per SM, 1 KiB reserved per CTA), tensor
+  // memory (512 columns, NT per CTA) and registers (128 per thread).  The
+  // runtime's occupancy query is not used: it reported one CTA per SM for ~108 KB
+  // CTAs that fit twice.
+  int per_sm = int(233472 / (smem + kTcStaticSmem + 1024));
+  per_sm = std::min(per_sm, int(512 / NT));
+  per_sm = std::min(per_sm, int(65536 / (NT * 128)));
   if (per_sm < 1) per_sm = 1;
   if (nsm < 1) nsm = 1;
   const uint64_t want = uint64_t(nsm) * per_sm;
   const unsigned grid = unsigned(hp.n_tiles < want ? hp.n_tiles : want);
-  k_pass_tc<NTMAX><<<grid, nt, smem, st>>>(amp, plan, off, err);
+  k_pass_tc<NT><<<grid, NT, smem, st>>>(amp, plan, off, prm, err);
   count_launch();
   return cudaGetLastError();
 }
 
 bool tc_pass_fits(uint32_t T, uint32_t c, uint32_t n_stages, uint32_t data_bytes) {
-  if (T < 11 || T > 13 || T - c < 4) return false;
-  size_t total = reg_layout(T, c, n_stages, data_bytes).total;
-  const size_t floor_ = tc_smem_floor((1u << (T - 4)) >> 7);
-  if (total < floor_) total = floor_;
-  return total + kTcStaticSmem <= kSmemOptIn;
+  if (T < 11 || T > 13 || T < c + 4 || c < 1 || n_stages < 1 || n_stages > uint32_t(kMaxStages) ||
+      data_bytes > kMaxPassData)
+    return false;
+  return tc_layout(T, n_stages, data_bytes).total + kTcStaticSmem <= kSmemOptIn;
 }
 
 static size_t pass_smem(uint32_t T, uint32_t c, int kmax) {
@@ -809,9 +897,11 @@ static cudaError_t launch_k(float2 *amp, const uint8_t *plan, uint32_t off, cons
 cudaError_t launch_pass(float2 *amp, const uint8_t *plan_dev, uint32_t pass_off,
                         const PlanPass &hp, const RegPassParams *prm, int *err, cudaStream_t stream) {
   if (hp.kind == KIND_TC) {
-    if (hp.T <= 11) return launch_tc<128>(amp, plan_dev, pass_off, hp, err, stream);
-    if (hp.T == 12) return launch_tc<256>(amp, plan_dev, pass_off, hp, err, stream);
-    return launch_tc<512>(amp, plan_dev, pass_off, hp, err, stream);
+    if (!prm || !err) return cudaErrorInvalidValue;
+    if (hp.T == 11) return launch_tc<128>(amp, plan_dev, pass_off, hp, *prm, err, stream);
+    if (hp.T == 12) return launch_tc<256>(amp, plan_dev, pass_off, hp, *prm, err, stream);
+    if (hp.T == 13) return launch_tc<512>(amp, plan_dev, pass_off, hp, *prm, err, stream);
+    return cudaErrorInvalidValue;
   }
   if (hp.kind == KIND_REG) {
     if (!prm || !err) return cudaErrorInvalidValue;

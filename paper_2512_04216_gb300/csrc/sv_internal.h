@@ -34,6 +34,11 @@ constexpr int kMaxK = 5;       // largest fused block
 
 enum : uint32_t { KIND_SMEM = 0, KIND_REG = 1, KIND_TC = 2 };
 
+// PlanPass::flags.  A pass of unitary ops maps each tile's amplitudes by a
+// unitary of the tile's 2^T-dimensional space (its ops act on tile qubits, with
+// outer qubits only as fixed controls and phases), so it keeps every tile's norm.
+constexpr uint32_t kPassUnitary = 1;
+
 struct alignas(16) PlanPass {
   uint64_t outer_mask;  // physical qubits outside the tile (within n)
   uint64_t high_mask;   // tile qubits >= c (their ascending order = local bits c..T-1)
@@ -50,7 +55,8 @@ struct alignas(16) PlanPass {
   uint32_t n_stages;
   uint32_t stages_off;  // byte offset of StageRec[n_stages]
   uint32_t data_bytes;  // bytes from ops_off to the end of this pass's records
-  uint32_t pad_[3];
+  uint32_t flags;       // kPassUnitary: every op of the pass is unitary
+  uint32_t pad_[2];
   int8_t lq[32];        // local bit -> physical qubit
 };
 

@@ -125,6 +125,16 @@ static bool gate_matrix(const sv_gate &g, GateM &out, std::string &err) {
           return false;
         }
       }
+      // max |(U^dagger U - I)_ij|: the tensor-core pass restores tile norms only
+      // for passes whose gates are all unitary
+      double dev = 0.0;
+      for (size_t a = 0; a < K; a++)
+        for (size_t b = 0; b < K; b++) {
+          cd x = (a == b) ? cd(-1.0) : cd(0.0);
+          for (size_t r = 0; r < K; r++) x += std::conj(out.m[r * K + a]) * out.m[r * K + b];
+          dev = std::max(dev, std::abs(x));
+        }
+      out.unitary = dev <= 1e-6;
       break;
     }
     default:
@@ -656,8 +666,15 @@ static void apply_on_positions(std::vector<cd> &U, const std::vector<cd> &G, int
 
 // Packs a tensor-core pass (records after the PlanPass headers); false when
 // it does not fit, leaving buf untouched.
+static RegPassParams reg_params(const PlanPass &hp, const StageRec &first, const StageRec &last,
+                                const int *outq);
+
+// `unitary`: every gate of the pass is unitary (the kernel then restores tile
+// norms); `outq`: local bit -> physical qubit of the store; `rp` receives the
+// kernel's address tables and record checks.
 static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint32_t> &omask, const int *lpos,
-                         int T, int c, PlanPass &hp, std::vector<uint8_t> &buf, sv_plan_info &info) {
+                         int T, int c, bool unitary, const int *outq, PlanPass &hp, std::vector<uint8_t> &buf,
+                         RegPassParams &rp, sv_plan_info &info) {
   std::vector<HStage> stages;
   assign_stages(ops, omask, T, c, 4, stages, true);
   size_t nphase = 0, terms_bytes = 0, nmma = 0;
@@ -753,6 +770,12 @@ static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint3
   hp.n_phase_terms = nterms;
   hp.kind = KIND_TC;
   hp.R = 4;
+  hp.flags = unitary ? kPassUnitary : 0u;
+  rp = reg_params(hp, srecs.front(), srecs.back(), outq);
+  rp.chk[0] = hp.T;
+  rp.chk[1] = hp.n_stages;
+  rp.chk[2] = hp.data_bytes;
+  rp.chk[3] = hp.ops_off;
   info.n_stages += srecs.size();
   info.tc_stages += nmma;
   return true;
@@ -1113,8 +1136,10 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
     bool store_natural = true;
     for (int q = 0; q < c; q++) store_natural &= store_lanes[size_t(q)] == q;
     // tensor-core stages (precision 1) when the pass fits the TC kernel
-    if (o.precision == 1 && kmx <= 4 &&
-        pack_tc_pass(ph.ops, omask, lpos, int(hp.T), c, hp, buf, plan.info)) {
+    bool unitary = true;
+    for (uint32_t gi : ph.acc) unitary &= gates[gi].unitary;
+    if (o.precision == 1 && kmx <= 4 && !ph.relabeled &&
+        pack_tc_pass(ph.ops, omask, lpos, int(hp.T), c, unitary, outq, hp, buf, plan.rparams[p], plan.info)) {
       hp.kmax = kmx;
       for (auto &op : ph.ops)
         if (op.type == OP_DENSE) plan.info.flops += uint64_t(amps * 8.0 * double(1 << op.blk.k()));

@@ -17,6 +17,7 @@ struct GateM {
   uint64_t mask = 0;
   bool diag = false;
   bool swap = false;  // SWAP gate (a pure exchange of two qubits)
+  bool unitary = true;  // false for a UNITARY matrix with max |U^dagger U - I| > 1e-6
   std::vector<std::complex<double>> m;  // 2^k x 2^k row-major
 };
 

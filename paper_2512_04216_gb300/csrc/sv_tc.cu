@@ -1,4 +1,4 @@
-// sv_tc.cu -- tensor-core (tcgen05, 3xTF32) pass kernel.
+// sv_tc.cu -- tensor-core (tcgen05, 3xTF32) stage product: self-test and host helpers.
 //
 // A register stage of a pass (see StageRec) holds, in every thread, the 16
 // amplitudes of one "row": the 16 values of the stage's four register qubits
@@ -16,21 +16,20 @@
 // x and x_lo = x - x_hi; the product is taken as A_hi*B_hi + A_hi*B_lo +
 // A_lo*B_hi with float32 accumulation, dropping A_lo*B_lo -- the split-precision
 // tensor-core scheme of Ootomo & Yokota (2022), after Markidis et al. (2018).
-// B is split on the host, A on the device; both round x_hi to the nearest TF32
-// value and take x_lo = x - x_hi (exact in float32).
+// B is split on the host (x_hi = x rounded to the nearest TF32 value), A on the
+// device (Veltkamp splitting, also round to nearest); x_lo takes either sign,
+// so the tensor core's truncation of x_lo to TF32 has no systematic direction.
 //
-// Mapping to tcgen05 (one CTA, 128 * H threads, H = 1, 2 or 4 row groups):
-//   * A_hi, A_lo of row group h live in tensor memory (lane = row % 128,
-//     32 columns each), written by the threads with tcgen05.st;
-//   * B_hi, B_lo (per stage, 8 KB) sit in shared memory in the canonical
-//     K-major layout without swizzle (8 x 16-byte core matrices);
-//   * two accumulators D0, D1 (32 fp32 columns each per row group) live in
-//     tensor memory; two threads (lane 0 of two warps) per row group each issue
-//     the 3 products of half of the K steps (3 x 2 MMAs of shape M=128, N=32,
-//     K=8) into their own accumulator and commit them to their own mbarrier --
-//     one issuing thread waits ~230 cycles per tcgen05.mma, so issue is spread;
-//   * D = D0 + D1 is formed in registers after tcgen05.ld; every mbarrier wait
-//     is bounded by %globaltimer and reports SV_ERR_TIMEOUT through `err`.
+// Mapping to tcgen05 (per 128-row group):
+//   * A_hi, A_lo live in tensor memory (lane = row % 128, 32 columns each),
+//     written by the threads with tcgen05.st;
+//   * B' = [B_hi ; B_lo] (per stage, 64 x 32, 8 KB) sits in shared memory in the
+//     canonical K-major layout without swizzle (8-row x 16-byte core matrices);
+//   * one thread issues the stage's 8 MMAs (issue_stage_mma): A_hi times B'
+//     (N = 64) gives A_hi B_hi in D_left and A_hi B_lo in D_right, then A_lo
+//     times B_hi (N = 32) accumulates into D_left; the threads add D_left and
+//     D_right (round to nearest) after tcgen05.ld;
+//   * every mbarrier wait is bounded by %globaltimer and reported, never trapped.
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -46,9 +45,8 @@ namespace svgb {
 __global__ void __launch_bounds__(128) k_tc_selftest(const float *__restrict__ A, const uint8_t *__restrict__ bimg,
                                                      float *__restrict__ D, int *__restrict__ status) {
   __shared__ __align__(1024) uint8_t bsm[kTcBImage];
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tbase_s;
-  __shared__ int abort_s;
   const uint32_t tid = threadIdx.x, warp = tid >> 5;
   for (uint32_t i = tid; i < kTcBImage / 16; i += blockDim.x)
     reinterpret_cast<uint4 *>(bsm)[i] = reinterpret_cast<const uint4 *>(bimg)[i];
@@ -57,43 +55,37 @@ __global__ void __launch_bounds__(128) k_tc_selftest(const float *__restrict__ A
     tmem_alloc(&tbase_s, 128);
     tmem_relinquish();
   }
-  if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    abort_s = 0;
-  }
+  if (tid == 0) mbar_init(&bar, 1);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tbase_s;
   const uint32_t tq = tbase + ((warp * 32u) << 16);
-  float x[32];
-  for (int i = 0; i < 32; i++) x[i] = A[tid * 32 + i];
-  uint32_t hi[32], lo[32];
-  split_row(x, hi, lo);
-  tmem_st32(tq + 0, hi);
-  tmem_st32(tq + 32, lo);
+  float2 v[16];
+  for (int j = 0; j < 16; j++) v[j] = make_float2(A[tid * 32 + 2 * j], A[tid * 32 + 2 * j + 1]);
+  store_row_split(tq, v);
   tmem_wait_st();
   tc_fence_before();
   __syncthreads();
-  if ((tid & 31) == 0 && warp < kTcIssuersPerGroup) {
+  if (tid == 0) {
     tc_fence_after();
-    issue_stage_mma_half(tbase, 0, warp, smem_u32(bsm));
-    mma_commit(&bar[warp]);
+    issue_stage_mma(tbase, smem_u32(bsm));
+    mma_commit(&bar);
   }
-  if (!mbar_wait_bounded(&bar[0], 0) || !mbar_wait_bounded(&bar[1], 0)) abort_s = 1;
-  __syncthreads();
+  const bool ok = mbar_wait_bounded(&bar, 0);
   tc_fence_after();
-  if (!abort_s) {
-    uint32_t d0[32], d1[32];
-    tmem_ld32(tq + 64, d0);
-    tmem_ld32(tq + 96, d1);
-    tmem_wait_ld();
-    for (int i = 0; i < 32; i++) D[tid * 32 + i] = __fadd_rn(__uint_as_float(d0[i]), __uint_as_float(d1[i]));
+  if (__syncthreads_and(ok)) {
+    load_row_sum(tq, v);
+    for (int j = 0; j < 16; j++) {
+      D[tid * 32 + 2 * j] = v[j].x;
+      D[tid * 32 + 2 * j + 1] = v[j].y;
+    }
+    if (tid == 0) *status = 0;
+  } else if (tid == 0) {
+    *status = 1;
   }
   tc_fence_before();
   __syncthreads();
-  if (tid == 0) *status = abort_s;
   if (warp == 0) tmem_dealloc(tbase, 128);
 }
 
@@ -138,7 +130,7 @@ static inline float tf32_rn(float f) {
 
 size_t tc_b_offset(int n, int k) {
   const int ks = k >> 3, kk = k & 7;
-  return size_t(ks) * 1024 + size_t(n >> 3) * 256 + size_t(kk >> 2) * 128 + size_t(n & 7) * 16 +
+  return size_t(ks) * kTcBKStep + size_t(n >> 3) * 256 + size_t(kk >> 2) * 128 + size_t(n & 7) * 16 +
          size_t(kk & 3) * 4;
 }
 
@@ -150,7 +142,7 @@ void tc_b_image(const double *B, uint8_t *img) {
       const float hi = tf32_rn(float(x));
       const float lo = tf32_rn(float(x - double(hi)));
       std::memcpy(img + tc_b_offset(n, k), &hi, 4);
-      std::memcpy(img + 4096 + tc_b_offset(n, k), &lo, 4);
+      std::memcpy(img + tc_b_offset(n + 32, k), &lo, 4);
     }
 }
 

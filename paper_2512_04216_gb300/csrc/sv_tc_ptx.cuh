@@ -74,7 +74,7 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                : "memory");
 }
 
-// D(tmem) (+)= A(tmem) * B(smem descriptor); kind::tf32, M=128, N=32, K=8.
+// D(tmem) (+)= A(tmem) * B(smem descriptor); kind::tf32, M=128, K=8, N from idesc.
 __device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
                                             uint32_t accumulate) {
   asm volatile(
@@ -120,50 +120,68 @@ __device__ __forceinline__ uint64_t b_desc(uint32_t saddr) {
          (uint64_t(1) << 46);
 }
 
-// Instruction descriptor: D f32, A/B tf32, both K-major, N=32, M=128.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+// Instruction descriptors: D f32, A/B tf32, both K-major, M=128, N=64 or N=32.
+constexpr uint32_t kIdescTf32(uint32_t n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
+constexpr uint32_t kIdescN64 = kIdescTf32(64);
+constexpr uint32_t kIdescN32 = kIdescTf32(32);
 
-// Half h (K steps 2h, 2h+1) of the 3xTF32 product of one stage for row group g,
-// accumulated into its own D_h (columns 64 + 32h of the group); issued by one
-// thread.  A single issuing thread waits ~230 cycles per tcgen05.mma whatever
-// the shape, so each group's products are split over two issuers and the two
-// partial accumulators are added after tcgen05.ld.
-__device__ __forceinline__ void issue_stage_mma_half(uint32_t tbase, uint32_t g, uint32_t h, uint32_t b_saddr) {
-  const uint32_t a_hi = tbase + g * kTcColsPerGroup, a_lo = a_hi + 32, d = a_hi + 64 + 32 * h;
-  const uint32_t bhi = b_saddr, blo = b_saddr + 4 * 1024;
+// The 3xTF32 product of one stage for one 128-row group, issued by one thread:
+//   [D_left | D_right] = A_hi * [B_hi | B_lo]^T   (N = 64, 4 K steps)
+//   D_left            += A_lo * B_hi^T            (N = 32, 4 K steps)
+// so D_left + D_right = A_hi B_hi + A_lo B_hi + A_hi B_lo.  Stacking B_hi and
+// B_lo along N takes 8 MMAs per stage instead of 12.  cols: the group's TMEM
+// columns (A_hi at +0, A_lo at +32, D at +64); b_saddr: the stage image B'.
+__device__ __forceinline__ void issue_stage_mma(uint32_t cols, uint32_t b_saddr) {
+  const uint32_t a_hi = cols, a_lo = cols + 32, d = cols + 64;
 #pragma unroll
-  for (uint32_t i = 0; i < 2; i++) {
-    const uint32_t ks = 2 * h + i;
-    mma_tf32_ts(d, a_hi + 8 * ks, b_desc(blo + ks * 1024), kIdesc, i > 0);
-  }
+  for (uint32_t ks = 0; ks < 4; ks++) mma_tf32_ts(d, a_hi + 8 * ks, b_desc(b_saddr + ks * kTcBKStep), kIdescN64, ks > 0);
 #pragma unroll
-  for (uint32_t i = 0; i < 2; i++) {
-    const uint32_t ks = 2 * h + i;
-    mma_tf32_ts(d, a_lo + 8 * ks, b_desc(bhi + ks * 1024), kIdesc, 1);
-  }
-#pragma unroll
-  for (uint32_t i = 0; i < 2; i++) {
-    const uint32_t ks = 2 * h + i;
-    mma_tf32_ts(d, a_hi + 8 * ks, b_desc(bhi + ks * 1024), kIdesc, 1);
-  }
+  for (uint32_t ks = 0; ks < 4; ks++) mma_tf32_ts(d, a_lo + 8 * ks, b_desc(b_saddr + ks * kTcBKStep), kIdescN32, 1);
 }
 
-// x_hi: x rounded to the nearest TF32 value (ties away from zero; the 13 low
-// mantissa bits cleared), so x_lo = x - x_hi (exact in float32) takes either
-// sign and |x_lo| <= 2^-11 |x|.  Truncating instead would give x_lo the sign
-// of x, and the tensor core's own treatment of x_lo's low bits would then bias
-// every product towards zero.
-__device__ __forceinline__ uint32_t tf32_hi_bits(float x) {
-  return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
+// Veltkamp splitting (Dekker 1971) of a float pair: with c = x * (2^13 + 1),
+// hi = c - (c - x) keeps the 11 leading significant bits of x, rounded to
+// nearest, which is exactly a TF32 value; lo = x - hi is exact in float32 and
+// takes either sign, |lo| <= 2^-12 |x|.  Each step is one paired instruction
+// (an FMA with multiplier -1 is a single-rounding subtraction).
+__device__ __forceinline__ void split_pair(float2 x, float2 &hi, float2 &lo) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 c = __fmul2_rn(x, make_float2(8193.f, 8193.f));
+  const float2 t = __ffma2_rn(x, m1, c);   // c - x
+  hi = __ffma2_rn(t, m1, c);               // c - (c - x)
+  lo = __ffma2_rn(hi, m1, x);              // x - hi
 }
 
-__device__ __forceinline__ void split_row(const float (&x)[32], uint32_t (&hi)[32], uint32_t (&lo)[32]) {
+// Split the 16 amplitudes of a row and store A_hi, A_lo (32 columns each,
+// interleaved re, im) at TMEM address a (this thread's lane).
+__device__ __forceinline__ void store_row_split(uint32_t a, const float2 (&v)[16]) {
+  uint32_t h[32], l[32];
 #pragma unroll
-  for (int i = 0; i < 32; i++) {
-    const uint32_t h = tf32_hi_bits(x[i]);
-    hi[i] = h;
-    lo[i] = __float_as_uint(__fsub_rn(x[i], __uint_as_float(h)));
+  for (int j = 0; j < 16; j++) {
+    float2 hi, lo;
+    split_pair(v[j], hi, lo);
+    h[2 * j] = __float_as_uint(hi.x);
+    h[2 * j + 1] = __float_as_uint(hi.y);
+    l[2 * j] = __float_as_uint(lo.x);
+    l[2 * j + 1] = __float_as_uint(lo.y);
   }
+  tmem_st32(a, h);
+  tmem_st32(a + 32, l);
+}
+
+// Read D_left, D_right of this thread's lane (columns 64.. of the group) and
+// return their sum (round to nearest) as 16 amplitudes.
+__device__ __forceinline__ void load_row_sum(uint32_t a, float2 (&v)[16]) {
+  uint32_t dl[32], dr[32];
+  tmem_ld32(a + 64, dl);
+  tmem_ld32(a + 96, dr);
+  tmem_wait_ld();
+#pragma unroll
+  for (int j = 0; j < 16; j++)
+    v[j] = __fadd2_rn(make_float2(__uint_as_float(dl[2 * j]), __uint_as_float(dl[2 * j + 1])),
+                      make_float2(__uint_as_float(dr[2 * j]), __uint_as_float(dr[2 * j + 1])));
 }
 
 }  // namespace svgb
