@@ -453,7 +453,11 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 4 : 2) : (NTMA
           const uint4 t4 = q[j];
           xo[4 * j] = t4.x; xo[4 * j + 1] = t4.y; xo[4 * j + 2] = t4.z; xo[4 * j + 3] = t4.w;
         }
-        __syncthreads();  // previous readers of buf_x are done
+        // A thread writes its amplitudes back to exactly the positions it read
+        // them from at stage s - 1, which no other thread reads, so only the first
+        // exchange after a stage-0 read of the natural-order tile from this same
+        // buffer (32-amplitude passes) must wait for every thread's reads.
+        if (kShared && s == 1) __syncthreads();
 #pragma unroll
         for (int j = 0; j < NR; j++) sts64(sx + (xo[j] ^ PBp), v[j]);
         q = reinterpret_cast<const uint4 *>(st.xo);
