@@ -12,13 +12,17 @@
 //
 // The array's name in host code is a host-side stand-in, not a device
 // address, so host code never passes `g_static_scratch` itself to a kernel:
-// the entry point looks up the device address once per device with
-// cudaGetSymbolAddress (with that device current) and passes that pointer.
+// every call looks up the array's device address on the current device with
+// cudaGetSymbolAddress (which allocates nothing) and passes that pointer.  The
+// lookup is not cached, so the address stays right if the device's context is
+// torn down and rebuilt (cudaDeviceReset) and the module is loaded again
+// elsewhere.
+#include <cmath>
 #include <cstdint>
-#include <mutex>
 
 #include "../../include/sv.h"
 #include "sv_internal.h"
+#include <math_constants.h>
 
 namespace svgb {
 
@@ -27,29 +31,25 @@ namespace svgb {
 constexpr int kStaticMaxQubits = 28;
 constexpr size_t kStaticParts = size_t(1) << (kStaticMaxQubits - 12);
 constexpr size_t kStaticDoubles = 2 * kStaticParts + 2;
+static_assert(kStaticParts >= reduce_parts_c(kStaticMaxQubits),
+              "the fixed scratch must hold one partial pair per reduction CTA at the largest size");
 
 static __device__ __align__(256) double g_static_scratch[kStaticDoubles];
 
-// out[0] = <Z_mask> = sum p (-1)^parity / sum p, out[1] = sum p.
+// out[0] = <Z_mask> = sum p (-1)^parity / sum p, out[1] = sum p.  A state whose
+// norm is zero or not finite gives out[0] = NaN (sv_expect_pauli reports the
+// same case as SV_ERR_ARG; this call cannot, as it does not synchronise).
 __global__ void k_finish_expect(const double *__restrict__ sums, double *__restrict__ out) {
   const double p = sums[0], pz = sums[1];
-  out[0] = p > 0.0 ? pz / p : 0.0;
+  out[0] = (p > 0.0 && isfinite(p)) ? pz / p : CUDART_NAN;
   out[1] = p;
 }
 
-static double *g_scratch_dev[64] = {nullptr};
-static std::mutex g_scratch_mu;
-
-static cudaError_t static_scratch(int dev, double **out) {
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_dev[dev]) {
-    void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_dev[dev] = static_cast<double *>(p);
-  }
-  *out = g_scratch_dev[dev];
-  return cudaSuccess;
+static cudaError_t static_scratch(double **out) {
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  *out = static_cast<double *>(p);
+  return e;
 }
 
 }  // namespace svgb
@@ -65,11 +65,8 @@ extern "C" int sv_expect_z_static(const void *amplitudes, int n_qubits, uint64_t
   if (z_mask >> n_qubits) return set_last_error(SV_ERR_ARG, "z_mask has bits beyond n_qubits");
   if (reinterpret_cast<uintptr_t>(amplitudes) % 16)
     return set_last_error(SV_ERR_ARG, "amplitudes must be 16-byte aligned");
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess && (dev < 0 || dev >= 64)) e = cudaErrorInvalidDevice;
   double *scratch = nullptr;
-  if (e == cudaSuccess) e = static_scratch(dev, &scratch);
+  cudaError_t e = static_scratch(&scratch);
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   if (e == cudaSuccess)
     e = launch_reduce_pz(static_cast<const float2 *>(amplitudes), n_qubits, z_mask, scratch, kStaticParts,
