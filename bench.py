@@ -3,16 +3,17 @@
 
 One step = the whole path on the 28-qubit workload: reset to |0..0>, apply a
 random layered circuit (n=28, depth 40, 1680 gates: fusion, pass planning and
-the pass kernels), FP64 CDF + 1e5 shots from pre-drawn uniforms, FP64 norm, a
-Z-string expectation, then reset to a seeded basis state and apply the 28-qubit
-QFT.  The complex64 state is 2 GiB, larger than the 129 MB L2, so every pass
+the pass kernels), FP64 CDF + 1e5 shots from pre-drawn uniforms with the FP64
+norm and a Z-string expectation taken from the same read of the state, then
+reset to a seeded basis state and apply the 28-qubit QFT.  The complex64 state is 2 GiB, larger than the 129 MB L2, so every pass
 streams from HBM.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line.  ``value`` is algorithmic HBM GB/s over the step (bytes
-the path must move: 16 B per amplitude per pass, 8 B per amplitude per reset,
-norm, CDF and expectation read) divided by device time.  ``roofline`` refers
+the path must move: 16 B per amplitude per pass, 8 B per amplitude per reset
+and for the one readout read that builds the CDF and the norm and expectation
+sums) divided by device time.  ``roofline`` refers
 to the pass kernel, timed per launch with CUDA events on the state's stream.
 ``--impl reference`` times the complex128 CPU oracle on a bounded sample of the
 same workload (rank 0 only).
@@ -139,7 +140,7 @@ def job_value(bytes_per_step: float, steps: int, world: int, seconds: float) -> 
 
 def step_bytes(plan_rand, plan_qft, n):
     amps = float(1 << n)
-    return plan_rand["bytes"] + plan_qft["bytes"] + 5 * 8.0 * amps  # 2 resets + cdf + norm + expect
+    return plan_rand["bytes"] + plan_qft["bytes"] + 3 * 8.0 * amps  # 2 resets + one readout read
 
 
 def run_ours(args, rank, world, local_rank):
@@ -169,12 +170,14 @@ def run_ours(args, rank, world, local_rank):
     L = capi._L
     import ctypes
 
+    ex, n2 = ctypes.c_double(), ctypes.c_double()
+
     def step_device():
         capi.sv_reset(h, 0)
         capi.sv_apply_circuit(h, ir_r, len(circ), opts)
-        capi._check(L.sv_sample_uniforms(h, u_dev.data_ptr(), SHOTS, out_dev.data_ptr(), None, 1))
-        capi.sv_norm(h)
-        capi.sv_expect_pauli(h, 0, ZMASK)
+        # draws, <Z_mask> and the norm from one read of the state
+        capi._check(L.sv_sample_expect_z(h, u_dev.data_ptr(), SHOTS, out_dev.data_ptr(), None, 1, ZMASK,
+                                         ctypes.byref(ex), ctypes.byref(n2)))
         capi.sv_reset(h, x)
         capi.sv_apply_circuit(h, ir_q, len(qft), opts)
 
@@ -185,10 +188,8 @@ def run_ours(args, rank, world, local_rank):
     def step_e2e():
         capi.sv_reset(h, 0)
         capi.sv_apply_circuit(h, ir_r, len(circ), opts)
-        capi._check(L.sv_sample_uniforms(h, u_pin.data_ptr(), SHOTS, out_host.ctypes.data,
-                                         ctypes.byref(nb), 0))
-        capi.sv_norm(h)
-        capi.sv_expect_pauli(h, 0, ZMASK)
+        capi._check(L.sv_sample_expect_z(h, u_pin.data_ptr(), SHOTS, out_host.ctypes.data, ctypes.byref(nb), 0,
+                                         ZMASK, ctypes.byref(ex), ctypes.byref(n2)))
         capi.sv_reset(h, x)
         capi.sv_apply_circuit(h, ir_q, len(qft), opts)
         capi.sv_synchronize(h)
@@ -269,7 +270,7 @@ def run_ours(args, rank, world, local_rank):
     value = job_value(bytes_step, args.steps, world, dev_ms * 1e-3)
     e2e_val = job_value(bytes_step, args.steps, world, e2e_s)
     h2d = plan_r["upload_bytes"] + plan_q["upload_bytes"] + SHOTS * 8
-    d2h = SHOTS * 8 + 8 + 3 * 8
+    d2h = SHOTS * 8 + 8 + 2 * 8
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 3),
@@ -634,7 +635,7 @@ def run_serve_mode(args):
     # highest-rate point again with shortest-predicted-first admission
     from paper_2512_04216_gb300 import costmodel
     t0 = time.perf_counter()
-    model = costmodel.calibrate(ns=tuple(range(8, 31, 2)), reps=1)
+    model = costmodel.calibrate(W.calibration_circuits, ns=tuple(range(8, 31, 2)), reps=1)
     cal_s = time.perf_counter() - t0
     import torch
     from paper_2512_04216_gb300 import StateVector, capi

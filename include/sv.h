@@ -195,6 +195,21 @@ int sv_sample_uniforms(sv_state *s, const double *uniforms, uint64_t shots,
                        uint64_t *out_bitstrings, uint64_t *out_n_boundary, int on_device);
 
 /*
+ * End-of-circuit readout from one read of the state (§III-B: all shots drawn
+ * from the final state, expectation values from the same cached state): the
+ * FP64 CDF built for sampling also accumulates, per 4096-amplitude block,
+ * sum_i |a_i|^2 (-1)^popcount(i & z_mask).  Draws are exactly those of
+ * sv_sample_uniforms with the same uniforms (shots may be 0: readout only);
+ * *out_expect = <Z_mask> = that sum / sum_i |a_i|^2 and *out_norm2 =
+ * sum_i |a_i|^2 (the CDF total; equal to sv_norm's value up to the order of the
+ * double-precision additions).  z_mask bits must be < n_qubits (0 gives 1).
+ * Synchronises.  SV_ERR_ARG for a zero-norm state or null outputs.
+ */
+int sv_sample_expect_z(sv_state *s, const double *uniforms, uint64_t shots, uint64_t *out_bitstrings,
+                       uint64_t *out_n_boundary, int on_device, uint64_t z_mask, double *out_expect,
+                       double *out_norm2);
+
+/*
  * Alias sampling (§III-C: shots drawn by alias sampling at O(1) work per shot;
  * Walker 1974).  sv_alias_build snapshots the current state's outcome
  * distribution into a Walker alias table held by the state (8 bytes per basis
@@ -297,9 +312,11 @@ int sv_take_qubit(sv_state *s, int qubit, double tol, int *value, sv_state **out
  * Limit: n_qubits <= 28 -- the scratch is a fixed 1 MiB array compiled into the
  * library, which every GPU that loads it holds until the process exits; larger
  * states return SV_ERR_ARG.  No cudaMalloc, cudaFree or other allocating call
- * is made.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls on a device share the one array,
+ * is made.  Every call looks up the array's device address on the current
+ * device (cudaGetSymbolAddress, which allocates nothing); the first call on a
+ * device may load the library's device code there, so make it before any
+ * stream capture.  A state whose norm is zero or not finite gives out[0] = NaN
+ * (sv_expect_pauli returns SV_ERR_ARG for it).  All calls on a device share the one array,
  * which keeps the last call's contents; every slot a call reads is written
  * earlier in that same call, so nothing needs clearing, but calls whose work
  * overlaps on the GPU (e.g. queued on different streams) race -- serialise them.

@@ -109,6 +109,7 @@ _SIGS = {
     "sv_take_qubit": ([_P, _i, ctypes.c_double, ctypes.POINTER(_i), ctypes.POINTER(_P)], _i),
     "sv_diag_bounded_wait": ([_i], _i),
     "sv_expect_z_static": ([_P, _i, _u64, _P, _P], _i),
+    "sv_sample_expect_z": ([_P, _P, _u64, _P, _P, _i, _u64, _P, _P], _i),
     "sv_batch_create": ([ctypes.c_size_t, _P, _P, _P, _P, _P, _P, _P, _i, _P, ctypes.POINTER(_P)], _i),
     "sv_batch_expectation": ([_P, ctypes.c_size_t, _P], _i),
     "sv_batch_launch": ([_P], _i),
@@ -284,6 +285,17 @@ def sv_sample_uniforms(h, uniforms, shots: int, out, on_device: bool) -> int:
     _check(_L.sv_sample_uniforms(h, _ptr(uniforms), int(shots), _ptr(out), ctypes.byref(nb),
                                  int(bool(on_device))))
     return int(nb.value)
+
+
+def sv_sample_expect_z(h, uniforms, shots: int, out, on_device: bool, z_mask: int):
+    """Draws (as sv_sample_uniforms), <Z_mask> and ||psi||^2 from one read of the
+    state; returns (n_boundary, expectation, norm2)."""
+    nb = ctypes.c_uint64(0)
+    e = ctypes.c_double(0.0)
+    n2 = ctypes.c_double(0.0)
+    _check(_L.sv_sample_expect_z(h, _ptr(uniforms), int(shots), _ptr(out), ctypes.byref(nb),
+                                 int(bool(on_device)), int(z_mask), ctypes.byref(e), ctypes.byref(n2)))
+    return int(nb.value), float(e.value), float(n2.value)
 
 
 def sv_alias_build(h):

@@ -676,20 +676,37 @@ int sv_set_amplitudes(sv_state *s, const void *in, uint64_t offset, uint64_t cou
   return SV_OK;
 }
 
+// With obs (non-null), the CDF build also forms sum p (-1)^popcount(i & zmask)
+// from the same read: obs[0] = <Z_mask>, obs[1] = ||psi||^2 (the CDF total).
 static int sample_impl(sv_state *s, const double *u, uint64_t seed, int use_seed, uint64_t shots,
-                       uint64_t *out, uint64_t *out_nb, int on_device) {
+                       uint64_t *out, uint64_t *out_nb, int on_device, uint64_t zmask = 0,
+                       double *obs = nullptr) {
   CHECK_STATE(s);
-  if (shots == 0) {
+  if (shots == 0 && !obs) {
     if (out_nb) *out_nb = 0;
     return SV_OK;
   }
-  if (!out) return fail(SV_ERR_ARG, "out is null");
-  if (!use_seed && !u) return fail(SV_ERR_ARG, "uniforms is null");
+  if (shots && !out) return fail(SV_ERR_ARG, "out is null");
+  if (shots && !use_seed && !u) return fail(SV_ERR_ARG, "uniforms is null");
+  if (obs && (zmask >> s->n)) return fail(SV_ERR_ARG, "z_mask has bits beyond n_qubits");
   DeviceGuard g(s->device);
   int rc = ensure_cdf(s);
   if (rc) return rc;
   const double nbytes = double(size_t(8) << s->n);
-  CK(s, timed(s, "cdf", nbytes, [&] { return launch_build_cdf(s->amp, s->n, s->ms, s->dscal + 2, s->stream); }));
+  CK(s, timed(s, "cdf", nbytes, [&] {
+       return launch_build_cdf(s->amp, s->n, s->ms, s->dscal + 2, s->stream, zmask, obs ? s->dscal + 3 : nullptr);
+     }));
+  if (shots == 0) {  // readout of <Z_mask> and the norm only
+    CK(s, cudaMemcpyAsync(s->hscal + 2, s->dscal + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    rc = check_device_error(s);
+    if (rc) return rc;
+    if (!(s->hscal[2] > 0.0)) return fail(SV_ERR_ARG, "state has zero norm");
+    obs[0] = s->hscal[3] / s->hscal[2];
+    obs[1] = s->hscal[2];
+    if (out_nb) *out_nb = 0;
+    return SV_OK;
+  }
   const double *u_dev = u;
   uint64_t *out_dev = out;
   if (!on_device) {
@@ -710,13 +727,21 @@ static int sample_impl(sv_state *s, const double *u, uint64_t seed, int use_seed
      }));
   if (!on_device)
     CK(s, cudaMemcpyAsync(out, out_dev, shots * sizeof(uint64_t), cudaMemcpyDeviceToHost, s->stream));
-  if (out_nb || !on_device) {
+  if (out_nb || !on_device || obs) {
     CK(s, cudaMemcpyAsync(s->hscal, s->dcount, sizeof(uint64_t), cudaMemcpyDeviceToHost, s->stream));
+    if (obs) CK(s, cudaMemcpyAsync(s->hscal + 2, s->dscal + 2, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     CK(s, cudaStreamSynchronize(s->stream));
     uint64_t nb;
     std::memcpy(&nb, s->hscal, sizeof(nb));
     if (out_nb) *out_nb = nb;
-    return check_device_error(s);
+    rc = check_device_error(s);
+    if (rc) return rc;
+    if (obs) {
+      if (!(s->hscal[2] > 0.0)) return fail(SV_ERR_ARG, "state has zero norm");
+      obs[0] = s->hscal[3] / s->hscal[2];
+      obs[1] = s->hscal[2];
+    }
+    return SV_OK;
   }
   return SV_OK;
 }
@@ -728,6 +753,19 @@ int sv_sample(sv_state *s, uint64_t shots, uint64_t seed, uint64_t *out_bitstrin
 int sv_sample_uniforms(sv_state *s, const double *uniforms, uint64_t shots, uint64_t *out_bitstrings,
                        uint64_t *out_n_boundary, int on_device) {
   return sample_impl(s, uniforms, 0, 0, shots, out_bitstrings, out_n_boundary, on_device);
+}
+
+int sv_sample_expect_z(sv_state *s, const double *uniforms, uint64_t shots, uint64_t *out_bitstrings,
+                       uint64_t *out_n_boundary, int on_device, uint64_t z_mask, double *out_expect,
+                       double *out_norm2) {
+  if (!out_expect || !out_norm2) return fail(SV_ERR_ARG, "out_expect and out_norm2 are required");
+  double obs[2] = {0.0, 0.0};
+  const int rc = sample_impl(s, uniforms, 0, 0, shots, out_bitstrings, out_n_boundary, on_device, z_mask, obs);
+  if (rc == SV_OK) {
+    *out_expect = obs[0];
+    *out_norm2 = obs[1];
+  }
+  return rc;
 }
 
 int sv_alias_release(sv_state *s) {

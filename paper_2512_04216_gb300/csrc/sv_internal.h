@@ -176,8 +176,10 @@ constexpr int kBlockBits = 12;  // 4096 amplitudes = 64 chunks
 
 cudaError_t launch_reduce_pz(const float2 *amp, int n, uint64_t zmask, double *part,
                              size_t n_part, double *out2, cudaStream_t st);
+// Builds the CDF; with ztotal_dev, the same read also writes
+// sum p_i * (-1)^popcount(i & zmask) to ztotal_dev[0].
 cudaError_t launch_build_cdf(const float2 *amp, int n, MeasureScratch &ms, double *total_dev,
-                             cudaStream_t st);
+                             cudaStream_t st, uint64_t zmask = 0, double *ztotal_dev = nullptr);
 cudaError_t launch_sample(const float2 *amp, int n, const MeasureScratch &ms,
                           const double *total_dev, const double *u, uint64_t seed, int use_seed,
                           uint64_t shots, uint64_t *out, uint64_t *n_boundary, cudaStream_t st);
@@ -193,6 +195,9 @@ cudaError_t launch_collapse(float2 *amp, int n, int q, int outcome, int to_zero,
                             cudaStream_t st);
 
 size_t reduce_parts(int n);
+// Amplitudes per reduction CTA (k_reduce_pz): reduce_parts(n) = ceil(2^n / kReduceCtaAmps).
+constexpr uint64_t kReduceCtaAmps = 4096;
+constexpr uint64_t reduce_parts_c(int n) { return ((uint64_t(1) << n) + kReduceCtaAmps - 1) / kReduceCtaAmps; }
 
 // Walker alias table (sv_alias.cu).  Entry i of the table packs
 // (own_i << 32) | alias_i: bucket i keeps own_i of its 2^31 units for outcome

@@ -27,6 +27,7 @@ __host__ __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { re
 constexpr int kRT = 256;                     // threads per reduction CTA
 constexpr int kPerThread = 16;               // amplitudes per thread
 constexpr int kCtaAmps = kRT * kPerThread;   // 4096 = one sampler block
+static_assert(uint64_t(kCtaAmps) == kReduceCtaAmps, "reduce_parts_c must match the reduction kernel");
 
 // ---- compensated float32 accumulation -----------------------------------
 // __fadd_rn/__fmul_rn are never contracted into FMAs, which would break the
@@ -154,6 +155,10 @@ __global__ void __launch_bounds__(kRT) k_reduce_pz(const float2 *__restrict__ am
       acc_pair(zs, zc, n1 ? -s1 : s1, n1 ? -c1 : c1);
     }
   }
+  if (!zmask) {  // Z_0 is the identity: every sign is +1
+    zs = ps;
+    zc = pc;
+  }
   warp_acc_pair(ps, pc);
   warp_acc_pair(zs, zc);
   const int w = threadIdx.x >> 5;
@@ -219,18 +224,30 @@ cudaError_t launch_reduce_pz(const float2 *amp, int n, uint64_t zmask, double *p
 }
 
 // ---- CDF --------------------------------------------------------------------
-// Chunk sums (64 amplitudes; four threads each) and 4096-amplitude block sums.
+// Chunk sums (64 amplitudes; four threads each) and 4096-amplitude block sums;
+// with zblock, also the block's sum of p * (-1)^popcount(i & zmask), from the
+// same read of the amplitudes.
 __global__ void __launch_bounds__(kRT) k_chunk_block(const float2 *__restrict__ amp, int n,
                                                      double *__restrict__ chunk,
-                                                     double *__restrict__ blocksum) {
+                                                     double *__restrict__ blocksum, uint64_t zmask,
+                                                     double *__restrict__ zblock) {
   __shared__ __align__(16) float2 tile[kCtaAmps];
   __shared__ double cs[kCtaAmps / 64];
+  __shared__ double zred[kRT / 32];
   const uint64_t N = uint64_t(1) << n;
   const uint64_t start = uint64_t(blockIdx.x) * kCtaAmps;
   const uint32_t cnt = uint32_t(umin64(kCtaAmps, N - start));
   stage_load(tile, amp, start, cnt);
   float ps, pc, zs, zc;
-  thread_sums(tile, cnt, start, 0, ps, pc, zs, zc);
+  thread_sums(tile, cnt, start, zblock ? zmask : 0, ps, pc, zs, zc);
+  if (zblock) {
+    if (!zmask) {  // Z_0 is the identity: every sign is +1
+      zs = ps;
+      zc = pc;
+    }
+    warp_acc_pair(zs, zc);
+    if ((threadIdx.x & 31) == 0) zred[threadIdx.x >> 5] = cs_to_double(zs, zc);
+  }
   // four consecutive threads hold one 64-amplitude chunk
 #pragma unroll
   for (int o = 1; o < 4; o <<= 1) {
@@ -253,7 +270,31 @@ __global__ void __launch_bounds__(kRT) k_chunk_block(const float2 *__restrict__ 
     for (uint32_t c = threadIdx.x; c < nch; c += 32) v += cs[c];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) blocksum[blockIdx.x] = v;
+    if (threadIdx.x == 0) {
+      blocksum[blockIdx.x] = v;
+      if (zblock) {
+        double z = 0.0;
+        for (int w = 0; w < kRT / 32; w++) z += zred[w];
+        zblock[blockIdx.x] = z;
+      }
+    }
+  }
+}
+
+// out[0] = sum of x[0 .. count) in a fixed order (one CTA).
+__global__ void __launch_bounds__(1024) k_sum_doubles(const double *__restrict__ x, size_t count,
+                                                      double *__restrict__ out) {
+  __shared__ double red[32];
+  double a = 0.0;
+  for (size_t i = threadIdx.x; i < count; i += blockDim.x) a += x[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < int(blockDim.x >> 5); i++) t += red[i];
+    out[0] = t;
   }
 }
 
@@ -344,17 +385,28 @@ __global__ void k_copy_last(const double *__restrict__ x, size_t count, double *
 }
 
 cudaError_t launch_build_cdf(const float2 *amp, int n, MeasureScratch &ms, double *total_dev,
-                             cudaStream_t st) {
+                             cudaStream_t st, uint64_t zmask, double *ztotal_dev) {
   const uint64_t N = uint64_t(1) << n;
   const size_t nblk = size_t((N + kCtaAmps - 1) / kCtaAmps);
   const size_t nseg = (nblk + kScanSeg - 1) / kScanSeg;
   if (nblk > ms.n_block || nseg > ms.n_part) return cudaErrorInvalidValue;
-  k_chunk_block<<<unsigned(nblk), kRT, 0, st>>>(amp, n, ms.chunk, ms.block);
+  // per-block Z sums: the second half of the reduction scratch (2 * n_part
+  // doubles; the scan uses the first nseg <= nblk)
+  double *zblock = nullptr;
+  if (ztotal_dev) {
+    if (nblk > ms.n_part) return cudaErrorInvalidValue;
+    zblock = ms.part + ms.n_part;
+  }
+  k_chunk_block<<<unsigned(nblk), kRT, 0, st>>>(amp, n, ms.chunk, ms.block, zmask, zblock);
   k_scan_reduce<<<unsigned(nseg), kScanT, 0, st>>>(ms.block, nblk, ms.part);
   k_scan_top<<<1, kScanT, 0, st>>>(ms.part, nseg);
   k_scan_apply<<<unsigned(nseg), kScanT, 0, st>>>(ms.block, nblk, ms.part);
   k_copy_last<<<1, 1, 0, st>>>(ms.block, nblk, total_dev);
   count_launch(5);
+  if (zblock) {
+    k_sum_doubles<<<1, 1024, 0, st>>>(zblock, nblk, ztotal_dev);
+    count_launch();
+  }
   return cudaGetLastError();
 }
 

@@ -81,6 +81,14 @@ class StateVector:
         nb = capi.sv_sample_uniforms(self.h, u, u.shape[0], out, on_device)
         return out, nb
 
+    def sample_expect_z(self, uniforms, z_mask: int):
+        """Draws for the uniforms, <Z_mask> and ||psi||^2 from one read of the state:
+        (bitstrings, n_boundary, expectation, norm2)."""
+        u = np.ascontiguousarray(uniforms, dtype=np.float64)
+        out = np.empty(u.shape[0], dtype=np.uint64)
+        nb, e, n2 = capi.sv_sample_expect_z(self.h, u, u.shape[0], out, False, z_mask)
+        return out, nb, e, n2
+
     def alias_build(self):
         """Snapshot the outcome distribution into a Walker alias table (synchronises)."""
         capi.sv_alias_build(self.h)

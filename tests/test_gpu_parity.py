@@ -281,3 +281,25 @@ def test_large_mirror_and_qft_28(sv):
     want = np.exp(2j * np.pi * ((x * y) % (1 << n)) / (1 << n)) / math.sqrt(1 << n)
     assert np.max(np.abs(amps[idx] - want)) < 1e-6
     s.close()
+
+
+@pytest.mark.parametrize("n", [3, 12, 17, 24])
+def test_fused_readout_matches_separate_calls_and_oracle(sv, n):
+    # sv_sample_expect_z: the draws of sv_sample_uniforms, and <Z_mask> and the
+    # norm from the same read of the state, against the oracle's double sums.
+    c = W.random_layered(n, 8, 40 + n)
+    s, g = _run_gpu(sv, n, c)
+    u = W.shot_uniforms(50 + n, 4096)
+    x1, nb1 = s.sample_uniforms(u)
+    for mask in (0, 1, (1 << n) - 1, 0b1011 & ((1 << n) - 1)):
+        x2, nb2, e, n2 = s.sample_expect_z(u, mask)
+        assert np.array_equal(x1, x2) and nb1 == nb2
+        assert abs(e - oracle.expect_z(g, mask)) < 1e-12, (n, mask)
+        assert abs(n2 - oracle.norm2(g)) < 1e-12
+        assert abs(n2 - s.norm2()) < 1e-12
+    assert abs(s.expect_z(0) - 1.0) < 1e-12  # Z_0 is the identity
+    _, nb0, e0, n0 = s.sample_expect_z(np.empty(0), 0b11 & ((1 << n) - 1))  # readout only
+    assert nb0 == 0 and abs(e0 - oracle.expect_z(g, 0b11 & ((1 << n) - 1))) < 1e-12
+    with pytest.raises(sv.capi.SvError):
+        s.sample_expect_z(u, 1 << n)
+    s.close()
