@@ -154,23 +154,23 @@ class CostModel:
         return CostModel(**json.loads(s))
 
 
-def calibrate(ns=(10, 12, 14, 16, 18, 20, 22, 24, 26, 28), reps: int = 2, opts=None, seed: int = 7) -> CostModel:
+def calibrate(circuits_for, ns=(10, 12, 14, 16, 18, 20, 22, 24, 26, 28), reps: int = 2, opts=None) -> CostModel:
     """Measures the coefficients on the current device (a one-time routine):
     one joint least-squares fit of T = c_fix + c_gate * dense gates + C_pass(n)
-    * passes + c_flop * effective flops over synthetic circuits at every n in
-    `ns` (each timed warm: best of reps + 1 runs on one state)."""
+    * passes + c_flop * effective flops over the caller's calibration circuits at
+    every n in `ns` (each timed warm: best of reps + 1 runs on one state).
+    `circuits_for(n)` returns the gate lists to time at n qubits; a mix of
+    shallow and deep circuits, with and without diagonal gates, makes the fit
+    well conditioned."""
     import torch
 
-    import workloads as W
     from . import capi
     from .statevector import StateVector
 
     model = CostModel(ns=[int(n) for n in ns])
     rows, times, shot_samples = [], [], []
     for i, n in enumerate(ns):
-        circuits = [W.random_layered(n, 8, seed + n), W.random_layered(n, 2, seed + 2 * n),
-                    W.random_layered(n, 24, seed + 3 * n), W.random_layered(n, 60, seed + 4 * n),
-                    W.qft(n), W.ghz(n), W.ghz(n)[:1]]
+        circuits = list(circuits_for(n))
         s = StateVector(n)
         for c in circuits:
             st = capi.sv_plan_stats(n, c, opts)

@@ -19,7 +19,7 @@ def P():
 def test_prediction_on_held_out_circuits(P):
     import torch
     from paper_2512_04216_gb300 import capi, costmodel
-    model = costmodel.calibrate(ns=(12, 15, 18, 21, 24), reps=1)
+    model = costmodel.calibrate(W.calibration_circuits, ns=(12, 15, 18, 21, 24), reps=1)
     errs = []
     for n, c in ((13, W.random_layered(13, 30, 1)), (17, W.random_layered(17, 25, 2)),
                  (20, W.qft(20)), (23, W.random_layered(23, 12, 3)), (22, W.random_gate_soup(22, 300, 4))):
@@ -42,7 +42,7 @@ def test_prediction_on_held_out_circuits(P):
 
 def test_server_with_cost_model(P):
     from paper_2512_04216_gb300 import costmodel, serve
-    model = costmodel.calibrate(ns=(8, 12, 16, 20), reps=1)
+    model = costmodel.calibrate(W.calibration_circuits, ns=(8, 12, 16, 20), reps=1)
     specs = W.serving_requests(20, 3, 500.0, n_lo=8, n_hi=18, mean_n=12.0, d_lo=4, d_hi=12, shots=200)
     reqs = serve.make_requests(specs, W.random_layered)
     a = serve.Server(small_max_qubits=10, streams=4, cost_model=model).run(reqs)

@@ -268,3 +268,11 @@ def serving_requests(count: int, seed: int, rate_hz: float, n_lo: int = 8, n_hi:
             req["zmask"] = m
         reqs.append(req)
     return reqs
+
+
+def calibration_circuits(n: int, seed: int = 7):
+    """Circuits the runtime model is calibrated on at n qubits: random layered
+    circuits of depth 2, 8, 24 and 60, the QFT, GHZ and a single gate."""
+    return [random_layered(n, 8, seed + n), random_layered(n, 2, seed + 2 * n),
+            random_layered(n, 24, seed + 3 * n), random_layered(n, 60, seed + 4 * n),
+            qft(n), ghz(n), ghz(n)[:1]]
