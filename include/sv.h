@@ -131,7 +131,8 @@ int sv_wrap(void *dev_ptr, int n_qubits, int dtype, void *cuda_stream, sv_state 
  * for the state's stream.  NULL is accepted. */
 int sv_destroy(sv_state *s);
 
-/* Change the stream later work is queued on. */
+/* Change the stream later work is queued on; that stream first waits for the
+ * work already queued on the old one. */
 int sv_set_stream(sv_state *s, void *cuda_stream);
 
 /* Wait for all queued work on the state's stream. */
@@ -268,8 +269,9 @@ int sv_expect_pauli(sv_state *s, uint64_t x_mask, uint64_t z_mask, double *out);
  *
  * sv_clone creates a new library-owned state (its own 2^n * 8-byte buffer, on
  * `cuda_stream`) holding a copy of src as of all work queued on src's stream;
- * the copy is queued on the new state's stream.  SV_ERR_OOM when the buffer
- * cannot be allocated.
+ * the copy is queued on the new state's stream, and work queued on src's stream
+ * afterwards (including sv_destroy(src)) waits for it.  SV_ERR_OOM when the
+ * buffer cannot be allocated.
  */
 int sv_measure_qubit(sv_state *s, int qubit, double u, int *outcome, double *prob);
 int sv_reset_qubit(sv_state *s, int qubit, double u, int *outcome);
@@ -282,7 +284,8 @@ int sv_clone(sv_state *src, void *cuda_stream, sv_state **out);
  * sv_merge creates a new (n_a + n_b)-qubit state a (x) b: a's qubits become
  * qubits 0..n_a-1 and b's become n_a..n_a+n_b-1, out[i_b * 2^n_a + i_a] =
  * b[i_b] * a[i_a].  Queued on `cuda_stream` after all work queued on a's and
- * b's streams; a and b are unchanged and stay valid.  SV_ERR_ARG past 36
+ * b's streams; work queued on a's or b's stream afterwards waits for it; a and
+ * b are unchanged and stay valid.  SV_ERR_ARG past 36
  * qubits or across devices, SV_ERR_OOM without room for the result.
  *
  * sv_take_qubit removes `qubit` from a register in which it is in a basis

@@ -337,14 +337,30 @@ int sv_wrap(void *dev_ptr, int n_qubits, int dtype, void *cuda_stream, sv_state 
   return SV_OK;
 }
 
+// dst waits for the work queued on src so far.
+static cudaError_t stream_after(cudaStream_t dst, cudaStream_t src) {
+  if (dst == src) return cudaSuccess;
+  cudaEvent_t ev = nullptr;
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev, src);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(dst, ev, 0);
+  if (ev) cudaEventDestroy(ev);
+  return e;
+}
+
 int sv_destroy(sv_state *s) {
   free_state(s);
   return SV_OK;
 }
 
 int sv_set_stream(sv_state *s, void *cuda_stream) {
-  if (!s) return fail(SV_ERR_ARG, "null state");
-  s->stream = static_cast<cudaStream_t>(cuda_stream);
+  CHECK_STATE(s);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  DeviceGuard g(s->device);
+  // work queued on the new stream follows the work already queued on the old one
+  // (scratch reallocations synchronise only the state's current stream)
+  CK(s, stream_after(st, s->stream));
+  s->stream = st;
   return SV_OK;
 }
 
@@ -542,15 +558,6 @@ int sv_reset_qubit(sv_state *s, int qubit, double u, int *outcome) {
 }
 
 // Orders `dst`'s stream after all work queued on `src`'s stream.
-static cudaError_t stream_after(cudaStream_t dst, cudaStream_t src) {
-  if (dst == src) return cudaSuccess;
-  cudaEvent_t ev = nullptr;
-  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventRecord(ev, src);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(dst, ev, 0);
-  if (ev) cudaEventDestroy(ev);
-  return e;
-}
 
 int sv_clone(sv_state *src, void *cuda_stream, sv_state **out) {
   CHECK_STATE(src);
@@ -562,6 +569,9 @@ int sv_clone(sv_state *src, void *cuda_stream, sv_state **out) {
   const size_t bytes = (size_t(1) << src->n) * sizeof(float2);
   cudaError_t e = stream_after(d->stream, src->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d->amp, src->amp, bytes, cudaMemcpyDeviceToDevice, d->stream);
+  // later work on the source (an apply that overwrites it, or its destroy) waits
+  // for the copy that reads it on the clone's stream
+  if (e == cudaSuccess) e = stream_after(src->stream, d->stream);
   if (e != cudaSuccess) {
     free_state(d);
     *out = nullptr;
@@ -585,6 +595,9 @@ int sv_merge(sv_state *a, sv_state *b, void *cuda_stream, sv_state **out) {
   if (e == cudaSuccess)
     e = timed(d, "merge", double(size_t(8) << d->n),
               [&] { return launch_kron(a->amp, a->n, b->amp, b->n, d->amp, d->stream); });
+  // later work on either source waits for the merge that reads it
+  if (e == cudaSuccess) e = stream_after(a->stream, d->stream);
+  if (e == cudaSuccess) e = stream_after(b->stream, d->stream);
   if (e != cudaSuccess) {
     free_state(d);
     *out = nullptr;
