@@ -45,6 +45,7 @@ SHOTS = 100_000
 ZMASK = 0b1011  # <Z_0 Z_1 Z_3>
 OPTS = dict(k_max=5, tile_qubits=12, low_qubits=5, precision=0, kernel_variant=0)
 METRIC = "state-vector apply HBM GB/s vs peak"
+SERVE_SMALL_MAX = 14  # requests up to this many qubits go to the batched kernel
 # FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -611,26 +612,53 @@ def run_alias_mode(args):
     }
 
 
-def run_serve_mode(args):
-    """Config: Poisson stream of random layered circuits, n geometric-skewed on
-    8..30 (mean ~16), depth ~ U{10..100}, 1000 shots or a Z-string mask; served
-    by the continuous-batching loop and by the plain path."""
+LARGE_QUBITS = 25  # requests from here on bound both serving paths by their device time
+
+
+def serving_sweep(count: int, factors, small_max: int) -> dict:
+    """Poisson stream of random layered circuits (n geometric-skewed on 8..30,
+    mean ~16; depth ~ U{10..100}; 1000 shots or a Z-string mask), served by the
+    continuous-batching loop and by the plain one-circuit-at-a-time path at
+    rates `factors` x the plain path's capacity.  Also the Amdahl ceiling of the
+    served/plain circuits/s ratio: the plain makespan of the whole stream over
+    the plain time of its >= 25-qubit requests, whose device work (the same pass
+    kernels on both paths, each saturating the GPU) no scheduling removes."""
     from paper_2512_04216_gb300 import serve
-    count = args.requests
     specs0 = W.serving_requests(count, 4, 1.0)
     reqs0 = serve.make_requests(specs0, W.random_layered)
     for r in reqs0:
         r.t = 0.0
-    plain_cap = serve.summarize(serve.run_plain(reqs0))["circuits_per_s"]
-    out = {"plain_capacity_circuits_per_s": plain_cap, "points": []}
-    for f in [float(x) for x in args.rate_factors.split(",")]:
-        rate = f * plain_cap
+    res0 = serve.run_plain(reqs0)
+    cap = serve.summarize(res0)
+    n_of = {r.id: r.n for r in reqs0}
+    large_s = sum(r.t_done - r.t_start for r in res0 if n_of[r.id] >= LARGE_QUBITS)
+    n_large = sum(1 for r in reqs0 if r.n >= LARGE_QUBITS)
+    out = {"requests_per_point": count, "small_max_qubits": small_max,
+           "plain_capacity_circuits_per_s": cap["circuits_per_s"],
+           "amdahl_ceiling": {"ratio": cap["makespan_s"] / large_s if large_s > 0 else None,
+                              "plain_makespan_s": cap["makespan_s"], "large_requests": n_large,
+                              "large_qubits_from": LARGE_QUBITS, "large_plain_s": large_s},
+           "points": []}
+    for f in factors:
+        rate = f * cap["circuits_per_s"]
         specs = W.serving_requests(count, 4, rate)
         reqs = serve.make_requests(specs, W.random_layered)
-        srv = serve.summarize(serve.Server().run(reqs))
+        res = serve.Server(small_max_qubits=small_max).run(reqs)
+        srv = serve.summarize(res)
+        srv["batched_requests"] = sum(1 for r in res if r.path == "batch")
         pl = serve.summarize(serve.run_plain(reqs))
         out["points"].append({"rate_factor": f, "rate_hz": rate, "served": srv, "plain": pl,
                               "circuits_per_s_ratio": srv["circuits_per_s"] / pl["circuits_per_s"]})
+    return out
+
+
+def run_serve_mode(args):
+    """Config: the serving stream (serving_sweep) at every --rate-factors point,
+    then the runtime model's held-out accuracy and shortest-predicted-first admission."""
+    from paper_2512_04216_gb300 import serve
+    count = args.requests
+    out = serving_sweep(count, [float(x) for x in args.rate_factors.split(",")], args.serve_small_max)
+    plain_cap = out["plain_capacity_circuits_per_s"]
     # runtime model (Eq. 1) calibrated on this GPU: held-out accuracy, and the
     # highest-rate point again with shortest-predicted-first admission
     from paper_2512_04216_gb300 import costmodel
@@ -660,7 +688,7 @@ def run_serve_mode(args):
     f = float(args.rate_factors.split(",")[-1])
     specs = W.serving_requests(count, 4, f * plain_cap)
     reqs = serve.make_requests(specs, W.random_layered)
-    spt = serve.summarize(serve.Server(cost_model=model).run(reqs))
+    spt = serve.summarize(serve.Server(small_max_qubits=args.serve_small_max, cost_model=model).run(reqs))
     out["cost_model"] = {"calibration_s": cal_s, "held_out_abs_rel_err": [round(e, 3) for e in errs],
                          "rate_factor": f, "served_shortest_predicted_first": spt}
     best = max(p["circuits_per_s_ratio"] for p in out["points"])
@@ -697,6 +725,10 @@ def main():
     ap.add_argument("--batch-circuits", type=int, default=4096)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate-factors", default="0.5,1,2,4")
+    ap.add_argument("--serve-small-max", type=int, default=SERVE_SMALL_MAX,
+                    help="largest request (qubits) the server sends to the batched kernel")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="leave the serving sweep out of the bench line (profiling runs)")
     args = ap.parse_args()
     N_QUBITS, DEPTH = args.n_qubits, args.depth
     if args.workload == "large":
@@ -725,6 +757,10 @@ def main():
         torch.cuda.set_device(local_rank)
         td.init_process_group("nccl")
     line = run_ours(args, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_serving:
+        # the metric's second half: mixed-stream circuits/s and p50/p99 against the
+        # plain path, bounded to 200 requests at 1x and 4x the plain capacity
+        line["serving"] = serving_sweep(200, (1.0, 4.0), args.serve_small_max)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_step, threads, desc = oracle_sample(gates_sample=12, measure=True)
         v = bytes_step_host() / t_step / 1e9
