@@ -268,6 +268,10 @@ def run_ours(args, rank, world, local_rank):
                  "hbm_GBps": round(achieved, 1), "hbm_frac": round(achieved / peak, 4),
                  "fp32_TFLOPs": round(achieved_tf, 2), "fp32_frac": round(achieved_tf / FP32_PEAK_TFLOPS, 4),
                  "avg_launch_ms": round(pk["ms"] / max(pk["launches"], 1), 4)})
+    config = config_dict(world)
+    # the default step's statistics are also stored for the reference arm; a
+    # non-default run (other size or options) reports its own plan
+    config["passes_per_step"] = plan_r["n_passes"] + plan_q["n_passes"]
     value = job_value(bytes_step, args.steps, world, dev_ms * 1e-3)
     e2e_val = job_value(bytes_step, args.steps, world, e2e_s)
     h2d = plan_r["upload_bytes"] + plan_q["upload_bytes"] + SHOTS * 8
@@ -277,12 +281,7 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dev_ms / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
         "data": "synthetic (seeded random layered circuit, QFT, SplitMix64 uniforms)",
-        "config": {"workload": workload_name(), "n_qubits": n, "depth": DEPTH, "gates": len(circ) + len(qft),
-                   "shots": SHOTS, "fusion_k_max": OPTS["k_max"], "tile_qubits": OPTS["tile_qubits"],
-                   "kernel_variant": OPTS.get("kernel_variant", 0), "precision": OPTS["precision"],
-                   "passes_per_step": plan_r["n_passes"] + plan_q["n_passes"],
-                   "l2": f"inputs larger than L2 ({(8 << n) / 2**30:.3g} GiB state vs 129 MB L2)",
-                   "parallelism": f"replicas{world}"},
+        "config": config,
         "roofline": roof,
         "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
                         "GB/s": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] > 0 and v["bytes"] else None,
@@ -304,58 +303,119 @@ def capi_get(capi, h, i):
     return complex(out[0])
 
 
-def oracle_sample(gates_sample: int, measure: bool = True):
-    """Times the oracle on a bounded sample of the step at full size: the first
-    `gates_sample` gates of the random circuit on 2^28 complex128 amplitudes,
-    then (optionally) its CDF + 1e5 draws, norm and expectation.  Returns
-    (extrapolated seconds per step, threads, description)."""
+# Plan statistics of the default step (n=28 depth-40 random circuit + QFT-28 with
+# OPTS): the reference arm reports them without loading the library;
+# tests/test_bench_host.py checks them against the planner.
+DEFAULT_PLAN = {"passes_per_step": 75, "bytes_step": 328564998144.0}
+
+
+def oracle_gate_time(threads: int):
+    """Seconds per gate of each kind in the step (U3 and CX of the random circuit;
+    H, CP and SWAP of the QFT), the oracle applying one gate of each kind in turn
+    to a 2^28 complex128 state with `threads` threads.  Returns
+    ({kind: seconds}, threads used)."""
     import oracle
     o = oracle.default()
-    o.set_threads(os.cpu_count() or 1)
-    threads = o.max_threads()
+    o.set_threads(threads)
+    used = o.max_threads()
     n = N_QUBITS
     circ = W.random_layered(n, DEPTH, SEED)
-    total_gates = len(circ) + len(W.qft(n))
-    t0 = time.perf_counter()
-    psi = o.run(n, circ[:gates_sample])
-    t_g = (time.perf_counter() - t0) / gates_sample
-    t_m = 0.0
-    if measure:
+    qft = W.qft(n)
+    pick = {}
+    for g in circ + qft:
+        pick.setdefault(g[0], g)
+    psi = oracle.basis(n)
+    psi = o.run(n, [pick["u3"]], psi)  # untimed: touches every page of the new state
+    times = {}
+    for kind, g in pick.items():
         t0 = time.perf_counter()
-        o.sample(psi, W.shot_uniforms(SEED, SHOTS))
-        o.norm2(psi)
-        o.expect_z(psi, ZMASK)
-        t_m = time.perf_counter() - t0
+        psi = o.run(n, [g], psi)
+        times[kind] = time.perf_counter() - t0
     del psi
-    desc = (f"oracle (complex128, {threads} threads) on the first {gates_sample} of {total_gates} gates "
-            f"at n={n}{' + CDF/1e5 shots/norm/<Z>' if measure else ''}; per-gate time x {total_gates} gates"
-            f"{' + measured measurement time' if measure else ''}")
-    return t_g * total_gates + t_m, threads, desc
+    return times, used
 
 
-def bytes_step_host():
-    from paper_2512_04216_gb300 import capi
+def oracle_step_time(threads: int, measure_psi=None):
+    """The oracle's time for one step, by gate kind: sum over kinds of (gates of
+    that kind in the step) x (its measured per-gate time), plus the measured
+    CDF + 1e5 draws, norm and <Z> on a 2^28 state (psi, or a fresh basis state).
+    Returns (seconds, threads used, description)."""
+    import oracle
+    from collections import Counter
     n = N_QUBITS
-    opts = capi.make_opts(**OPTS)
-    return step_bytes(capi.sv_plan_stats(n, W.random_layered(n, DEPTH, SEED), opts),
-                      capi.sv_plan_stats(n, W.qft(n), opts), n)
+    counts = Counter(g[0] for g in W.random_layered(n, DEPTH, SEED) + W.qft(n))
+    per_gate, used = oracle_gate_time(threads)
+    t_gates = sum(counts[k] * per_gate[k] for k in counts)
+    o = oracle.default()
+    o.set_threads(threads)
+    psi = oracle.basis(n, W.basis_index(n, SEED)) if measure_psi is None else measure_psi
+    t0 = time.perf_counter()
+    o.sample(psi, W.shot_uniforms(SEED, SHOTS))
+    o.norm2(psi)
+    o.expect_z(psi, ZMASK)
+    t_m = time.perf_counter() - t0
+    del psi
+    desc = (f"oracle (complex128, {used} thread{'s' if used > 1 else ''}) at n={n}: one gate of each kind "
+            f"({', '.join(f'{k} {per_gate[k]:.3f} s' for k in sorted(per_gate))}) times the step's "
+            f"{sum(counts.values())} gates by kind, + measured CDF/{SHOTS} draws/norm/<Z> ({t_m:.2f} s)")
+    return t_gates + t_m, used, desc
+
+
+def oracle_config1_s() -> float:
+    """The oracle on the small configuration in full (n=12 random layered depth 20,
+    CDF and 1024 draws), one thread."""
+    import oracle
+    o = oracle.default()
+    o.set_threads(1)
+    t0 = time.perf_counter()
+    psi = o.run(12, W.random_layered(12, 20, 1))
+    o.sample(psi, W.shot_uniforms(1, 1024))
+    return time.perf_counter() - t0
+
+
+def cpu_baseline() -> dict:
+    """The oracle as it stands on the host cores: all cores (the line's value)
+    and one thread, each extrapolated from a by-kind gate sample of the step, and
+    the small configuration timed in full."""
+    bstep = DEFAULT_PLAN["bytes_step"]
+    t_all, cores, desc = oracle_step_time(os.cpu_count() or 1)
+    t_one, _, desc1 = oracle_step_time(1)
+    return {"value": bstep / t_all / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": desc,
+            "ms_per_step": t_all * 1e3,
+            "single_thread": {"value": bstep / t_one / 1e9, "ms_per_step": t_one * 1e3, "sample": desc1},
+            "config1_full_one_thread_ms": oracle_config1_s() * 1e3}
+
+
+def config_dict(world: int) -> dict:
+    """The workload description both arms print (plan statistics from DEFAULT_PLAN)."""
+    n = N_QUBITS
+    return {"workload": workload_name(), "n_qubits": n, "depth": DEPTH,
+            "gates": len(W.random_layered(n, DEPTH, SEED)) + len(W.qft(n)),
+            "shots": SHOTS, "fusion_k_max": OPTS["k_max"], "tile_qubits": OPTS["tile_qubits"],
+            "kernel_variant": OPTS.get("kernel_variant", 0), "precision": OPTS["precision"],
+            "passes_per_step": DEFAULT_PLAN["passes_per_step"],
+            "l2": f"inputs larger than L2 ({(8 << n) / 2**30:.3g} GiB state vs 129 MB L2)",
+            "parallelism": f"replicas{world}"}
 
 
 def run_reference(args):
-    bstep = bytes_step_host()
+    """The oracle arm: every step is a by-kind gate sample of the step at n=28 on
+    all host cores plus the measured readout, extrapolated to the whole step."""
+    bstep = DEFAULT_PLAN["bytes_step"]
     vals = []
     desc = threads = None
     for i in range(args.warmup + args.steps):
-        t_step, threads, desc = oracle_sample(gates_sample=4, measure=True)
+        t_step, threads, desc = oracle_step_time(os.cpu_count() or 1)
         if i >= args.warmup:
             vals.append(t_step)
     t = statistics.median(vals)
     v = bstep / t / 1e9
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     return {
-        "impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": 1,
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-        "config": {"workload": workload_name(), "n_qubits": N_QUBITS},
+        "config": config_dict(world),
         "cpu_baseline": {"value": v, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": desc},
         "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -762,10 +822,7 @@ def main():
         # plain path, bounded to 200 requests at 1x and 4x the plain capacity
         line["serving"] = serving_sweep(200, (1.0, 4.0), args.serve_small_max)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t_step, threads, desc = oracle_sample(gates_sample=12, measure=True)
-        v = bytes_step_host() / t_step / 1e9
-        line["cpu_baseline"] = {"value": v, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": desc,
-                                "ms_per_step": t_step * 1e3}
+        line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
