@@ -497,13 +497,19 @@ int sv_batch_create(size_t n_circ, const sv_gate *const *irs, const size_t *n_ga
   if (e == cudaSuccess) e = cudaMalloc(&b->scratch, std::max<uint64_t>(scratch, 2) * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&b->out, std::max<uint64_t>(outs, 2) * sizeof(uint64_t));
   if (e == cudaSuccess) e = cudaMalloc(&b->ex, 2 * n_circ * sizeof(double));
-  if (e == cudaSuccess) e = cudaMemset(b->ex, 0, 2 * n_circ * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&b->counter, 2 * sizeof(uint32_t));  // work queue, error word
-  if (e == cudaSuccess) e = cudaMemset(b->counter, 0, 2 * sizeof(uint32_t));
+  // The records, the circuit table and the zeroed words are written on the
+  // batch's own stream, ahead of every launch of the graph on it.  (On the legacy
+  // default stream they were not ordered before launches on a non-blocking
+  // stream: a pageable cudaMemcpy may return before its DMA lands and cudaMemset
+  // is asynchronous, so a launch under load could read stale records.)
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->ex, 0, 2 * n_circ * sizeof(double), b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->counter, 0, 2 * sizeof(uint32_t), b->stream);
   b->plans_size = plans.size();
-  if (e == cudaSuccess) e = cudaMemcpy(b->plan_dev, plans.data(), plans.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
-    e = cudaMemcpy(b->circ_dev, b->circ.data(), n_circ * sizeof(BatchCirc), cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(b->plan_dev, plans.data(), plans.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->circ_dev, b->circ.data(), n_circ * sizeof(BatchCirc), cudaMemcpyHostToDevice, b->stream);
   // capture the launch once; sv_batch_launch replays the graph
   if (e == cudaSuccess) e = prepare_any(b);
   cudaStream_t cap = nullptr;
@@ -577,8 +583,9 @@ int sv_batch_amplitudes(sv_batch *b, size_t circuit, void *out) {
   const BatchCirc &c = b->circ[b->slot[circuit]];
   if (!b->keep && c.n <= uint32_t(kBatchSmemQubits))
     return set_last_error(SV_ERR_ARG, "states of <= %d qubits are kept only with keep_states", kBatchSmemQubits);
-  const cudaError_t e = cudaMemcpy(out, b->arena + c.state_off, (size_t(1) << c.n) * sizeof(float2),
-                                   cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaMemcpyAsync(out, b->arena + c.state_off, (size_t(1) << c.n) * sizeof(float2),
+                                  cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return set_last_error(SV_ERR_CUDA, "sv_batch_amplitudes: %s", cudaGetErrorString(e));
   return SV_OK;
 }

@@ -187,7 +187,7 @@ int check_device_error(sv_state *s) {
   int e = 0;
   CK(s, cudaMemcpy(&e, s->derr, sizeof(int), cudaMemcpyDeviceToHost));
   if (e) {
-    CK(s, cudaMemset(s->derr, 0, sizeof(int)));
+    CK(s, cudaMemsetAsync(s->derr, 0, sizeof(int), s->stream));  // ordered before the state's later kernels
     if (e & 2) {
       s->poisoned = true;
       return fail(SV_ERR_STATE, "a pass found its device plan records different from the host's; the state is "

@@ -100,3 +100,31 @@ def test_batch_autotune_returns_a_candidate(P):
     best, ms = P.capi.sv_batch_autotune(args, reps=1)
     assert best.k_max in (1, 2, 3) and best.tile_qubits in (10, 11, 12, 13)
     assert ms > 0
+
+
+def test_batch_records_reach_the_device_before_the_launch_under_copy_traffic(P):
+    # A batch's plan records and circuit table must be on the device before its
+    # graph runs, whatever else the copy engines are doing: here a 2 GiB
+    # host-to-device copy on another stream is queued right before each batch is
+    # created and launched on a fresh (non-blocking) stream.  A launch that read
+    # stale records would fail the kernel's record validation (synchronize
+    # raises) or give wrong states.
+    import torch
+    mix, circs = _mix(48, 9, n_lo=8, n_hi=14, d_hi=8)
+    ns = [m[0] for m in mix]
+    shots = [64] * len(mix)
+    seeds = [2000 + i for i in range(len(mix))]
+    host = torch.empty(1 << 29, dtype=torch.float32).pin_memory()
+    dev = torch.empty(1 << 29, dtype=torch.float32, device="cuda")
+    side = torch.cuda.Stream()
+    for rep in range(4):
+        with torch.cuda.stream(side):
+            dev.copy_(host, non_blocking=True)
+        b = P.Batch(circs, ns, shots, seeds, keep_states=True, stream=torch.cuda.Stream())
+        b.launch()
+        b.synchronize()
+        for i in (0, len(mix) // 2, len(mix) - 1):
+            g = b.amplitudes(i).astype(np.complex128)
+            assert oracle.fidelity(oracle.run(ns[i], circs[i]), g) >= 1 - FID_TOL, (rep, i)
+        b.close()
+    torch.cuda.synchronize()
