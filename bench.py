@@ -426,7 +426,7 @@ def run_reference(args):
 def run_batch_mode(args):
     """Config: many independent random layered circuits (n ~ U{10..20},
     depth ~ U{10..60}, 4096 shots each) in one persistent graph-captured launch,
-    autotuned on a 256-circuit sample, against the plain one-circuit-at-a-time
+    autotuned on the batch itself, against the plain one-circuit-at-a-time
     path timed on a sample and scaled to the batch."""
     import torch
     from paper_2512_04216_gb300 import Batch, StateVector, capi
@@ -436,10 +436,9 @@ def run_batch_mode(args):
     ns = [m[0] for m in mix]
     shots = [4096] * count
     seeds = [m[2] for m in mix]
-    sample_idx = list(range(0, count, max(1, count // 256)))
-    sargs = capi.BatchArgs([circs[i] for i in sample_idx], [ns[i] for i in sample_idx],
-                           [shots[i] for i in sample_idx], [seeds[i] for i in sample_idx])
-    best, best_ms = capi.sv_batch_autotune(sargs, reps=1)
+    # tuned on the batch itself: a sample too small to fill the GPU times one large
+    # circuit's latency, not the batch's throughput
+    best, best_ms = capi.sv_batch_autotune(capi.BatchArgs(circs, ns, shots, seeds), reps=1)
     b = Batch(circs, ns, shots, seeds, k_max=best.k_max, tile_qubits=best.tile_qubits)
     for _ in range(args.warmup):
         b.launch()
