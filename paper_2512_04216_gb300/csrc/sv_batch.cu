@@ -26,6 +26,7 @@
 #include "sv_device.cuh"
 #include "sv_internal.h"
 #include "sv_plan.h"
+#include "sv_regpass.cuh"
 
 namespace svgb {
 
@@ -33,6 +34,16 @@ constexpr int kBatchNT = 256;
 constexpr int kBatchSmemQubits = 13;  // states up to this size stay in shared memory
 constexpr int kBatchMaxQubits = 24;
 constexpr int kBatchMaxK = 3;
+// Arena states (more than kBatchSmemQubits qubits) planned with tiles of
+// kBatchRegT qubits run register-stage passes (16 amplitudes a thread, 256
+// threads = 2^(kBatchRegT - 4)) in this much of the CTA's shared memory.
+constexpr int kBatchRegT = 12;
+constexpr size_t kBatchRegSmem = 96 * 1024;
+// Largest register pass (records and tables) the batched kernel runs.
+__host__ __device__ inline bool batch_reg_fits(uint32_t c, uint32_t ns, uint32_t data_bytes) {
+  return ns >= 1 && ns <= uint32_t(kMaxStages) &&
+         reg_layout(kBatchRegT, c, ns, data_bytes, 4, true).total + sizeof(RegPassParams) <= kBatchRegSmem;
+}
 
 struct alignas(16) BatchCirc {
   uint64_t plan_off;     // byte offset of the circuit's plan in the plan buffer
@@ -59,6 +70,7 @@ __host__ __device__ inline BatchLayout batch_layout(int kmax) {
   L.off_chunk = o; o += (size_t(1) << (kBatchSmemQubits - 6)) * 8;
   L.off_tot = o; o += kBatchNT * 8;
   L.total = (o + 15) & ~size_t(15);
+  if (L.total < kBatchRegSmem) L.total = kBatchRegSmem;  // the arena's register passes use the same space
   return L;
 }
 
@@ -167,6 +179,19 @@ __device__ __forceinline__ bool batch_plan_ok(const uint8_t *plans, uint64_t pla
   const uint8_t *plan = plans + C.plan_off;
   for (uint32_t p = 0; p < C.n_passes; p++) {
     const PlanPass P = reinterpret_cast<const PlanPass *>(plan)[p];
+    if (P.kind == KIND_REG) {  // arena register pass: the checks k_pass_reg makes, and the budget
+      if (C.n <= uint32_t(kBatchSmemQubits) || P.T != uint32_t(kBatchRegT) || P.R != 4u || P.c < 1 ||
+          P.c + 4 > P.T || P.n_tiles != (uint64_t(1) << (C.n - P.T)) || !batch_reg_fits(P.c, P.n_stages, P.data_bytes))
+        return false;
+      if (C.plan_off + P.aux_off + sizeof(RegPassParams) > plans_size ||
+          C.plan_off + P.ops_off + uint64_t(P.data_bytes) > plans_size || (P.aux_off & 15u) || (P.ops_off & 15u))
+        return false;
+      const RegPassParams *prm = reinterpret_cast<const RegPassParams *>(plan + P.aux_off);
+      if (prm->chk[0] != P.T || prm->chk[1] != P.n_stages || prm->chk[2] != P.data_bytes || prm->chk[3] != P.ops_off)
+        return false;
+      continue;
+    }
+    if (P.kind != KIND_SMEM) return false;
     if (P.T < 1 || P.T > uint32_t(kBatchSmemQubits) || P.c < 1 || P.c > P.T || P.T > C.n) return false;
     if (C.n <= uint32_t(kBatchSmemQubits) && P.T != C.n) return false;
     if (P.n_tiles != (uint64_t(1) << (C.n - P.T))) return false;
@@ -217,7 +242,7 @@ __device__ __forceinline__ void batch_ops(float2 *tile, float2 *mat, uint32_t *a
 }
 
 template <int KMAX>
-__global__ void __launch_bounds__(kBatchNT) k_batch(const uint8_t *__restrict__ plans,
+__global__ void __launch_bounds__(kBatchNT, KMAX <= 2 ? 2 : 1) k_batch(const uint8_t *__restrict__ plans,
                                                    const BatchCirc *__restrict__ circs, uint32_t n_circ,
                                                    float2 *__restrict__ arena, double *__restrict__ scratch,
                                                    uint64_t *__restrict__ out, double *__restrict__ ex,
@@ -263,6 +288,20 @@ __global__ void __launch_bounds__(kBatchNT) k_batch(const uint8_t *__restrict__ 
       __syncthreads();
       for (uint32_t p = 0; p < C.n_passes; p++) {
         const PlanPass P = reinterpret_cast<const PlanPass *>(plan)[p];
+        if (P.kind == KIND_REG) {
+          // register stages over the circuit's tiles in order; the address tables
+          // go to the end of the register region first
+          RegPassParams *prm_s = reinterpret_cast<RegPassParams *>(smem + kBatchRegSmem - sizeof(RegPassParams));
+          {
+            const uint4 *src = reinterpret_cast<const uint4 *>(plan + P.aux_off);
+            uint4 *dst = reinterpret_cast<uint4 *>(prm_s);
+            for (uint32_t i = threadIdx.x; i < sizeof(RegPassParams) / 16; i += blockDim.x) dst[i] = src[i];
+          }
+          __syncthreads();
+          reg_pass_tiles<4>(st, plan, reinterpret_cast<const PlanPass *>(plan) + p, *prm_s, smem, 0, 1);
+          __syncthreads();
+          continue;
+        }
         const uint32_t Lt = 1u << P.T, nseg = 1u << (P.T - P.c);
         const uint32_t cs = P.c - 1u, cmask = (1u << cs) - 1u;
         for (uint32_t s = threadIdx.x; s < nseg; s += blockDim.x) segoff[s] = pdep_u64(s, P.high_mask);
@@ -425,6 +464,11 @@ int sv_batch_create(size_t n_circ, const sv_gate *const *irs, const size_t *n_ga
       return set_last_error(SV_ERR_ARG, "circuit %zu: too many shots", i);
     }
     po.tile_qubits = n <= kBatchSmemQubits ? n : T;
+    po.kernel_variant = 1;
+    // arena states with tiles of kBatchRegT qubits: register-stage passes (16
+    // amplitudes a thread) where every pass fits the kernel's register region
+    const bool try_reg = n > kBatchSmemQubits && T == kBatchRegT;
+    if (try_reg) po.kernel_variant = 2;
     Plan plan;
     std::string err;
     if (n_gates[i] && !irs[i]) {
@@ -434,6 +478,31 @@ int sv_batch_create(size_t n_circ, const sv_gate *const *irs, const size_t *n_ga
     if (!build_plan(n, irs[i], n_gates[i], &po, plan, err)) {
       free_batch(b);
       return set_last_error(SV_ERR_ARG, "circuit %zu: %s", i, err.c_str());
+    }
+    if (try_reg) {
+      bool ok = true;
+      for (auto &pp : plan.passes)
+        if (pp.kind == KIND_REG && (pp.R != 4u || pp.T != uint32_t(kBatchRegT) || !batch_reg_fits(pp.c, pp.n_stages, pp.data_bytes)))
+          ok = false;
+      if (!ok) {  // shared-memory sweeps instead
+        po.kernel_variant = 1;
+        plan = Plan();
+        if (!build_plan(n, irs[i], n_gates[i], &po, plan, err)) {
+          free_batch(b);
+          return set_last_error(SV_ERR_ARG, "circuit %zu: %s", i, err.c_str());
+        }
+      }
+    }
+    // address tables of the register passes follow the circuit's records; each
+    // pass record points at its table (aux_off, from the circuit's plan base)
+    while (plan.bytes.size() % 16) plan.bytes.push_back(0);
+    for (size_t pi = 0; pi < plan.passes.size(); pi++) {
+      if (plan.passes[pi].kind != KIND_REG) continue;
+      const uint32_t aux = uint32_t(plan.bytes.size());
+      const uint8_t *rp = reinterpret_cast<const uint8_t *>(&plan.rparams[pi]);
+      plan.bytes.insert(plan.bytes.end(), rp, rp + sizeof(RegPassParams));
+      plan.passes[pi].aux_off = aux;
+      std::memcpy(plan.bytes.data() + plan.pass_offs[pi], &plan.passes[pi], sizeof(PlanPass));
     }
     for (auto &pp : plan.passes) {
       if (pp.kmax > uint32_t(kBatchMaxK)) {

@@ -56,7 +56,9 @@ struct alignas(16) PlanPass {
   uint32_t stages_off;  // byte offset of StageRec[n_stages]
   uint32_t data_bytes;  // bytes from ops_off to the end of this pass's records
   uint32_t flags;       // kPassUnitary: every op of the pass is unitary
-  uint32_t pad_[2];
+  uint32_t aux_off;     // batched plans, KIND_REG passes: byte offset of the pass's
+                        // RegPassParams from the circuit's plan base (0 otherwise)
+  uint32_t pad_;
   int8_t lq[32];        // local bit -> physical qubit
 };
 

@@ -128,3 +128,27 @@ def test_batch_records_reach_the_device_before_the_launch_under_copy_traffic(P):
             assert oracle.fidelity(oracle.run(ns[i], circs[i]), g) >= 1 - FID_TOL, (rep, i)
         b.close()
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("k_max", [1, 2, 3])
+def test_batch_arena_register_passes_match_oracle(P, k_max):
+    # States above 13 qubits live in the arena; with 12-qubit tiles their passes
+    # run as register stages (phase ops, SWAPs folded into the store, dense blocks
+    # up to k_max qubits).  Every circuit against the oracle.
+    circs, ns = [], []
+    for n in (14, 15, 16, 18):
+        circs += [W.qft(n), W.ghz(n), W.random_gate_soup(n, 120, seed=900 + n), W.random_layered(n, 6, 950 + n)]
+        ns += [n] * 4
+    seeds = [3000 + i for i in range(len(ns))]
+    b = P.Batch(circs, ns, [256] * len(ns), seeds, k_max=k_max, tile_qubits=12, keep_states=True)
+    b.launch()
+    b.synchronize()
+    for i, n in enumerate(ns):
+        g = b.amplitudes(i).astype(np.complex128)
+        ref = oracle.run(n, circs[i])
+        assert float(np.max(np.abs(g - ref))) <= AMP_TOL, (i, n)
+        assert oracle.fidelity(ref, g) >= 1 - FID_TOL, (i, n)
+        x = b.samples(i)
+        xo, bnd, _ = oracle.sample(g, W.shot_uniforms(seeds[i], 256))
+        assert not ((x.astype(np.int64) != xo.astype(np.int64)) & (bnd == 0)).any(), i
+    b.close()
