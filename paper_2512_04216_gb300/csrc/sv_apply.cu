@@ -184,10 +184,10 @@ bool reg_pass_fits(uint32_t T, uint32_t c, uint32_t R, uint32_t n_stages, uint32
 // other thread reads, so no barrier is needed before the writes.  The next tile
 // is prefetched (16-byte cp.async, natural order) into a separate load buffer as
 // soon as every thread has read the current tile from it (the first exchange's
-// barrier), so the load overlaps most of the tile's stages.  Passes of unitary ops (kPassUnitary) restore each
-// tile's norm before the store: the exact pass keeps it, and the tensor cores'
-// float32 accumulation rounds toward zero, which would otherwise shrink the
-// state by ~1e-7 per stage.
+// barrier), so the load overlaps most of the tile's stages.  (The tensor cores'
+// float32 accumulation rounds toward zero and shrinks the state by ~1e-7 of its
+// norm per stage; sv_apply_circuit restores the norm of a unitary circuit once,
+// after its last pass.)
 // ---------------------------------------------------------------------------
 
 constexpr int kTcErrTimeout = 1;
@@ -195,7 +195,7 @@ constexpr size_t kTcStaticSmem = 1024;  // mbarriers and the TMEM base (the stat
 
 struct TcLayout {
   uint32_t L, NT;
-  size_t off_in, off_x, off_red, off_tt, off_data, total;
+  size_t off_in, off_x, off_tt, off_data, total;
 };
 
 __host__ __device__ inline TcLayout tc_layout(uint32_t T, uint32_t ns, uint32_t data_bytes) {
@@ -205,7 +205,6 @@ __host__ __device__ inline TcLayout tc_layout(uint32_t T, uint32_t ns, uint32_t 
   size_t o = 0;
   r.off_in = o; o += size_t(r.L) * 8;  // load buffer (natural order)
   r.off_x = o; o += size_t(r.L) * 8;   // exchange buffer (swizzled)
-  r.off_red = o; o += size_t(r.NT / 32) * 8;  // per warp: the tile-norm partials
   r.off_tt = o; o += size_t(ns) * r.NT * 4;
   o = (o + 15) & ~size_t(15);
   r.off_data = o; o += data_bytes;
@@ -230,7 +229,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
               const __grid_constant__ RegPassParams prm, int *__restrict__ err) {
   constexpr int NR = 16;  // R = 4 register qubits
   constexpr uint32_t kT = NT == 128 ? 11u : (NT == 256 ? 12u : 13u);
-  constexpr uint32_t NW = NT / 32, NG = NT / 128;
+  constexpr uint32_t NG = NT / 128;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar[NG];
   __shared__ uint32_t tbase_s;
@@ -238,7 +237,6 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
   const uint32_t T = P->T, c = P->c, ns = P->n_stages;
   const uint32_t data_off = P->ops_off, data_bytes = P->data_bytes;
   const uint64_t outer_mask = P->outer_mask, n_tiles = P->n_tiles;
-  const bool unitary = (P->flags & kPassUnitary) != 0u;
   // the launch's shared memory was sized from the host's copy of these fields
   if (T != kT || T != prm.chk[0] || ns != prm.chk[1] || data_bytes != prm.chk[2] || data_off != prm.chk[3] ||
       P->R != 4u || P->kind != KIND_TC || ns == 0 || ns > uint32_t(kMaxStages)) {
@@ -247,7 +245,6 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
   }
   const TcLayout lay = tc_layout(T, ns, data_bytes);
   uint32_t *tt = reinterpret_cast<uint32_t *>(smem + lay.off_tt);
-  float2 *red = reinterpret_cast<float2 *>(smem + lay.off_red);
   uint8_t *data = smem + lay.off_data;
   const uint32_t tid = threadIdx.x, warp = tid >> 5, g = tid >> 7;
 
@@ -310,11 +307,6 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
     }
 #pragma unroll
     for (int j = 0; j < NR; j++) v[j] = lds64(sin + t_ldx + prm.lo[j]);
-    float2 nin = make_float2(0.f, 0.f);
-    if (unitary) {
-#pragma unroll
-      for (int j = 0; j < NR; j++) nin = __ffma2_rn(v[j], v[j], nin);
-    }
     if (ns == 1) {  // no exchange barrier: make sure every thread has read the load buffer
       if (__syncthreads_or(bad)) {
         aborted = true;
@@ -383,35 +375,6 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
       }
     }
     if (aborted) break;
-    if (unitary) {
-      float2 nout = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int j = 0; j < NR; j++) nout = __ffma2_rn(v[j], v[j], nout);
-      float a = nin.x + nin.y, b = nout.x + nout.y;
-#pragma unroll
-      for (int m = 16; m > 0; m >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, m);
-        b += __shfl_xor_sync(0xffffffffu, b, m);
-      }
-      if ((tid & 31u) == 0) red[warp] = make_float2(a, b);
-      if (__syncthreads_or(bad)) {
-        aborted = true;
-        break;
-      }
-      float si = 0.f, so = 0.f;
-#pragma unroll
-      for (uint32_t x = 0; x < NW; x++) {
-        const float2 r = red[x];
-        si += r.x;
-        so += r.y;
-      }
-      if (si > 0.f && so > 0.f) {
-        const float sc = sqrtf(__fdiv_rn(si, so));
-        const float2 s2 = make_float2(sc, sc);
-#pragma unroll
-        for (int j = 0; j < NR; j++) v[j] = __fmul2_rn(v[j], s2);
-      }
-    }
     {
       float2 *dst = amp + base + t_st;
 #pragma unroll

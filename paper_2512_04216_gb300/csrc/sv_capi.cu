@@ -442,6 +442,18 @@ int sv_apply_circuit(sv_state *s, const sv_gate *ir, size_t n_gates, const sv_op
     if (rc) return rc;
   }
   const double pass_bytes = 16.0 * double(uint64_t(1) << s->n);
+  // Tensor-core passes shrink the norm by ~1e-7 per stage (float32 accumulation
+  // rounding toward zero); a unitary circuit keeps ||psi||^2, so its norm is
+  // measured before the first pass and restored after the last.
+  const bool restore = opts && opts->precision == 1 && builder.unitary() && s->n >= 11;
+  if (restore) {
+    int rc = ensure_reduce(s);
+    if (rc) return rc;
+    CK(s, timed(s, "reduce", double(size_t(8) << s->n), [&] {
+         return launch_reduce_pz(s->amp, s->n, 0, s->ms.part, s->ms.n_part, s->dscal + 4, s->stream);
+       }));
+  }
+  bool any_tc = false;
   size_t chunk = 2;
   while (!builder.done()) {
     Plan plan;
@@ -455,6 +467,7 @@ int sv_apply_circuit(sv_state *s, const sv_gate *ir, size_t n_gates, const sv_op
     std::memcpy(sl.host, plan.bytes.data(), bytes);
     CK(s, cudaMemcpyAsync(sl.dev, sl.host, bytes, cudaMemcpyHostToDevice, s->stream));
     for (size_t p = 0; p < plan.passes.size(); p++) {
+      any_tc |= plan.passes[p].kind == KIND_TC;
       const char *kname = plan.passes[p].kind == KIND_TC ? "pass_tc" : "pass";
       CK(s, timed(s, kname, pass_bytes, [&] {
            return launch_pass(s->amp, sl.dev, plan.pass_offs[p], plan.passes[p], &plan.rparams[p], s->derr,
@@ -463,6 +476,13 @@ int sv_apply_circuit(sv_state *s, const sv_gate *ir, size_t n_gates, const sv_op
     }
     CK(s, cudaEventRecord(sl.done, s->stream));
     sl.live = true;
+  }
+  if (restore && any_tc) {
+    CK(s, timed(s, "reduce", double(size_t(8) << s->n), [&] {
+         return launch_reduce_pz(s->amp, s->n, 0, s->ms.part, s->ms.n_part, s->dscal + 6, s->stream);
+       }));
+    CK(s, timed(s, "norm_restore", double(size_t(16) << s->n),
+                [&] { return launch_norm_restore(s->amp, s->n, s->dscal + 4, s->dscal + 6, s->stream); }));
   }
   return SV_OK;
 }

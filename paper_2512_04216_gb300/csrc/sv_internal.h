@@ -34,10 +34,6 @@ constexpr int kMaxK = 5;       // largest fused block
 
 enum : uint32_t { KIND_SMEM = 0, KIND_REG = 1, KIND_TC = 2 };
 
-// PlanPass::flags.  A pass of unitary ops maps each tile's amplitudes by a
-// unitary of the tile's 2^T-dimensional space (its ops act on tile qubits, with
-// outer qubits only as fixed controls and phases), so it keeps every tile's norm.
-constexpr uint32_t kPassUnitary = 1;
 
 struct alignas(16) PlanPass {
   uint64_t outer_mask;  // physical qubits outside the tile (within n)
@@ -55,7 +51,7 @@ struct alignas(16) PlanPass {
   uint32_t n_stages;
   uint32_t stages_off;  // byte offset of StageRec[n_stages]
   uint32_t data_bytes;  // bytes from ops_off to the end of this pass's records
-  uint32_t flags;       // kPassUnitary: every op of the pass is unitary
+  uint32_t pad0_;
   uint32_t aux_off;     // batched plans, KIND_REG passes: byte offset of the pass's
                         // RegPassParams from the circuit's plan base (0 otherwise)
   uint32_t pad_;
@@ -153,6 +149,10 @@ static_assert(sizeof(PlanPass) == 112, "PlanPass layout");
 static_assert(sizeof(StageRec) == 288, "StageRec layout");
 static_assert(sizeof(OpRec) == 16, "OpRec layout");
 static_assert(sizeof(PhaseTerm) == 16, "PhaseTerm layout");
+
+// ||psi||^2 restoration after a unitary circuit: amp *= sqrt(before[0] / after[0])
+// (both device doubles; nothing changes if either is not positive).
+cudaError_t launch_norm_restore(float2 *amp, int n, const double *before, const double *after, cudaStream_t st);
 
 // Launch one pass kernel (sv_apply.cu).  plan_dev/pass_off locate the PlanPass;
 // host_pass is the same record on the host (for grid size and template choice).

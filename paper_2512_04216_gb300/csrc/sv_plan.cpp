@@ -125,8 +125,8 @@ static bool gate_matrix(const sv_gate &g, GateM &out, std::string &err) {
           return false;
         }
       }
-      // max |(U^dagger U - I)_ij|: the tensor-core pass restores tile norms only
-      // for passes whose gates are all unitary
+      // max |(U^dagger U - I)_ij|: sv_apply_circuit restores the norm after a
+      // tensor-core apply only when every gate is unitary
       double dev = 0.0;
       for (size_t a = 0; a < K; a++)
         for (size_t b = 0; b < K; b++) {
@@ -669,11 +669,10 @@ static void apply_on_positions(std::vector<cd> &U, const std::vector<cd> &G, int
 static RegPassParams reg_params(const PlanPass &hp, const StageRec &first, const StageRec &last,
                                 const int *outq);
 
-// `unitary`: every gate of the pass is unitary (the kernel then restores tile
-// norms); `outq`: local bit -> physical qubit of the store; `rp` receives the
-// kernel's address tables and record checks.
+// `outq`: local bit -> physical qubit of the store; `rp` receives the kernel's
+// address tables and record checks.
 static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint32_t> &omask, const int *lpos,
-                         int T, int c, bool unitary, const int *outq, PlanPass &hp, std::vector<uint8_t> &buf,
+                         int T, int c, const int *outq, PlanPass &hp, std::vector<uint8_t> &buf,
                          RegPassParams &rp, sv_plan_info &info) {
   std::vector<HStage> stages;
   assign_stages(ops, omask, T, c, 4, stages, true);
@@ -770,7 +769,6 @@ static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint3
   hp.n_phase_terms = nterms;
   hp.kind = KIND_TC;
   hp.R = 4;
-  hp.flags = unitary ? kPassUnitary : 0u;
   rp = reg_params(hp, srecs.front(), srecs.back(), outq);
   rp.chk[0] = hp.T;
   rp.chk[1] = hp.n_stages;
@@ -1136,10 +1134,8 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
     bool store_natural = true;
     for (int q = 0; q < c; q++) store_natural &= store_lanes[size_t(q)] == q;
     // tensor-core stages (precision 1) when the pass fits the TC kernel
-    bool unitary = true;
-    for (uint32_t gi : ph.acc) unitary &= gates[gi].unitary;
     if (o.precision == 1 && kmx <= 4 && !ph.relabeled &&
-        pack_tc_pass(ph.ops, omask, lpos, int(hp.T), c, unitary, outq, hp, buf, plan.rparams[p], plan.info)) {
+        pack_tc_pass(ph.ops, omask, lpos, int(hp.T), c, outq, hp, buf, plan.rparams[p], plan.info)) {
       hp.kmax = kmx;
       for (auto &op : ph.ops)
         if (op.type == OP_DENSE) plan.info.flops += uint64_t(amps * 8.0 * double(1 << op.blk.k()));

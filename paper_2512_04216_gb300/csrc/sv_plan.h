@@ -42,6 +42,12 @@ class PlanBuilder {
  public:
   bool init(int n, const sv_gate *ir, size_t ng, const sv_opts *opts, std::string &err);
   bool done() const { return remaining_.empty(); }
+  // Every gate of the circuit is unitary (named gates; UNITARY matrices within 1e-6).
+  bool unitary() const {
+    for (const GateM &g : gates_)
+      if (!g.unitary) return false;
+    return true;
+  }
   bool next(Plan &plan, size_t max_passes, std::string &err);
 
  private:
