@@ -184,10 +184,11 @@ bool reg_pass_fits(uint32_t T, uint32_t c, uint32_t R, uint32_t n_stages, uint32
 // other thread reads, so no barrier is needed before the writes.  The next tile
 // is prefetched (16-byte cp.async, natural order) into a separate load buffer as
 // soon as every thread has read the current tile from it (the first exchange's
-// barrier), so the load overlaps most of the tile's stages.  (The tensor cores'
+// barrier), so the load overlaps most of the tile's stages.  The group's threads
+// wait for the product on the group's mbarrier themselves.  (The tensor cores'
 // float32 accumulation rounds toward zero and shrinks the state by ~1e-7 of its
-// norm per stage; sv_apply_circuit restores the norm of a unitary circuit once,
-// after its last pass.)
+// norm per stage; for a unitary circuit the passes track the norm, see TcNorm
+// and NormAcc.)
 // ---------------------------------------------------------------------------
 
 constexpr int kTcErrTimeout = 1;
@@ -223,10 +224,37 @@ __device__ __forceinline__ void group_bar_sync(uint32_t g) {
   }
 }
 
+// Running sum of |a|^2 over a thread's tiles: each tile's 16 amplitudes in
+// float32 pairs (re^2, im^2), then added to a float32 sum with its rounding
+// error kept in a second float (TwoSum, Knuth), so the sum over hundreds of tiles
+// keeps ~2^-44 relative accuracy without per-tile FP64 instructions (slow on this
+// part).  The pair goes to double once, at the end of the kernel.
+struct NormAcc {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add_row(const float2 (&v)[16]) {
+    float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 16; j++) a = __ffma2_rn(v[j], v[j], a);
+    const float x = __fadd_rn(a.x, a.y);
+    const float t = __fadd_rn(s, x);
+    const float bp = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    s = t;
+    c = __fadd_rn(c, e);
+  }
+  // warp sum in double, one atomic add per warp
+  __device__ __forceinline__ void flush(double *dst) const {
+    double x = double(s) + double(c);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31u) == 0) atomicAdd(dst, x);
+  }
+};
+
 template <int NT>
 __global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
     k_pass_tc(float2 *__restrict__ amp, const uint8_t *__restrict__ plan, uint32_t pass_off,
-              const __grid_constant__ RegPassParams prm, int *__restrict__ err) {
+              const __grid_constant__ RegPassParams prm, int *__restrict__ err, const TcNorm nrm) {
   constexpr int NR = 16;  // R = 4 register qubits
   constexpr uint32_t kT = NT == 128 ? 11u : (NT == 256 ? 12u : 13u);
   constexpr uint32_t NG = NT / 128;
@@ -297,6 +325,15 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
   uint32_t parity = 0;
   bool bad = false, aborted = false;
   float2 v[NR];
+  // the previous pass's norm drift, undone on load: a <- a + a * delta with
+  // delta = sqrt(ref / prev) - 1 (~1e-7, far finer than float32 steps of 1)
+  float delta = 0.f;
+  if (nrm.ref && nrm.prev) {
+    const double r = *nrm.ref, q = *nrm.prev;
+    if (r > 0.0 && q > 0.0 && r < 1e300 && q < 1e300) delta = float(sqrt(r / q) - 1.0);
+  }
+  if (nrm.clear && blockIdx.x == 0 && tid == 0) *nrm.clear = 0.0;
+  NormAcc acc_in, acc_out;
   while (tile < n_tiles) {
     const uint64_t next = tile + gridDim.x;
     const uint64_t base_next = next < n_tiles ? pdep_u64(next, outer_mask) : 0;
@@ -307,6 +344,12 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
     }
 #pragma unroll
     for (int j = 0; j < NR; j++) v[j] = lds64(sin + t_ldx + prm.lo[j]);
+    if (nrm.in_sum) acc_in.add_row(v);
+    if (delta != 0.f) {
+      const float2 d2 = make_float2(delta, delta);
+#pragma unroll
+      for (int j = 0; j < NR; j++) v[j] = __ffma2_rn(v[j], d2, v[j]);
+    }
     if (ns == 1) {  // no exchange barrier: make sure every thread has read the load buffer
       if (__syncthreads_or(bad)) {
         aborted = true;
@@ -357,14 +400,16 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
         tmem_wait_st();
         tc_fence_before();
         group_bar_sync(g);  // the group's rows are in tensor memory
-        if ((tid & 127u) == 0) {  // one thread issues, commits and waits; the others block
+        if ((tid & 127u) == 0) {  // one thread issues and commits
           tc_fence_after();
           issue_stage_mma(gcols, smem_u32(data + (st.b_off - data_off)));
           mma_commit(&bar[g]);
-          if (!mbar_wait_bounded(&bar[g], parity)) bad = true;
         }
+        // every thread of the group waits for the commit's phase itself (a
+        // thread cannot reach the next stage's wait before the whole group has
+        // passed the next group barrier, so phases cannot be skipped)
+        if (!mbar_wait_bounded(&bar[g], parity)) bad = true;
         parity ^= 1u;
-        group_bar_sync(g);  // the product is in tensor memory
         tc_fence_after();
         load_row_sum(tq, v);
       }
@@ -375,6 +420,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
       }
     }
     if (aborted) break;
+    if (nrm.out_sum) acc_out.add_row(v);
     {
       float2 *dst = amp + base + t_st;
 #pragma unroll
@@ -388,6 +434,8 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
   __syncthreads();
   if (warp == 0) tmem_dealloc(tbase, NT);
   if (tid == 0 && aborted) atomicOr(err, kTcErrTimeout);
+  if (nrm.in_sum) acc_in.flush(nrm.in_sum);
+  if (nrm.out_sum) acc_out.flush(nrm.out_sum);
 }
 
 // Smallest dynamic shared memory that keeps (512 / TMEM columns) CTAs per SM at
@@ -400,7 +448,7 @@ static size_t tc_smem_floor(uint32_t nt) {
 
 template <int NT>
 static cudaError_t launch_tc(float2 *amp, const uint8_t *plan, uint32_t off, const PlanPass &hp,
-                             const RegPassParams &prm, int *err, cudaStream_t st) {
+                             const RegPassParams &prm, int *err, cudaStream_t st, const TcNorm &nrm) {
   const TcLayout lay = tc_layout(hp.T, hp.n_stages, hp.data_bytes);
   size_t smem = lay.total;
   const size_t floor_ = tc_smem_floor(NT);
@@ -433,7 +481,7 @@ static cudaError_t launch_tc(float2 *amp, const uint8_t *plan, uint32_t off, con
   if (nsm < 1) nsm = 1;
   const uint64_t want = uint64_t(nsm) * per_sm;
   const unsigned grid = unsigned(hp.n_tiles < want ? hp.n_tiles : want);
-  k_pass_tc<NT><<<grid, NT, smem, st>>>(amp, plan, off, prm, err);
+  k_pass_tc<NT><<<grid, NT, smem, st>>>(amp, plan, off, prm, err, nrm);
   count_launch();
   return cudaGetLastError();
 }
@@ -477,12 +525,14 @@ static cudaError_t launch_k(float2 *amp, const uint8_t *plan, uint32_t off, cons
 }
 
 cudaError_t launch_pass(float2 *amp, const uint8_t *plan_dev, uint32_t pass_off,
-                        const PlanPass &hp, const RegPassParams *prm, int *err, cudaStream_t stream) {
+                        const PlanPass &hp, const RegPassParams *prm, int *err, cudaStream_t stream,
+                        const TcNorm *norm) {
   if (hp.kind == KIND_TC) {
     if (!prm || !err) return cudaErrorInvalidValue;
-    if (hp.T == 11) return launch_tc<128>(amp, plan_dev, pass_off, hp, *prm, err, stream);
-    if (hp.T == 12) return launch_tc<256>(amp, plan_dev, pass_off, hp, *prm, err, stream);
-    if (hp.T == 13) return launch_tc<512>(amp, plan_dev, pass_off, hp, *prm, err, stream);
+    const TcNorm nrm = norm ? *norm : TcNorm{};
+    if (hp.T == 11) return launch_tc<128>(amp, plan_dev, pass_off, hp, *prm, err, stream, nrm);
+    if (hp.T == 12) return launch_tc<256>(amp, plan_dev, pass_off, hp, *prm, err, stream, nrm);
+    if (hp.T == 13) return launch_tc<512>(amp, plan_dev, pass_off, hp, *prm, err, stream, nrm);
     return cudaErrorInvalidValue;
   }
   if (hp.kind == KIND_REG) {

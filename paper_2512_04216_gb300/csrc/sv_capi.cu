@@ -74,7 +74,7 @@ struct sv_state {
   cudaStream_t stream = nullptr;
   // measurement scratch
   MeasureScratch ms;
-  double *dscal = nullptr;       // device scalars: [0] sum p, [1] sum pz, [2] total
+  double *dscal = nullptr;       // device scalars: [0] sum p, [1] sum pz, [2] total, [4..7] norm tracking
   uint64_t *dcount = nullptr;    // boundary counter
   int *derr = nullptr;           // device error word written by bounded waits
   double *hscal = nullptr;       // pinned host scalars
@@ -443,17 +443,13 @@ int sv_apply_circuit(sv_state *s, const sv_gate *ir, size_t n_gates, const sv_op
   }
   const double pass_bytes = 16.0 * double(uint64_t(1) << s->n);
   // Tensor-core passes shrink the norm by ~1e-7 per stage (float32 accumulation
-  // rounding toward zero); a unitary circuit keeps ||psi||^2, so its norm is
-  // measured before the first pass and restored after the last.
-  const bool restore = opts && opts->precision == 1 && builder.unitary() && s->n >= 11;
-  if (restore) {
-    int rc = ensure_reduce(s);
-    if (rc) return rc;
-    CK(s, timed(s, "reduce", double(size_t(8) << s->n), [&] {
-         return launch_reduce_pz(s->amp, s->n, 0, s->ms.part, s->ms.n_part, s->dscal + 4, s->stream);
-       }));
-  }
-  bool any_tc = false;
+  // rounding toward zero); a unitary circuit keeps ||psi||^2, so its passes track
+  // the norm (TcNorm): dscal[4] takes the first tensor-core pass's input sum,
+  // dscal[5..7] the output sums of successive tensor-core passes in rotation, and
+  // each later pass rescales what it loads by sqrt(dscal[4] / previous sum).
+  const bool track = opts && opts->precision == 1 && builder.unitary() && s->n >= 11;
+  if (track) CK(s, cudaMemsetAsync(s->dscal + 4, 0, 2 * sizeof(double), s->stream));
+  size_t n_tc = 0;
   size_t chunk = 2;
   while (!builder.done()) {
     Plan plan;
@@ -467,22 +463,28 @@ int sv_apply_circuit(sv_state *s, const sv_gate *ir, size_t n_gates, const sv_op
     std::memcpy(sl.host, plan.bytes.data(), bytes);
     CK(s, cudaMemcpyAsync(sl.dev, sl.host, bytes, cudaMemcpyHostToDevice, s->stream));
     for (size_t p = 0; p < plan.passes.size(); p++) {
-      any_tc |= plan.passes[p].kind == KIND_TC;
-      const char *kname = plan.passes[p].kind == KIND_TC ? "pass_tc" : "pass";
+      const bool tc = plan.passes[p].kind == KIND_TC;
+      TcNorm nrm;
+      if (tc && track) {
+        double *slot = s->dscal + 5;
+        if (n_tc == 0) {
+          nrm.in_sum = s->dscal + 4;
+        } else {
+          nrm.ref = s->dscal + 4;
+          nrm.prev = slot + (n_tc - 1) % 3;
+        }
+        nrm.out_sum = slot + n_tc % 3;      // zeroed by the memset or the previous pass
+        nrm.clear = slot + (n_tc + 1) % 3;  // read by the previous pass, summed into by the next
+        n_tc++;
+      }
+      const char *kname = tc ? "pass_tc" : "pass";
       CK(s, timed(s, kname, pass_bytes, [&] {
            return launch_pass(s->amp, sl.dev, plan.pass_offs[p], plan.passes[p], &plan.rparams[p], s->derr,
-                              s->stream);
+                              s->stream, &nrm);
          }));
     }
     CK(s, cudaEventRecord(sl.done, s->stream));
     sl.live = true;
-  }
-  if (restore && any_tc) {
-    CK(s, timed(s, "reduce", double(size_t(8) << s->n), [&] {
-         return launch_reduce_pz(s->amp, s->n, 0, s->ms.part, s->ms.n_part, s->dscal + 6, s->stream);
-       }));
-    CK(s, timed(s, "norm_restore", double(size_t(16) << s->n),
-                [&] { return launch_norm_restore(s->amp, s->n, s->dscal + 4, s->dscal + 6, s->stream); }));
   }
   return SV_OK;
 }

@@ -152,13 +152,31 @@ static_assert(sizeof(PhaseTerm) == 16, "PhaseTerm layout");
 
 // ||psi||^2 restoration after a unitary circuit: amp *= sqrt(before[0] / after[0])
 // (both device doubles; nothing changes if either is not positive).
-cudaError_t launch_norm_restore(float2 *amp, int n, const double *before, const double *after, cudaStream_t st);
+
+// Norm tracking across the tensor-core passes of one unitary circuit.  The
+// tensor cores' float32 accumulation rounds toward zero, so every stage product
+// shrinks the state by ~1e-7 of its norm, while a unitary circuit keeps
+// ||psi||^2.  The circuit's first tensor-core pass sums |a|^2 of what it loads
+// into in_sum; every tracked pass sums |a|^2 of what it stores into out_sum; a
+// later pass scales what it loads by sqrt(*ref / *prev) (ref: the first pass's
+// input sum, prev: the previous tracked pass's output sum).  So the drift of
+// every pass but the last is undone as the next pass reads the state, and no
+// extra pass over the state is needed.  All pointers are device doubles; null
+// disables the corresponding step.
+struct TcNorm {
+  double *in_sum = nullptr;        // zeroed before the pass
+  const double *ref = nullptr;     // with prev: the scale's numerator
+  const double *prev = nullptr;    // the previous tracked pass's output sum
+  double *out_sum = nullptr;       // zeroed before the pass
+  double *clear = nullptr;         // set to zero by this pass (the next pass's out_sum)
+};
 
 // Launch one pass kernel (sv_apply.cu).  plan_dev/pass_off locate the PlanPass;
 // host_pass is the same record on the host (for grid size and template choice).
+// `norm` applies to tensor-core passes only (may be null).
 cudaError_t launch_pass(float2 *amp, const uint8_t *plan_dev, uint32_t pass_off,
                         const PlanPass &host_pass, const RegPassParams *reg_params, int *err,
-                        cudaStream_t stream);
+                        cudaStream_t stream, const TcNorm *norm = nullptr);
 // Whether a tensor-core pass fits the kernel's shared memory.
 bool tc_pass_fits(uint32_t T, uint32_t c, uint32_t n_stages, uint32_t data_bytes);
 // Whether a register-stage pass fits the persistent kernel's shared-memory tables.

@@ -224,41 +224,6 @@ cudaError_t launch_reduce_pz(const float2 *amp, int n, uint64_t zmask, double *p
 }
 
 // ---- norm restoration --------------------------------------------------------
-// amp *= sqrt(before / after): a unitary circuit keeps ||psi||^2 exactly, so the
-// tensor-core path (whose float32 accumulation rounds toward zero) rescales once
-// after its last pass.  One CTA thread forms the factor in double.
-__global__ void __launch_bounds__(kRT) k_norm_restore(float4 *__restrict__ amp, uint64_t n4,
-                                                     const double *__restrict__ before,
-                                                     const double *__restrict__ after) {
-  __shared__ float sc;
-  if (threadIdx.x == 0) {
-    const double b = before[0], a = after[0];
-    sc = (b > 0.0 && a > 0.0) ? float(sqrt(b / a)) : 1.f;
-  }
-  __syncthreads();
-  const float s = sc;
-  if (s == 1.f) return;
-  const float2 s2 = make_float2(s, s);
-  for (uint64_t i = uint64_t(blockIdx.x) * kRT + threadIdx.x; i < n4; i += uint64_t(gridDim.x) * kRT) {
-    float4 v = amp[i];
-    const float2 lo = __fmul2_rn(make_float2(v.x, v.y), s2), hi = __fmul2_rn(make_float2(v.z, v.w), s2);
-    amp[i] = make_float4(lo.x, lo.y, hi.x, hi.y);
-  }
-}
-
-cudaError_t launch_norm_restore(float2 *amp, int n, const double *before, const double *after, cudaStream_t st) {
-  const uint64_t n4 = (uint64_t(1) << n) / 2;  // float4 = two amplitudes (n >= 1)
-  int dev = 0, sms = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return e;
-  const uint64_t want = uint64_t(sms) * 8, need = (n4 + kRT - 1) / kRT;
-  k_norm_restore<<<unsigned(need < want ? need : want), kRT, 0, st>>>(reinterpret_cast<float4 *>(amp), n4, before,
-                                                                    after);
-  count_launch();
-  return cudaGetLastError();
-}
-
 // ---- CDF --------------------------------------------------------------------
 // Chunk sums (64 amplitudes; four threads each) and 4096-amplitude block sums;
 // with zblock, also the block's sum of p * (-1)^popcount(i & zmask), from the

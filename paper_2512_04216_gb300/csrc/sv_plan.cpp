@@ -527,10 +527,14 @@ struct HStage {
 // Greedy, in op order: a stage takes every op whose earlier unplaced ops do not
 // share a bit with it and whose bits fit the stage's Rb register bits.  Phase
 // ops need no register bits.  The first stage avoids the c low bits (it loads
-// from HBM with the low bits on the lanes), and a store stage is appended when
-// the last stage holds a low bit.  With `tc` the dense ops of a stage become one
-// product applied before the stage's phase ops, so a dense op that touches a
-// bit of an accepted phase op waits for a later stage.
+// with the low bits on the lanes), and for register passes a store stage is
+// appended when the last stage holds a low bit.  With `tc` the dense ops of a
+// stage become one product applied before the stage's phase ops, so a dense op
+// that touches a bit of an accepted phase op waits for a later stage; and the
+// last stage stores whatever bits it holds (no store stage: an appended stage
+// costs a whole-tile exchange through shared memory, more than the partly
+// filled 32-byte sectors of a store whose lanes skip some low bits, which L2
+// merges before they reach DRAM).
 // `store_low` (default: the c low bits) is the set of local bits that the store
 // puts on the lanes; it differs from the load's low bits when SWAPs relabel qubits
 // (`store_natural` false: the store lanes are not local bits 0..c-1 in order, so a
@@ -574,11 +578,11 @@ static void assign_stages(const std::vector<HostOp> &ops, const std::vector<uint
     first = false;
   }
   if (st.empty()) st.push_back(HStage{});
-  if ((st.back().R & store_low) || (st.size() == 1 && !store_natural)) st.push_back(HStage{});
+  if (!tc && ((st.back().R & store_low) || (st.size() == 1 && !store_natural))) st.push_back(HStage{});
   for (size_t i = 0; i < st.size(); i++) {
     uint32_t allowed = all;
     if (i == 0) allowed &= ~low;
-    if (i + 1 == st.size()) allowed &= ~store_low;
+    if (i + 1 == st.size() && !tc) allowed &= ~store_low;
     for (int b = T - 1; b >= 0 && popc(uint64_t(st[i].R)) < Rb; b--)
       if (((allowed >> b) & 1u) && !((st[i].R >> b) & 1u)) st[i].R |= 1u << b;
   }
@@ -600,8 +604,32 @@ static StageRec make_stage(const HStage &hs, int T, int c, int Rb, bool load, bo
     tb = *store_lanes;  // output qubits 0..c-1 on the lanes, then the rest ascending
     for (int b : rest)
       if (std::find(tb.begin(), tb.end(), b) == tb.end()) tb.push_back(b);
-  } else if (load || store) {
+  } else if (load) {
     tb = rest;  // ascending: the low tile bits sit on the lanes
+  } else if (store) {
+    // the lowest bits not held in registers on the lanes, for the store; a bit
+    // whose swizzle image depends on the half-warp's earlier lane bits waits,
+    // so the exchange read into this stage stays conflict-free (register
+    // passes keep the c low bits out of their store stage, and get them in order)
+    uint32_t basis[4] = {0, 0, 0, 0};
+    std::vector<int> lanes, others;
+    for (int b : rest) {
+      uint32_t v = swz_col(b);
+      for (int i = 3; i >= 0; i--)
+        if ((v >> i) & 1u) {
+          if (basis[i]) {
+            v ^= basis[i];
+          } else {
+            basis[i] = v;
+            break;
+          }
+        }
+      if (v && lanes.size() < 4) lanes.push_back(b);
+      else others.push_back(b);
+    }
+    tb = lanes;
+    std::sort(others.begin(), others.end());
+    tb.insert(tb.end(), others.begin(), others.end());
   } else {
     // four lane bits whose swizzle images are independent (one half-warp of
     // 8-byte accesses then hits 16 distinct bank pairs), then the others

@@ -132,8 +132,9 @@ def test_tc_mirror_28(sv):
     # fidelity with |0...0>: |a_0|^2 / ||psi||^2
     assert abs(a0) ** 2 / norm2 >= 1 - FID_TOL, (abs(a0) ** 2, norm2)
     # The tensor cores' float32 accumulation rounds toward zero (~1e-7 of norm
-    # per stage product, ~500 products here); the kernel restores every tile's
-    # norm, which the exact unitary pass keeps, so the norm holds to the CUDA-core
+    # per stage product, ~500 products here); the passes of a unitary circuit
+    # track the norm and each pass undoes the previous pass's drift as it loads,
+    # so only the last pass's drift remains and the norm holds to the CUDA-core
     # path's bar.
     assert abs(norm2 - 1) < 1e-5, norm2
     s.close()
@@ -153,3 +154,23 @@ def test_tc_non_unitary_matrix_not_renormalised(sv):
     g = _run(sv, n, circ, k_max=4, tile_qubits=12)
     assert abs(oracle.norm2(g) - 0.81) < 1e-5
     _compare(g, ref, "0.9 x unitary")
+
+
+def test_tc_norm_tracking_keeps_input_norm(sv):
+    # The passes of a unitary circuit undo each pass's norm drift against the
+    # norm the circuit started from, which need not be 1: a state of norm^2
+    # 0.64 keeps 0.64 (relative 1e-5) through ~40 tensor-core passes, and the
+    # amplitudes still match the oracle's exact unitary action.
+    n = 18
+    rng = np.random.default_rng(9)
+    psi0 = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    psi0 = (0.8 * psi0 / np.linalg.norm(psi0)).astype(np.complex64)
+    circ = W.random_layered(n, 40, 17)
+    info = sv.capi.sv_plan_stats(n, circ, sv.capi.make_opts(4, 11, 5, 1))
+    assert info["passes_by_kind"][2] >= 20
+    g = _run(sv, n, circ, psi0=psi0, k_max=4, tile_qubits=11)
+    n0 = oracle.norm2(psi0.astype(np.complex128))
+    assert abs(oracle.norm2(g) / n0 - 1) < 1e-5, (oracle.norm2(g), n0)
+    ref = oracle.run(n, circ, psi0.astype(np.complex128))
+    err = float(np.max(np.abs(g - ref)))
+    assert err <= AMP_TOL, err
