@@ -1,24 +1,45 @@
-// Host interpreter of packed plans (register-stage and shared-memory passes), for
-// tests/test_plan_semantics.py.  It plans a circuit with the library's planner
-// (build_plan), then executes every pass the way the register kernel reads its
-// records -- the load's chunk rows (RegPassParams.ko), stage 0's offsets
-// (lo), each stage's thread bits (tb) and swizzled exchange offsets (xo), the
-// dense ops on register positions (rmask, (re, re, -im, im) matrices), the
-// register phase ops (classes, D), and the store (oq, go) -- in complex
-// double, and compares the result with the circuit's gates applied one by one.
-// With a chunk size it plans incrementally (PlanBuilder, as the library streams
-// its plans) and runs the chunks in order.
+// Host interpreter of packed plans (register-stage, tensor-core and shared-memory
+// passes), for tests/test_plan_semantics.py.  It plans a circuit with the
+// library's planner (build_plan), then executes every pass the way the register
+// and tensor-core kernels read their records -- the load's chunk rows
+// (RegPassParams.ko), stage 0's offsets (lo), each stage's thread bits (tb) and
+// swizzled exchange offsets (xo), the dense ops on register positions (rmask,
+// (re, re, -im, im) matrices) or the stage's product with its real-embedded
+// matrix B (D[m][n] = sum_k A[m][k] B[n][k], A = a thread's 16 amplitudes as
+// (re, im) pairs), the register phase ops (classes, D), and the store (oq, go)
+// -- in complex double, and compares the result with the circuit's gates applied
+// one by one.  With a chunk size it plans incrementally (PlanBuilder, as the
+// library streams its plans) and runs the chunks in order.
 // Shared-memory passes run the way k_pass reads theirs.  Exit status 0 when
-// every amplitude agrees within 1e-5, 2 otherwise, 3 on a tensor-core pass.
+// every amplitude agrees within 1e-5, 2 otherwise.
 #include "sv_plan.cpp"
 
 #include <cstdio>
 #include <random>
 
-// device-side helpers the planner links against
+// Device-side helpers the planner links against.  The stage image here holds
+// B as float pairs (hi = float(B), lo = float(B - hi)), [hi 32 x 32 | lo 32 x 32]
+// row-major in n: the interpreter checks what the planner computes and packs
+// (stages, their matrices, offsets), not the tensor cores' operand layout,
+// which the GPU self-test of the stage product covers.
 namespace svgb {
-bool tc_pass_fits(uint32_t, uint32_t, uint32_t, uint32_t) { return false; }
-void tc_b_image(const double *, uint8_t *) {}
+bool tc_pass_fits(uint32_t T, uint32_t c, uint32_t n_stages, uint32_t data_bytes) {
+  // the kernel's limits: 11 <= T <= 13, shared memory = load + exchange buffers
+  // (8 B an amplitude each), the per-thread stage tables, the pass's records
+  if (T < 11 || T > 13 || T < c + 4 || c < 1 || n_stages < 1 || n_stages > 64 || data_bytes > 160u * 1024u)
+    return false;
+  const size_t L = size_t(1) << T, NT = L >> 4;
+  size_t o = 16 * L + size_t(n_stages) * NT * 4;
+  o = (o + 15) & ~size_t(15);
+  return o + data_bytes + 1024 <= 232448;
+}
+void tc_b_image(const double *B, uint8_t *img) {
+  float *f = reinterpret_cast<float *>(img);
+  for (int i = 0; i < 32 * 32; i++) {
+    f[i] = float(B[i]);
+    f[1024 + i] = float(B[i] - double(f[i]));
+  }
+}
 bool reg_pass_fits(uint32_t, uint32_t, uint32_t, uint32_t, uint32_t) { return true; }
 }  // namespace svgb
 
@@ -67,9 +88,11 @@ static cdd turn_exp(uint32_t turn) {
   return cdd(std::cos(a), std::sin(a));
 }
 
+// Register-stage passes (KIND_REG) and tensor-core passes (KIND_TC: the same
+// records, with each stage's dense blocks folded into one product).
 static int exec_reg_pass(std::vector<cdd> &amp, const Plan &plan, size_t p) {
   const PlanPass &hp = plan.passes[p];
-  if (hp.kind != KIND_REG) return 3;
+  if (hp.kind != KIND_REG && hp.kind != KIND_TC) return 3;
   const uint8_t *base_ptr = plan.bytes.data();
   const RegPassParams &prm = plan.rparams[p];
   const uint32_t T = hp.T, c = hp.c, R = hp.R, NR = 1u << R, NT = 1u << (T - R), ns = hp.n_stages;
@@ -119,6 +142,23 @@ static int exec_reg_pass(std::vector<cdd> &amp, const Plan &plan, size_t p) {
         for (uint32_t tid = 0; tid < NT; tid++) {
           const uint32_t PB = (tt[s * NT + tid] >> 16) * 8u;
           for (uint32_t j = 0; j < NR; j++) v[tid][j] = xbuf[(st.xo[j] ^ PB) / 8u];
+        }
+      }
+      if (hp.kind == KIND_TC && (st.flags & 4u)) {  // the stage product, before its phase ops
+        if (NR != 16) return 3;
+        const float *bf = reinterpret_cast<const float *>(base_ptr + st.b_off);
+        for (uint32_t tid = 0; tid < NT; tid++) {
+          double A[32], D[32];
+          for (uint32_t j = 0; j < 16; j++) {
+            A[2 * j] = v[tid][j].real();
+            A[2 * j + 1] = v[tid][j].imag();
+          }
+          for (uint32_t nn = 0; nn < 32; nn++) {
+            double acc = 0;
+            for (uint32_t k = 0; k < 32; k++) acc += A[k] * (double(bf[nn * 32 + k]) + double(bf[1024 + nn * 32 + k]));
+            D[nn] = acc;
+          }
+          for (uint32_t j = 0; j < 16; j++) v[tid][j] = cdd(D[2 * j], D[2 * j + 1]);
         }
       }
       for (uint32_t o = st.op_begin; o < st.op_end; o++) {
@@ -265,6 +305,7 @@ int main(int argc, char **argv) {
   // chunk > 0: plan incrementally, `chunk` passes at a time (as sv_apply_circuit
   // streams its plan), and run the chunks' passes in order
   const int chunk = argc > 5 ? atoi(argv[5]) : 0;
+  o.precision = argc > 6 ? atoi(argv[6]) : 0;  // 1: tensor-core passes
   std::vector<Plan> plans;
   std::string err;
   if (chunk <= 0) {
@@ -300,17 +341,18 @@ int main(int argc, char **argv) {
   for (auto &x : a) x /= std::sqrt(nrm);
   b = a;
   for (auto &g : gates) apply_gate(a, n, g);
-  size_t total = 0;
+  size_t total = 0, n_tc = 0;
   for (const Plan &plan : plans)
     for (size_t p = 0; p < plan.passes.size(); p++, total++) {
+      n_tc += plan.passes[p].kind == KIND_TC;
       const int rc = plan.passes[p].kind == KIND_SMEM ? exec_smem_pass(b, plan, p) : exec_reg_pass(b, plan, p);
       if (rc) {
-        printf("pass %zu: %s\n", total, rc == 3 ? "tensor-core pass" : rc == 5 ? "unknown op" : "index out of range");
+        printf("pass %zu: %s\n", total, rc == 3 ? "unsupported pass" : rc == 5 ? "unknown op" : "index out of range");
         return rc;
       }
     }
   double e = 0;
   for (size_t i = 0; i < a.size(); i++) e = std::max(e, std::abs(a[i] - b[i]));
-  printf("plans %zu passes %zu maxerr %.3e\n", plans.size(), total, e);
+  printf("plans %zu passes %zu tensor-core %zu maxerr %.3e\n", plans.size(), total, n_tc, e);
   return e <= 1e-5 ? 0 : 2;
 }

@@ -123,6 +123,24 @@ def test_packed_passes_equal_gates(executor, k_max, T, c, variant):
     assert not bad, bad
 
 
+@pytest.mark.parametrize("k_max,T,c", [(4, 12, 5), (4, 11, 5), (2, 13, 5), (5, 12, 4), (4, 11, 3)])
+def test_packed_tensor_core_passes_equal_gates(executor, k_max, T, c):
+    """Tensor-core passes: each stage's dense blocks folded into one 16x16
+    product (the real embedding B), phase ops after it, no store-only stage
+    (the last stage stores whatever bits it holds), executed from the packed
+    records against gate-by-gate application."""
+    bad, n_tc = [], 0
+    for name, n, circ in EXEC_CASES:
+        r = subprocess.run([executor, str(k_max), str(T), str(c), "0", "0", "1"], input=_encode(n, circ),
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            bad.append(f"{name} n={n}: rc={r.returncode} {r.stdout.strip()}")
+        elif " tensor-core " in r.stdout:
+            n_tc += int(r.stdout.split(" tensor-core ")[1].split()[0])
+    assert not bad, bad
+    assert n_tc > 0
+
+
 @pytest.mark.parametrize("chunk", [1, 2, 3])
 def test_streamed_plan_chunks_compose(executor, chunk):
     """Planning a few passes at a time (as sv_apply_circuit streams its plan)
