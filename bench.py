@@ -676,6 +676,7 @@ def run_alias_mode(args):
 
 
 LARGE_QUBITS = 25  # requests from here on bound both serving paths by their device time
+SERVE_TC_FROM = 24  # both serving paths apply requests from here on with tensor-core passes
 
 
 def serving_sweep(count: int, factors, small_max: int) -> dict:
@@ -691,12 +692,12 @@ def serving_sweep(count: int, factors, small_max: int) -> dict:
     reqs0 = serve.make_requests(specs0, W.random_layered)
     for r in reqs0:
         r.t = 0.0
-    res0 = serve.run_plain(reqs0)
+    res0 = serve.run_plain(reqs0, tc_from_qubits=SERVE_TC_FROM)
     cap = serve.summarize(res0)
     n_of = {r.id: r.n for r in reqs0}
     large_s = sum(r.t_done - r.t_start for r in res0 if n_of[r.id] >= LARGE_QUBITS)
     n_large = sum(1 for r in reqs0 if r.n >= LARGE_QUBITS)
-    out = {"requests_per_point": count, "small_max_qubits": small_max,
+    out = {"requests_per_point": count, "small_max_qubits": small_max, "tensor_core_from_qubits": SERVE_TC_FROM,
            "plain_capacity_circuits_per_s": cap["circuits_per_s"],
            "amdahl_ceiling": {"ratio": cap["makespan_s"] / large_s if large_s > 0 else None,
                               "plain_makespan_s": cap["makespan_s"], "large_requests": n_large,
@@ -706,10 +707,10 @@ def serving_sweep(count: int, factors, small_max: int) -> dict:
         rate = f * cap["circuits_per_s"]
         specs = W.serving_requests(count, 4, rate)
         reqs = serve.make_requests(specs, W.random_layered)
-        res = serve.Server(small_max_qubits=small_max).run(reqs)
+        res = serve.Server(small_max_qubits=small_max, tc_from_qubits=SERVE_TC_FROM).run(reqs)
         srv = serve.summarize(res)
         srv["batched_requests"] = sum(1 for r in res if r.path == "batch")
-        pl = serve.summarize(serve.run_plain(reqs))
+        pl = serve.summarize(serve.run_plain(reqs, tc_from_qubits=SERVE_TC_FROM))
         out["points"].append({"rate_factor": f, "rate_hz": rate, "served": srv, "plain": pl,
                               "circuits_per_s_ratio": srv["circuits_per_s"] / pl["circuits_per_s"]})
     return out
@@ -751,7 +752,8 @@ def run_serve_mode(args):
     f = float(args.rate_factors.split(",")[-1])
     specs = W.serving_requests(count, 4, f * plain_cap)
     reqs = serve.make_requests(specs, W.random_layered)
-    spt = serve.summarize(serve.Server(small_max_qubits=args.serve_small_max, cost_model=model).run(reqs))
+    spt = serve.summarize(serve.Server(small_max_qubits=args.serve_small_max, cost_model=model,
+                                       tc_from_qubits=SERVE_TC_FROM).run(reqs))
     out["cost_model"] = {"calibration_s": cal_s, "held_out_abs_rel_err": [round(e, 3) for e in errs],
                          "rate_factor": f, "served_shortest_predicted_first": spt}
     best = max(p["circuits_per_s_ratio"] for p in out["points"])

@@ -16,10 +16,14 @@ either a shot count or a Z-string mask) arrive over time; the server
     their passes interleave on the device;
   * records arrival, start and finish times of every request;
   * with a calibrated cost model (costmodel.py, Eq. 1), admits waiting large
-    requests shortest predicted runtime first instead of fewest qubits first.
+    requests shortest predicted runtime first instead of fewest qubits first;
+  * with ``tc_from_qubits``, applies requests of at least that many qubits with
+    the tensor-core passes (``tc_opts``, precision 1) and smaller ones with
+    ``opts`` (on a GB300 the tensor-core path is faster from ~24 qubits; below,
+    planning and launches dominate a circuit and it is slightly slower).
 
 The plain path (``run_plain``) serves the same requests one at a time: create
-a state, apply, measure, destroy, on one stream.  Control is Python; every
+a state, apply, measure, destroy, on one stream, with the same per-size options.  Control is Python; every
 simulation step is a library call, and ctypes releases the GIL during each
 call so worker threads overlap.
 """
@@ -86,6 +90,15 @@ def make_requests(specs, circuit_fn):
     return reqs
 
 
+def default_tc_opts():
+    """Options of the tensor-core path: 3xTF32 stage products, blocks up to 4 qubits."""
+    return capi.make_opts(k_max=5, precision=1)
+
+
+def _opts_for(req: Request, opts, tc_opts, tc_from):
+    return tc_opts if (tc_from is not None and req.n >= tc_from) else opts
+
+
 def _run_single(req: Request, stream, opts, t0: float) -> Result:
     t_start = time.perf_counter() - t0
     with torch.cuda.stream(stream):
@@ -103,7 +116,8 @@ def _run_single(req: Request, stream, opts, t0: float) -> Result:
 
 class Server:
     def __init__(self, small_max_qubits: int = 14, streams: int = 8, hbm_budget: int | None = None,
-                 batch_max: int = 1024, opts=None, batch_opts=None, cost_model=None):
+                 batch_max: int = 1024, opts=None, batch_opts=None, cost_model=None,
+                 tc_from_qubits: int | None = None, tc_opts=None):
         self.small_max = small_max_qubits
         self.n_streams = streams
         if hbm_budget is None:
@@ -112,6 +126,8 @@ class Server:
         self.budget = hbm_budget
         self.batch_max = batch_max
         self.opts = opts if opts is not None else capi.make_opts()
+        self.tc_from = tc_from_qubits
+        self.tc_opts = tc_opts if tc_opts is not None else default_tc_opts()
         self.batch_opts = batch_opts or {}
         self.streams = queue.SimpleQueue()
         for _ in range(streams):
@@ -123,13 +139,16 @@ class Server:
     def predicted_ms(self, r: Request) -> float:
         """Cost-model runtime of a request (cached; planning on the host only)."""
         if r.id not in self._pred:
-            st = capi.sv_plan_stats_ir(r.n, r.ir, r.n_gates, self.opts)
+            st = capi.sv_plan_stats_ir(r.n, r.ir, r.n_gates, self._opts(r))
             ms = self.cost_model.apply_ms(r.n, st["n_passes"], self.cost_model.eff_flops(r.n, st),
                                           self.cost_model.dense_gates(r.ir, r.n_gates),
                                           self.cost_model.phase_amps(r.n, st))
             ms += self.cost_model.shots_ms(r.n, r.shots) if r.shots else self.cost_model.shots_ms(r.n, 0)
             self._pred[r.id] = ms
         return self._pred[r.id]
+
+    def _opts(self, r: Request):
+        return _opts_for(r, self.opts, self.tc_opts, self.tc_from)
 
     def _order_key(self, r: Request):
         if self.cost_model is None:
@@ -183,7 +202,7 @@ class Server:
                         raise ValueError(f"request {r.id} ({r.n} qubits) exceeds the HBM budget")
                     if used + need <= self.budget and not self.streams.empty():
                         st = self.streams.get()
-                        fut = pool.submit(_run_single, r, st, self.opts, t0)
+                        fut = pool.submit(_run_single, r, st, self._opts(r), t0)
                         inflight[fut] = ("single", need, st)
                         used += need
                         waiting_large.pop(i)
@@ -219,10 +238,11 @@ class Server:
         return sorted(results, key=lambda r: r.id)
 
 
-def run_plain(requests, opts=None, max_wall_s: float = 600.0):
+def run_plain(requests, opts=None, max_wall_s: float = 600.0, tc_from_qubits: int | None = None, tc_opts=None):
     """One circuit at a time, in arrival order, on one stream."""
     reqs = sorted(requests, key=lambda r: r.t)
     opts = opts if opts is not None else capi.make_opts()
+    tc_opts = tc_opts if tc_opts is not None else default_tc_opts()
     stream = torch.cuda.current_stream()
     results = []
     t0 = time.perf_counter()
@@ -232,7 +252,7 @@ def run_plain(requests, opts=None, max_wall_s: float = 600.0):
             raise TimeoutError(f"plain path did not finish in {max_wall_s} s")
         if r.t > now:
             time.sleep(r.t - now)
-        res = _run_single(r, stream, opts, t0)
+        res = _run_single(r, stream, _opts_for(r, opts, tc_opts, tc_from_qubits), t0)
         res.path = "plain"
         results.append(res)
     return sorted(results, key=lambda r: r.id)

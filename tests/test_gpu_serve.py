@@ -37,9 +37,12 @@ def _check_against_oracle(res, spec):
         assert abs(res.expect - oracle.expect_z(ref, spec["zmask"])) <= 1e-5
 
 
-def test_mix_equals_alone_and_oracle(S):
+@pytest.mark.parametrize("tc_from", [None, 14])
+def test_mix_equals_alone_and_oracle(S, tc_from):
+    # tc_from: requests of >= 14 qubits on the tensor-core passes, the rest of the
+    # stream path on CUDA cores
     reqs, specs = _requests(S, 40, 5, rate=400.0)
-    server = S.Server(small_max_qubits=12, streams=4)
+    server = S.Server(small_max_qubits=12, streams=4, tc_from_qubits=tc_from)
     mixed = server.run(reqs)
     assert {r.path for r in mixed} == {"batch", "stream"}
     for res, req, spec in zip(mixed, sorted(reqs, key=lambda r: r.id), sorted(specs, key=lambda s: s["id"])):
@@ -53,9 +56,10 @@ def test_mix_equals_alone_and_oracle(S):
         _check_against_oracle(res, spec)
 
 
-def test_plain_path_agrees(S):
+@pytest.mark.parametrize("tc_from", [None, 13])
+def test_plain_path_agrees(S, tc_from):
     reqs, specs = _requests(S, 16, 8, rate=1000.0, n_hi=16)
-    plain = S.run_plain(reqs)
+    plain = S.run_plain(reqs, tc_from_qubits=tc_from)
     for res, spec in zip(plain, sorted(specs, key=lambda s: s["id"])):
         _check_against_oracle(res, spec)
     s = S.summarize(plain)
