@@ -121,6 +121,11 @@ def _states():
     y = np.full(1 << n, 1.0, dtype=np.complex128)
     y[rng.integers(0, 1 << n, 150)] = 0.05
     yield "flat", y
+    # weights 3, 1, 1, 3 repeated: Q = 1.5 C, 0.5 C, 0.5 C, 1.5 C exactly, so deficit
+    # and excess prefixes tie (lights before heavies on ties decides the aliases)
+    for n in (2, 12):
+        t = np.tile(np.array([np.sqrt(3.0), 1.0, 1.0, np.sqrt(3.0)], dtype=np.complex128), 1 << (n - 2))
+        yield f"ties n={n}", t
 
 
 @pytest.mark.parametrize("name,psi", list(_states()), ids=lambda x: x if isinstance(x, str) else "")
