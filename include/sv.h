@@ -90,12 +90,15 @@ typedef struct sv_opts {
                           is a run of 2^c contiguous amplitudes (1..T; default 5) */
   int32_t precision;   /* 0 = FP32 CUDA cores for every block;
                           1 = 3xTF32 tensor cores (tcgen05): all dense blocks of a
-                          register stage as one 16x16 complex product; when every
-                          gate is unitary, ||psi||^2 is measured before the first
-                          pass and restored after the last (the tensor cores'
-                          float32 accumulation rounds toward zero, ~1e-7 of the
-                          norm per stage): two reads and one read+write of the
-                          state per sv_apply_circuit call */
+                          register stage as one 16x16 complex product (tiles of
+                          11..13 qubits; smaller states use the CUDA-core kernels);
+                          when every gate is unitary the passes track ||psi||^2
+                          (the tensor cores' float32 accumulation rounds toward
+                          zero, ~1e-7 of the norm per stage): the first tensor-core
+                          pass sums it on load, each pass on store, and each later
+                          pass rescales what it loads by sqrt(input / previous
+                          output), so only the last pass's drift remains -- no
+                          extra reads of the state */
   int32_t kernel_variant; /* 0 = amplitudes stay in registers across the ops of a
                           stage, shared memory only between stages (default): 32
                           amplitudes per thread when a pass's blocks have at most 2
