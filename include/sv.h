@@ -104,7 +104,14 @@ typedef struct sv_opts {
                           amplitudes per thread when a pass's blocks have at most 2
                           qubits and T <= 12, else 16;
                           1 = every op sweeps the shared-memory tile;
-                          2 = register stages with 16 amplitudes per thread */
+                          2 = register stages with 16 amplitudes per thread; with
+                          precision 1: blocks fused up to min(k_max, 5) qubits and
+                          5-qubit stages (32 x 32 complex products, 32 amplitudes
+                          per thread, T = 12 or 13) on every tensor-core pass whose
+                          records fit (at most four 32 KB stage images).  Without
+                          it, precision 1 uses 4-qubit stages, and 5-qubit stages
+                          only for a pass holding a 5-qubit block (a 5-qubit
+                          UNITARY gate) */
 } sv_opts;
 
 /* Statistics of the fusion + pass plan of a circuit (host-side only). */

@@ -22,6 +22,17 @@ extern "C" {
 int sv_tc_selftest(const float *a, const double *b, float *d);
 
 /*
+ * The same product for a stage of r register qubits (r = 4 or 5): K = 2^(r+1)
+ * columns, d[m][n] = sum_k a[m][k] * b[n][k] for m < 128, n, k < K, with a
+ * (float32, row-major 128 x K), b (double, row-major K x K) and d (128 x K
+ * floats) host memory owned by the caller.  r = 4 is sv_tc_selftest; r = 5 is
+ * the 64 x 64 real product of a 5-qubit stage (a 32 x 32 complex block), issued
+ * as 16 MMAs of N = 128 and N = 64.  Returns as sv_tc_selftest, and SV_ERR_ARG
+ * for another r.
+ */
+int sv_tc_selftest_r(int r, const float *a, const double *b, float *d);
+
+/*
  * Exercises the device-side timeout path without faulting or hanging the GPU:
  * one CTA waits on an mbarrier that nothing arrives on, with the same
  * %globaltimer bound the tensor-core kernels use (limit_ms in [1, 10000]).

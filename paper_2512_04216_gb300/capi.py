@@ -102,6 +102,7 @@ _SIGS = {
     "sv_version": ([], ctypes.c_char_p),
     "sv_launch_count": ([], ctypes.c_uint64),
     "sv_tc_selftest": ([_P, _P, _P], _i),
+    "sv_tc_selftest_r": ([_i, _P, _P, _P], _i),
     "sv_measure_qubit": ([_P, _i, ctypes.c_double, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_double)], _i),
     "sv_reset_qubit": ([_P, _i, ctypes.c_double, ctypes.POINTER(_i)], _i),
     "sv_clone": ([_P, _P, ctypes.POINTER(_P)], _i),
@@ -331,6 +332,18 @@ def sv_tc_selftest(a, b):
     assert a.shape == (128, 32) and b.shape == (32, 32)
     d = np.empty((128, 32), dtype=np.float32)
     _check(_L.sv_tc_selftest(a.ctypes.data, b.ctypes.data, d.ctypes.data))
+    return d
+
+
+def sv_tc_selftest_r(r, a, b):
+    """Tensor-core product check of an r-qubit stage (include/sv_diag.h):
+    a 128 x 2^(r+1) float32, b 2^(r+1) x 2^(r+1) float64."""
+    k = 2 << r
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    assert a.shape == (128, k) and b.shape == (k, k)
+    d = np.empty((128, k), dtype=np.float32)
+    _check(_L.sv_tc_selftest_r(int(r), a.ctypes.data, b.ctypes.data, d.ctypes.data))
     return d
 
 

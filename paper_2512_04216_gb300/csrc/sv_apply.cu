@@ -199,10 +199,10 @@ struct TcLayout {
   size_t off_in, off_x, off_tt, off_data, total;
 };
 
-__host__ __device__ inline TcLayout tc_layout(uint32_t T, uint32_t ns, uint32_t data_bytes) {
+__host__ __device__ inline TcLayout tc_layout(uint32_t T, uint32_t ns, uint32_t data_bytes, uint32_t R) {
   TcLayout r;
   r.L = 1u << T;
-  r.NT = 1u << (T - 4);
+  r.NT = 1u << (T - R);
   size_t o = 0;
   r.off_in = o; o += size_t(r.L) * 8;  // load buffer (natural order)
   r.off_x = o; o += size_t(r.L) * 8;   // exchange buffer (swizzled)
@@ -224,17 +224,18 @@ __device__ __forceinline__ void group_bar_sync(uint32_t g) {
   }
 }
 
-// Running sum of |a|^2 over a thread's tiles: each tile's 16 amplitudes in
+// Running sum of |a|^2 over a thread's tiles: each tile's row of amplitudes in
 // float32 pairs (re^2, im^2), then added to a float32 sum with its rounding
 // error kept in a second float (TwoSum, Knuth), so the sum over hundreds of tiles
 // keeps ~2^-44 relative accuracy without per-tile FP64 instructions (slow on this
 // part).  The pair goes to double once, at the end of the kernel.
 struct NormAcc {
   float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add_row(const float2 (&v)[16]) {
+  template <int NV>
+  __device__ __forceinline__ void add_row(const float2 (&v)[NV]) {
     float2 a = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int j = 0; j < 16; j++) a = __ffma2_rn(v[j], v[j], a);
+    for (int j = 0; j < NV; j++) a = __ffma2_rn(v[j], v[j], a);
     const float x = __fadd_rn(a.x, a.y);
     const float t = __fadd_rn(s, x);
     const float bp = __fsub_rn(t, s);
@@ -251,13 +252,17 @@ struct NormAcc {
   }
 };
 
-template <int NT>
-__global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
+// R = 4: 16 amplitudes a thread, T = 11, 12, 13 with 128, 256, 512 threads (3, 2,
+// 1 CTAs per SM); R = 5: 32 amplitudes a thread (5-qubit stages), T = 12, 13 with
+// 128, 256 threads.
+template <int NT, int R>
+__global__ void __launch_bounds__(NT, R == 5 ? 1 : (NT <= 128 ? 3 : (NT <= 256 ? 2 : 1)))
     k_pass_tc(float2 *__restrict__ amp, const uint8_t *__restrict__ plan, uint32_t pass_off,
               const __grid_constant__ RegPassParams prm, int *__restrict__ err, const TcNorm nrm) {
-  constexpr int NR = 16;  // R = 4 register qubits
-  constexpr uint32_t kT = NT == 128 ? 11u : (NT == 256 ? 12u : 13u);
+  constexpr int NR = 1 << R;  // amplitudes per thread
+  constexpr uint32_t kT = uint32_t(R) + (NT == 128 ? 7u : (NT == 256 ? 8u : 9u));
   constexpr uint32_t NG = NT / 128;
+  constexpr uint32_t kCols = tc_cols_per_group(R);
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar[NG];
   __shared__ uint32_t tbase_s;
@@ -267,11 +272,11 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
   const uint64_t outer_mask = P->outer_mask, n_tiles = P->n_tiles;
   // the launch's shared memory was sized from the host's copy of these fields
   if (T != kT || T != prm.chk[0] || ns != prm.chk[1] || data_bytes != prm.chk[2] || data_off != prm.chk[3] ||
-      P->R != 4u || P->kind != KIND_TC || ns == 0 || ns > uint32_t(kMaxStages)) {
+      P->R != uint32_t(R) || P->kind != KIND_TC || ns == 0 || ns > uint32_t(kMaxStages)) {
     if (threadIdx.x == 0) atomicOr(err, kPlanMismatch);
     return;
   }
-  const TcLayout lay = tc_layout(T, ns, data_bytes);
+  const TcLayout lay = tc_layout(T, ns, data_bytes, R);
   uint32_t *tt = reinterpret_cast<uint32_t *>(smem + lay.off_tt);
   uint8_t *data = smem + lay.off_data;
   const uint32_t tid = threadIdx.x, warp = tid >> 5, g = tid >> 7;
@@ -283,7 +288,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
   }
   fence_proxy_async_smem();  // stage images are read by the tensor cores
   if (warp == 0) {
-    tmem_alloc(&tbase_s, NT);  // 128 columns per row group
+    tmem_alloc(&tbase_s, NG * kCols);  // 4K columns per row group
     tmem_relinquish();
   }
   if (tid < NG) mbar_init(&bar[tid], 1);
@@ -295,7 +300,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
   // per-thread stage tables (own entries only): low 16 bits local index part, high 16 swizzled
   for (uint32_t s = 0; s < ns; s++) {
     uint32_t LB = 0;
-    for (uint32_t i = 0; i < T - 4; i++)
+    for (uint32_t i = 0; i < T - uint32_t(R); i++)
       if ((tid >> i) & 1u) LB |= 1u << stages[s].tb[i];
     tt[s * NT + tid] = LB | (swz(LB) << 16);
   }
@@ -304,7 +309,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
   constexpr int NK = NR / 2;  // 16-byte chunks per thread per tile
   const uint32_t sin = smem_u32(smem + lay.off_in), sx = smem_u32(smem + lay.off_x);
   const uint32_t tbase = tbase_s;
-  const uint32_t gcols = tbase + g * kTcColsPerGroup;
+  const uint32_t gcols = tbase + g * kCols;
   const uint32_t tq = gcols + (((warp & 3u) * 32u) << 16);  // this thread's lane
   const uint32_t t_ldx = (tt[tid] & 0xffffu) * 8u;
   uint64_t t_st = 0;
@@ -396,13 +401,13 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
         for (int j = 0; j < NR; j++) v[j] = lds64(sx + (xo[j] ^ PB));
       }
       if (st.flags & 4u) {
-        store_row_split(tq, v);
+        store_row_split<R>(tq, v);
         tmem_wait_st();
         tc_fence_before();
         group_bar_sync(g);  // the group's rows are in tensor memory
         if ((tid & 127u) == 0) {  // one thread issues and commits
           tc_fence_after();
-          issue_stage_mma(gcols, smem_u32(data + (st.b_off - data_off)));
+          issue_stage_mma<R>(gcols, smem_u32(data + (st.b_off - data_off)));
           mma_commit(&bar[g]);
         }
         // every thread of the group waits for the commit's phase itself (a
@@ -411,12 +416,12 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
         if (!mbar_wait_bounded(&bar[g], parity)) bad = true;
         parity ^= 1u;
         tc_fence_after();
-        load_row_sum(tq, v);
+        load_row_sum<R>(tq, v);
       }
       const uint32_t oe = st.op_end;
       for (uint32_t o = st.op_begin; o < oe; o++) {
         const OpRec op = ops[o];
-        reg_rphase<4>(v, data + (op.data_off - data_off), base, LB);
+        reg_rphase<R>(v, data + (op.data_off - data_off), base, LB);
       }
     }
     if (aborted) break;
@@ -432,7 +437,7 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tbase, NT);
+  if (warp == 0) tmem_dealloc(tbase, NG * kCols);
   if (tid == 0 && aborted) atomicOr(err, kTcErrTimeout);
   if (nrm.in_sum) acc_in.flush(nrm.in_sum);
   if (nrm.out_sum) acc_out.flush(nrm.out_sum);
@@ -440,57 +445,64 @@ __global__ void __launch_bounds__(NT, NT <= 128 ? 3 : (NT <= 256 ? 2 : 1))
 
 // Smallest dynamic shared memory that keeps (512 / TMEM columns) CTAs per SM at
 // most, so tcgen05.alloc never waits for a CTA that only finishes at the end.
-static size_t tc_smem_floor(uint32_t nt) {
+static size_t tc_smem_floor(uint32_t cols_per_cta) {
   const size_t per_sm = 233472;  // 228 KiB of shared memory per SM
-  const uint32_t ctas = 512u / nt;  // TMEM columns per CTA = nt
+  const uint32_t ctas = 512u / cols_per_cta;
   return per_sm / (ctas + 1) + 1024;
 }
 
-template <int NT>
+template <int NT, int R>
 static cudaError_t launch_tc(float2 *amp, const uint8_t *plan, uint32_t off, const PlanPass &hp,
                              const RegPassParams &prm, int *err, cudaStream_t st, const TcNorm &nrm) {
-  const TcLayout lay = tc_layout(hp.T, hp.n_stages, hp.data_bytes);
+  constexpr uint32_t cols = (NT / 128) * tc_cols_per_group(R);
+  const TcLayout lay = tc_layout(hp.T, hp.n_stages, hp.data_bytes, R);
   size_t smem = lay.total;
-  const size_t floor_ = tc_smem_floor(NT);
+  const size_t floor_ = tc_smem_floor(cols);
   if (smem < floor_) smem = floor_;
   if (smem + kTcStaticSmem > kSmemOptIn) return cudaErrorInvalidValue;
   static std::atomic<uint64_t> configured{0};
   static std::atomic<int> sms[64];
+  static std::atomic<int> regs{0};
   int dev = 0, nsm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = once_per_device(configured, sms, dev, [] {
-    cudaError_t r = cudaFuncSetAttribute(k_pass_tc<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t r = cudaFuncSetAttribute(k_pass_tc<NT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(kSmemOptIn - kTcStaticSmem));
     // all of the SM's unified memory as shared memory, so the occupancy below
     // (and the launch) can place two ~110 KB CTAs per SM
     if (r == cudaSuccess)
-      r = cudaFuncSetAttribute(k_pass_tc<NT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+      r = cudaFuncSetAttribute(k_pass_tc<NT, R>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                int(cudaSharedmemCarveoutMaxShared));
+    cudaFuncAttributes fa{};
+    if (r == cudaSuccess) r = cudaFuncGetAttributes(&fa, k_pass_tc<NT, R>);
+    if (r == cudaSuccess) regs.store(fa.numRegs, std::memory_order_relaxed);
     return r;
   }, &nsm);
   if (e != cudaSuccess) return e;
   // CTAs per SM: shared memory (228 KiB per SM, 1 KiB reserved per CTA), tensor
-  // memory (512 columns, NT per CTA) and registers (128 per thread).  The
-  // runtime's occupancy query is not used: it reported one CTA per SM for ~108 KB
-  // CTAs that fit twice.
+  // memory (512 columns) and registers (the kernel's count, allocated in
+  // 8-register steps).  The runtime's occupancy query is not used: it reported
+  // one CTA per SM for ~108 KB CTAs that fit twice.
+  const int nregs = std::max(8, (regs.load(std::memory_order_relaxed) + 7) & ~7);
   int per_sm = int(233472 / (smem + kTcStaticSmem + 1024));
-  per_sm = std::min(per_sm, int(512 / NT));
-  per_sm = std::min(per_sm, int(65536 / (NT * 128)));
+  per_sm = std::min(per_sm, int(512 / cols));
+  per_sm = std::min(per_sm, int(65536 / (NT * nregs)));
   if (per_sm < 1) per_sm = 1;
   if (nsm < 1) nsm = 1;
   const uint64_t want = uint64_t(nsm) * per_sm;
   const unsigned grid = unsigned(hp.n_tiles < want ? hp.n_tiles : want);
-  k_pass_tc<NT><<<grid, NT, smem, st>>>(amp, plan, off, prm, err, nrm);
+  k_pass_tc<NT, R><<<grid, NT, smem, st>>>(amp, plan, off, prm, err, nrm);
   count_launch();
   return cudaGetLastError();
 }
 
-bool tc_pass_fits(uint32_t T, uint32_t c, uint32_t n_stages, uint32_t data_bytes) {
-  if (T < 11 || T > 13 || T < c + 4 || c < 1 || n_stages < 1 || n_stages > uint32_t(kMaxStages) ||
-      data_bytes > kMaxPassData)
+bool tc_pass_fits(uint32_t T, uint32_t c, uint32_t n_stages, uint32_t data_bytes, uint32_t R) {
+  if (R != 4 && R != 5) return false;
+  if (T < R + 7 || T > R + (R == 4 ? 9 : 8) || T < c + R || c < 1 || n_stages < 1 ||
+      n_stages > uint32_t(kMaxStages) || data_bytes > kMaxPassData)
     return false;
-  return tc_layout(T, n_stages, data_bytes).total + kTcStaticSmem <= kSmemOptIn;
+  return tc_layout(T, n_stages, data_bytes, R).total + kTcStaticSmem <= kSmemOptIn;
 }
 
 static size_t pass_smem(uint32_t T, uint32_t c, int kmax) {
@@ -530,9 +542,14 @@ cudaError_t launch_pass(float2 *amp, const uint8_t *plan_dev, uint32_t pass_off,
   if (hp.kind == KIND_TC) {
     if (!prm || !err) return cudaErrorInvalidValue;
     const TcNorm nrm = norm ? *norm : TcNorm{};
-    if (hp.T == 11) return launch_tc<128>(amp, plan_dev, pass_off, hp, *prm, err, stream, nrm);
-    if (hp.T == 12) return launch_tc<256>(amp, plan_dev, pass_off, hp, *prm, err, stream, nrm);
-    if (hp.T == 13) return launch_tc<512>(amp, plan_dev, pass_off, hp, *prm, err, stream, nrm);
+    if (hp.R == 4) {
+      if (hp.T == 11) return launch_tc<128, 4>(amp, plan_dev, pass_off, hp, *prm, err, stream, nrm);
+      if (hp.T == 12) return launch_tc<256, 4>(amp, plan_dev, pass_off, hp, *prm, err, stream, nrm);
+      if (hp.T == 13) return launch_tc<512, 4>(amp, plan_dev, pass_off, hp, *prm, err, stream, nrm);
+    } else if (hp.R == 5) {
+      if (hp.T == 12) return launch_tc<128, 5>(amp, plan_dev, pass_off, hp, *prm, err, stream, nrm);
+      if (hp.T == 13) return launch_tc<256, 5>(amp, plan_dev, pass_off, hp, *prm, err, stream, nrm);
+    }
     return cudaErrorInvalidValue;
   }
   if (hp.kind == KIND_REG) {

@@ -931,14 +931,17 @@ int sv_alias_table(sv_state *s, uint64_t *out, uint64_t offset, uint64_t count, 
   return SV_OK;
 }
 
-int sv_tc_selftest(const float *a, const double *b, float *d) {
+int sv_tc_selftest_r(int r, const float *a, const double *b, float *d) {
+  if (r != 4 && r != 5) return fail(SV_ERR_ARG, "r must be 4 or 5");
   if (!a || !b || !d) return fail(SV_ERR_ARG, "null argument");
   int status = 0;
-  cudaError_t e = tc_selftest(a, b, d, &status);
+  cudaError_t e = tc_selftest(r, a, b, d, &status);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "tensor-core self-test");
   if (status) return fail(SV_ERR_TIMEOUT, "tensor-core self-test: the MMA completion wait gave up");
   return SV_OK;
 }
+
+int sv_tc_selftest(const float *a, const double *b, float *d) { return sv_tc_selftest_r(4, a, b, d); }
 
 int sv_diag_bounded_wait(int limit_ms) {
   if (limit_ms < 1 || limit_ms > 10000) return fail(SV_ERR_ARG, "limit_ms must be in [1, 10000]");

@@ -178,7 +178,7 @@ cudaError_t launch_pass(float2 *amp, const uint8_t *plan_dev, uint32_t pass_off,
                         const PlanPass &host_pass, const RegPassParams *reg_params, int *err,
                         cudaStream_t stream, const TcNorm *norm = nullptr);
 // Whether a tensor-core pass fits the kernel's shared memory.
-bool tc_pass_fits(uint32_t T, uint32_t c, uint32_t n_stages, uint32_t data_bytes);
+bool tc_pass_fits(uint32_t T, uint32_t c, uint32_t n_stages, uint32_t data_bytes, uint32_t R);
 // Whether a register-stage pass fits the persistent kernel's shared-memory tables.
 bool reg_pass_fits(uint32_t T, uint32_t c, uint32_t R, uint32_t n_stages, uint32_t data_bytes);
 

@@ -666,8 +666,9 @@ static StageRec make_stage(const HStage &hs, int T, int c, int Rb, bool load, bo
   return sr;
 }
 
-// U <- G * U for a 16x16 stage matrix U, G a k-qubit matrix on bit positions pos[].
-static void apply_on_positions(std::vector<cd> &U, const std::vector<cd> &G, int k, const int *pos) {
+// U <- G * U for an NU x NU stage matrix U (NU = 16 or 32), G a k-qubit matrix
+// on bit positions pos[].
+static void apply_on_positions(std::vector<cd> &U, int NU, const std::vector<cd> &G, int k, const int *pos) {
   const int KG = 1 << k;
   int gmask = 0;
   for (int x = 0; x < k; x++) gmask |= 1 << pos[x];
@@ -679,16 +680,16 @@ static void apply_on_positions(std::vector<cd> &U, const std::vector<cd> &G, int
     off[j] = o;
   }
   cd v[32], w[32];
-  for (int col = 0; col < 16; col++)
-    for (int r0 = 0; r0 < 16; r0++) {
+  for (int col = 0; col < NU; col++)
+    for (int r0 = 0; r0 < NU; r0++) {
       if (r0 & gmask) continue;
-      for (int j = 0; j < KG; j++) v[j] = U[size_t(r0 | off[j]) * 16 + col];
+      for (int j = 0; j < KG; j++) v[j] = U[size_t(r0 | off[j]) * NU + col];
       for (int r = 0; r < KG; r++) {
         cd a = 0.0;
         for (int j = 0; j < KG; j++) a += G[size_t(r) * KG + j] * v[j];
         w[r] = a;
       }
-      for (int r = 0; r < KG; r++) U[size_t(r0 | off[r]) * 16 + col] = w[r];
+      for (int r = 0; r < KG; r++) U[size_t(r0 | off[r]) * NU + col] = w[r];
     }
 }
 
@@ -698,12 +699,14 @@ static RegPassParams reg_params(const PlanPass &hp, const StageRec &first, const
                                 const int *outq);
 
 // `outq`: local bit -> physical qubit of the store; `rp` receives the kernel's
-// address tables and record checks.
+// address tables and record checks.  Rb: register qubits of a stage (4: 16x16
+// complex products, 5: 32x32).
 static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint32_t> &omask, const int *lpos,
                          int T, int c, const int *outq, PlanPass &hp, std::vector<uint8_t> &buf,
-                         RegPassParams &rp, sv_plan_info &info) {
+                         RegPassParams &rp, sv_plan_info &info, int Rb) {
+  const int NU = 1 << Rb, K = 2 * NU;
   std::vector<HStage> stages;
-  assign_stages(ops, omask, T, c, 4, stages, true);
+  assign_stages(ops, omask, T, c, Rb, stages, true);
   size_t nphase = 0, terms_bytes = 0, nmma = 0;
   for (auto &st : stages) {
     bool mma = false;
@@ -718,8 +721,9 @@ static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint3
     nmma += mma;
   }
   const size_t est = nphase * sizeof(OpRec) + terms_bytes + 16 * nphase + stages.size() * sizeof(StageRec) + 16 +
-                     nmma * kTcBImage + 16;
-  if (stages.size() > 64 || !tc_pass_fits(uint32_t(T), uint32_t(c), uint32_t(stages.size()), uint32_t(est)))
+                     nmma * tc_b_image_bytes(Rb) + 16;
+  if (stages.size() > 64 ||
+      !tc_pass_fits(uint32_t(T), uint32_t(c), uint32_t(stages.size()), uint32_t(est), uint32_t(Rb)))
     return false;
 
   align16(buf);
@@ -728,14 +732,14 @@ static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint3
   buf.resize(buf.size() + nphase * sizeof(OpRec), 0);
   std::vector<OpRec> recs;
   std::vector<StageRec> srecs;
-  std::vector<std::vector<double>> bmats;  // per MMA stage: B[n][k], 32x32
+  std::vector<std::vector<double>> bmats;  // per MMA stage: B[n][k], K x K
   uint32_t nterms = 0;
   for (size_t si = 0; si < stages.size(); si++) {
     const HStage &st = stages[si];
-    StageRec sr = make_stage(st, T, c, 4, si == 0, si + 1 == stages.size());
+    StageRec sr = make_stage(st, T, c, Rb, si == 0, si + 1 == stages.size());
     sr.op_begin = uint32_t(recs.size());
-    std::vector<cd> U(256, 0.0);
-    for (int d = 0; d < 16; d++) U[size_t(d) * 17] = 1.0;
+    std::vector<cd> U(size_t(NU) * NU, 0.0);
+    for (int d = 0; d < NU; d++) U[size_t(d) * (NU + 1)] = 1.0;
     bool mma = false;
     for (int o : st.ops) {
       const HostOp &op = ops[o];
@@ -752,7 +756,7 @@ static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint3
         const int k = op.blk.k();
         int pos[5];
         for (int m = 0; m < k; m++) pos[m] = popc(uint64_t(st.R & ((1u << lpos[op.blk.qs[m]]) - 1u)));
-        apply_on_positions(U, op.blk.M, k, pos);
+        apply_on_positions(U, NU, op.blk.M, k, pos);
         mma = true;
         info.n_blocks++;
         info.hist_k[k]++;
@@ -761,14 +765,14 @@ static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint3
     sr.op_end = uint32_t(recs.size());
     if (mma) {
       sr.flags |= 4u;
-      std::vector<double> B(32 * 32);
-      for (int r = 0; r < 16; r++)
-        for (int j = 0; j < 16; j++) {
-          const cd u = U[size_t(r) * 16 + j];
-          B[(2 * r) * 32 + 2 * j] = u.real();
-          B[(2 * r) * 32 + 2 * j + 1] = -u.imag();
-          B[(2 * r + 1) * 32 + 2 * j] = u.imag();
-          B[(2 * r + 1) * 32 + 2 * j + 1] = u.real();
+      std::vector<double> B(size_t(K) * K);
+      for (int r = 0; r < NU; r++)
+        for (int j = 0; j < NU; j++) {
+          const cd u = U[size_t(r) * NU + j];
+          B[size_t(2 * r) * K + 2 * j] = u.real();
+          B[size_t(2 * r) * K + 2 * j + 1] = -u.imag();
+          B[size_t(2 * r + 1) * K + 2 * j] = u.imag();
+          B[size_t(2 * r + 1) * K + 2 * j + 1] = u.real();
         }
       bmats.push_back(std::move(B));
     }
@@ -781,11 +785,11 @@ static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint3
   buf.resize(buf.size() + srecs.size() * sizeof(StageRec), 0);
   align16(buf);
   size_t bi = 0;
-  std::vector<uint8_t> img(kTcBImage);
+  std::vector<uint8_t> img(tc_b_image_bytes(Rb));
   for (auto &sr : srecs) {
     if (sr.flags & 4u) {
       sr.b_off = uint32_t(buf.size());
-      tc_b_image(bmats[bi++].data(), img.data());
+      tc_b_image(Rb, bmats[bi++].data(), img.data());
       put_bytes(buf, img.data(), img.size());
     }
   }
@@ -796,7 +800,7 @@ static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint3
   hp.n_stages = uint32_t(srecs.size());
   hp.n_phase_terms = nterms;
   hp.kind = KIND_TC;
-  hp.R = 4;
+  hp.R = uint32_t(Rb);
   rp = reg_params(hp, srecs.front(), srecs.back(), outq);
   rp.chk[0] = hp.T;
   rp.chk[1] = hp.n_stages;
@@ -930,7 +934,9 @@ bool PlanBuilder::init(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_
   }
   // kernel_variant: 0 = register stages where possible (32 amplitudes per
   // thread when the pass's blocks have at most 2 qubits and T <= 12, else 16),
-  // 1 = shared-memory sweeps, 2 = register stages with 16 amplitudes per thread
+  // 1 = shared-memory sweeps, 2 = register stages with 16 amplitudes per thread;
+  // with precision 1, variant 2 fuses up to 5 qubits and gives every
+  // tensor-core pass 5-qubit stages (32 amplitudes a thread)
   const bool o_smem = (o.kernel_variant == 1);
   if (o.kernel_variant < 0 || o.kernel_variant > 2) {
     err = "kernel_variant must be 0, 1 or 2";
@@ -1075,7 +1081,7 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
       }
       return w * (kx <= 2 ? 1.0 : (kx <= 4 ? 1.3 : 4.0));
     };
-    int kf = (o.precision == 1) ? std::min(kmax, 4) : std::min(kmax, 2);
+    int kf = (o.precision == 1) ? std::min(kmax, o.kernel_variant == 2 ? 5 : 4) : std::min(kmax, 2);
     // SWAPs of tile qubits become a relabeling of the store (register passes only)
     ph.relabeled = !o_smem && o.precision == 0;
     for (int q = 0; q < 64; q++) ph.rho[q] = q;
@@ -1161,9 +1167,14 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
       }
     bool store_natural = true;
     for (int q = 0; q < c; q++) store_natural &= store_lanes[size_t(q)] == q;
-    // tensor-core stages (precision 1) when the pass fits the TC kernel
-    if (o.precision == 1 && kmx <= 4 && !ph.relabeled &&
-        pack_tc_pass(ph.ops, omask, lpos, int(hp.T), c, outq, hp, buf, plan.rparams[p], plan.info)) {
+    // tensor-core stages (precision 1) when the pass fits the TC kernel: 4-qubit
+    // stages, or 5-qubit stages for a pass holding a 5-qubit block (or all
+    // passes with kernel variant 2), else 4-qubit ones if those fit
+    const int Rtc = (kmx == 5 || o.kernel_variant == 2) ? 5 : 4;
+    if (o.precision == 1 && kmx <= 5 && !ph.relabeled &&
+        (pack_tc_pass(ph.ops, omask, lpos, int(hp.T), c, outq, hp, buf, plan.rparams[p], plan.info, Rtc) ||
+         (Rtc == 5 && kmx <= 4 &&
+          pack_tc_pass(ph.ops, omask, lpos, int(hp.T), c, outq, hp, buf, plan.rparams[p], plan.info, 4)))) {
       hp.kmax = kmx;
       for (auto &op : ph.ops)
         if (op.type == OP_DENSE) plan.info.flops += uint64_t(amps * 8.0 * double(1 << op.blk.k()));

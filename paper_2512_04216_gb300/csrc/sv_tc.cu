@@ -1,12 +1,12 @@
 // sv_tc.cu -- tensor-core (tcgen05, 3xTF32) stage product: self-test and host helpers.
 //
-// A register stage of a pass (see StageRec) holds, in every thread, the 16
-// amplitudes of one "row": the 16 values of the stage's four register qubits
-// for the thread's fixed values of the other tile qubits.  All dense fused
-// blocks of the stage multiply into one 16x16 complex matrix U (built on the
-// host in complex128).  Applying it to the whole tile is the real GEMM
+// A register stage of a pass (see StageRec) holds, in every thread, the 2^R
+// amplitudes of one "row" (R = 4 or 5): the values of the stage's R register
+// qubits for the thread's fixed values of the other tile qubits.  All dense
+// fused blocks of the stage multiply into one 2^R x 2^R complex matrix U (built
+// on the host in complex128).  Applying it to the whole tile is the real GEMM
 //
-//     D[m][n] = sum_k A[m][k] * B[n][k],   m = row (thread), k, n < 32,
+//     D[m][n] = sum_k A[m][k] * B[n][k],   m = row (thread), k, n < K = 2^(R+1),
 //
 // with A[m][2j+c] = component c (re/im) of amplitude j of row m and B the real
 // embedding of U: B[2r][2j] = Re U[r][j], B[2r][2j+1] = -Im U[r][j],
@@ -21,13 +21,14 @@
 // so the tensor core's truncation of x_lo to TF32 has no systematic direction.
 //
 // Mapping to tcgen05 (per 128-row group):
-//   * A_hi, A_lo live in tensor memory (lane = row % 128, 32 columns each),
+//   * A_hi, A_lo live in tensor memory (lane = row % 128, K columns each),
 //     written by the threads with tcgen05.st;
-//   * B' = [B_hi ; B_lo] (per stage, 64 x 32, 8 KB) sits in shared memory in the
-//     canonical K-major layout without swizzle (8-row x 16-byte core matrices);
-//   * one thread issues the stage's 8 MMAs (issue_stage_mma): A_hi times B'
-//     (N = 64) gives A_hi B_hi in D_left and A_hi B_lo in D_right, then A_lo
-//     times B_hi (N = 32) accumulates into D_left; the threads add D_left and
+//   * B' = [B_hi ; B_lo] (per stage, 2K x K: 8 KB for R = 4, 32 KB for R = 5)
+//     sits in shared memory in the canonical K-major layout without swizzle
+//     (8-row x 16-byte core matrices);
+//   * one thread issues the stage's K/4 MMAs (issue_stage_mma): A_hi times B'
+//     (N = 2K) gives A_hi B_hi in D_left and A_hi B_lo in D_right, then A_lo
+//     times B_hi (N = K) accumulates into D_left; the threads add D_left and
 //     D_right (round to nearest) after tcgen05.ld;
 //   * every mbarrier wait is bounded by %globaltimer and reported, never trapped.
 #include <cstdint>
@@ -42,17 +43,19 @@ namespace svgb {
 
 // ---- self-test: one 128 x 32 x 32 product -----------------------------------------
 
+template <int R>
 __global__ void __launch_bounds__(128) k_tc_selftest(const float *__restrict__ A, const uint8_t *__restrict__ bimg,
                                                      float *__restrict__ D, int *__restrict__ status) {
-  __shared__ __align__(1024) uint8_t bsm[kTcBImage];
+  constexpr uint32_t K = tc_k(R), IMG = tc_b_image_bytes(R), COLS = tc_cols_per_group(R);
+  extern __shared__ __align__(1024) uint8_t bsm[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tbase_s;
   const uint32_t tid = threadIdx.x, warp = tid >> 5;
-  for (uint32_t i = tid; i < kTcBImage / 16; i += blockDim.x)
+  for (uint32_t i = tid; i < IMG / 16; i += blockDim.x)
     reinterpret_cast<uint4 *>(bsm)[i] = reinterpret_cast<const uint4 *>(bimg)[i];
   fence_proxy_async_smem();
   if (warp == 0) {
-    tmem_alloc(&tbase_s, 128);
+    tmem_alloc(&tbase_s, COLS);
     tmem_relinquish();
   }
   if (tid == 0) mbar_init(&bar, 1);
@@ -61,24 +64,24 @@ __global__ void __launch_bounds__(128) k_tc_selftest(const float *__restrict__ A
   tc_fence_after();
   const uint32_t tbase = tbase_s;
   const uint32_t tq = tbase + ((warp * 32u) << 16);
-  float2 v[16];
-  for (int j = 0; j < 16; j++) v[j] = make_float2(A[tid * 32 + 2 * j], A[tid * 32 + 2 * j + 1]);
-  store_row_split(tq, v);
+  float2 v[1 << R];
+  for (uint32_t j = 0; j < K / 2; j++) v[j] = make_float2(A[tid * K + 2 * j], A[tid * K + 2 * j + 1]);
+  store_row_split<R>(tq, v);
   tmem_wait_st();
   tc_fence_before();
   __syncthreads();
   if (tid == 0) {
     tc_fence_after();
-    issue_stage_mma(tbase, smem_u32(bsm));
+    issue_stage_mma<R>(tbase, smem_u32(bsm));
     mma_commit(&bar);
   }
   const bool ok = mbar_wait_bounded(&bar, 0);
   tc_fence_after();
   if (__syncthreads_and(ok)) {
-    load_row_sum(tq, v);
-    for (int j = 0; j < 16; j++) {
-      D[tid * 32 + 2 * j] = v[j].x;
-      D[tid * 32 + 2 * j + 1] = v[j].y;
+    load_row_sum<R>(tq, v);
+    for (uint32_t j = 0; j < K / 2; j++) {
+      D[tid * K + 2 * j] = v[j].x;
+      D[tid * K + 2 * j + 1] = v[j].y;
     }
     if (tid == 0) *status = 0;
   } else if (tid == 0) {
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(128) k_tc_selftest(const float *__restrict__ A
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tbase, 128);
+  if (warp == 0) tmem_dealloc(tbase, COLS);
 }
 
 // ---- bounded-wait check: an mbarrier that nothing arrives on -------------------------
@@ -128,44 +131,53 @@ static inline float tf32_rn(float f) {
   return r;
 }
 
-size_t tc_b_offset(int n, int k) {
+size_t tc_b_offset(int R, int n, int k) {
   const int ks = k >> 3, kk = k & 7;
-  return size_t(ks) * kTcBKStep + size_t(n >> 3) * 256 + size_t(kk >> 2) * 128 + size_t(n & 7) * 16 +
+  return size_t(ks) * tc_b_kstep(R) + size_t(n >> 3) * 256 + size_t(kk >> 2) * 128 + size_t(n & 7) * 16 +
          size_t(kk & 3) * 4;
 }
 
-void tc_b_image(const double *B, uint8_t *img) {
-  std::memset(img, 0, kTcBImage);
-  for (int n = 0; n < 32; n++)
-    for (int k = 0; k < 32; k++) {
-      const double x = B[n * 32 + k];
+void tc_b_image(int R, const double *B, uint8_t *img) {
+  const int K = int(tc_k(R));
+  std::memset(img, 0, tc_b_image_bytes(R));
+  for (int n = 0; n < K; n++)
+    for (int k = 0; k < K; k++) {
+      const double x = B[n * K + k];
       const float hi = tf32_rn(float(x));
       const float lo = tf32_rn(float(x - double(hi)));
-      std::memcpy(img + tc_b_offset(n, k), &hi, 4);
-      std::memcpy(img + tc_b_offset(n + 32, k), &lo, 4);
+      std::memcpy(img + tc_b_offset(R, n, k), &hi, 4);
+      std::memcpy(img + tc_b_offset(R, n + K, k), &lo, 4);
     }
 }
 
-cudaError_t tc_selftest(const float *A_host, const double *B_host, float *D_host, int *status_host) {
-  std::vector<uint8_t> img(kTcBImage);
-  tc_b_image(B_host, img.data());
+cudaError_t tc_selftest(int R, const float *A_host, const double *B_host, float *D_host, int *status_host) {
+  if (R != 4 && R != 5) return cudaErrorInvalidValue;
+  const uint32_t K = tc_k(R), IMG = tc_b_image_bytes(R);
+  std::vector<uint8_t> img(IMG);
+  tc_b_image(R, B_host, img.data());
+  const size_t abytes = size_t(128) * K * 4;
   float *dA = nullptr, *dD = nullptr;
   uint8_t *dB = nullptr;
   int *dS = nullptr;
-  cudaError_t e = cudaMalloc(&dA, 128 * 32 * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&dD, 128 * 32 * 4);
-  if (e == cudaSuccess) e = cudaMalloc(&dB, kTcBImage);
+  cudaError_t e = cudaMalloc(&dA, abytes);
+  if (e == cudaSuccess) e = cudaMalloc(&dD, abytes);
+  if (e == cudaSuccess) e = cudaMalloc(&dB, IMG);
   if (e == cudaSuccess) e = cudaMalloc(&dS, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemcpy(dA, A_host, 128 * 32 * 4, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(dB, img.data(), kTcBImage, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(dD, 0, 128 * 32 * 4);
+  if (e == cudaSuccess) e = cudaMemcpy(dA, A_host, abytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dB, img.data(), IMG, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(dD, 0, abytes);
   if (e == cudaSuccess) {
-    k_tc_selftest<<<1, 128>>>(dA, dB, dD, dS);
+    if (R == 4) {
+      k_tc_selftest<4><<<1, 128, IMG>>>(dA, dB, dD, dS);
+    } else {
+      e = cudaFuncSetAttribute(k_tc_selftest<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(IMG));
+      if (e == cudaSuccess) k_tc_selftest<5><<<1, 128, IMG>>>(dA, dB, dD, dS);
+    }
     count_launch();
-    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  if (e == cudaSuccess) e = cudaMemcpy(D_host, dD, 128 * 32 * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(D_host, dD, abytes, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(status_host, dS, sizeof(int), cudaMemcpyDeviceToHost);
   cudaFree(dA);
   cudaFree(dD);

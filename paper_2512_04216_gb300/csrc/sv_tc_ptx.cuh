@@ -120,25 +120,26 @@ __device__ __forceinline__ uint64_t b_desc(uint32_t saddr) {
          (uint64_t(1) << 46);
 }
 
-// Instruction descriptors: D f32, A/B tf32, both K-major, M=128, N=64 or N=32.
+// Instruction descriptors: D f32, A/B tf32, both K-major, M=128, N given.
 constexpr uint32_t kIdescTf32(uint32_t n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
 }
-constexpr uint32_t kIdescN64 = kIdescTf32(64);
-constexpr uint32_t kIdescN32 = kIdescTf32(32);
 
 // The 3xTF32 product of one stage for one 128-row group, issued by one thread:
-//   [D_left | D_right] = A_hi * [B_hi | B_lo]^T   (N = 64, 4 K steps)
-//   D_left            += A_lo * B_hi^T            (N = 32, 4 K steps)
+//   [D_left | D_right] = A_hi * [B_hi | B_lo]^T   (N = 2K, K/8 K steps)
+//   D_left            += A_lo * B_hi^T            (N = K, K/8 K steps)
 // so D_left + D_right = A_hi B_hi + A_lo B_hi + A_hi B_lo.  Stacking B_hi and
-// B_lo along N takes 8 MMAs per stage instead of 12.  cols: the group's TMEM
-// columns (A_hi at +0, A_lo at +32, D at +64); b_saddr: the stage image B'.
+// B_lo along N takes K/4 MMAs per stage instead of 3K/8.  cols: the group's
+// TMEM columns (A_hi at +0, A_lo at +K, D at +2K); b_saddr: the stage image B'.
+template <int R>
 __device__ __forceinline__ void issue_stage_mma(uint32_t cols, uint32_t b_saddr) {
-  const uint32_t a_hi = cols, a_lo = cols + 32, d = cols + 64;
+  constexpr uint32_t K = tc_k(R), KS = K / 8, STEP = tc_b_kstep(R);
+  const uint32_t a_hi = cols, a_lo = cols + K, d = cols + 2 * K;
 #pragma unroll
-  for (uint32_t ks = 0; ks < 4; ks++) mma_tf32_ts(d, a_hi + 8 * ks, b_desc(b_saddr + ks * kTcBKStep), kIdescN64, ks > 0);
+  for (uint32_t ks = 0; ks < KS; ks++)
+    mma_tf32_ts(d, a_hi + 8 * ks, b_desc(b_saddr + ks * STEP), kIdescTf32(2 * K), ks > 0);
 #pragma unroll
-  for (uint32_t ks = 0; ks < 4; ks++) mma_tf32_ts(d, a_lo + 8 * ks, b_desc(b_saddr + ks * kTcBKStep), kIdescN32, 1);
+  for (uint32_t ks = 0; ks < KS; ks++) mma_tf32_ts(d, a_lo + 8 * ks, b_desc(b_saddr + ks * STEP), kIdescTf32(K), 1);
 }
 
 // Veltkamp splitting (Dekker 1971) of a float pair: with c = x * (2^13 + 1),
@@ -154,34 +155,45 @@ __device__ __forceinline__ void split_pair(float2 x, float2 &hi, float2 &lo) {
   lo = __ffma2_rn(hi, m1, x);              // x - hi
 }
 
-// Split the 16 amplitudes of a row and store A_hi, A_lo (32 columns each,
-// interleaved re, im) at TMEM address a (this thread's lane).
-__device__ __forceinline__ void store_row_split(uint32_t a, const float2 (&v)[16]) {
-  uint32_t h[32], l[32];
+// Split the 2^R amplitudes of a row and store A_hi, A_lo (K columns each,
+// interleaved re, im) at TMEM address a (this thread's lane), 16 amplitudes
+// (32 columns) at a time.
+template <int R>
+__device__ __forceinline__ void store_row_split(uint32_t a, const float2 (&v)[1 << R]) {
+  constexpr uint32_t K = tc_k(R);
 #pragma unroll
-  for (int j = 0; j < 16; j++) {
-    float2 hi, lo;
-    split_pair(v[j], hi, lo);
-    h[2 * j] = __float_as_uint(hi.x);
-    h[2 * j + 1] = __float_as_uint(hi.y);
-    l[2 * j] = __float_as_uint(lo.x);
-    l[2 * j + 1] = __float_as_uint(lo.y);
+  for (uint32_t hh = 0; hh < K / 32; hh++) {
+    uint32_t h[32], l[32];
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+      float2 hi, lo;
+      split_pair(v[16 * hh + j], hi, lo);
+      h[2 * j] = __float_as_uint(hi.x);
+      h[2 * j + 1] = __float_as_uint(hi.y);
+      l[2 * j] = __float_as_uint(lo.x);
+      l[2 * j + 1] = __float_as_uint(lo.y);
+    }
+    tmem_st32(a + 32 * hh, h);
+    tmem_st32(a + K + 32 * hh, l);
   }
-  tmem_st32(a, h);
-  tmem_st32(a + 32, l);
 }
 
-// Read D_left, D_right of this thread's lane (columns 64.. of the group) and
-// return their sum (round to nearest) as 16 amplitudes.
-__device__ __forceinline__ void load_row_sum(uint32_t a, float2 (&v)[16]) {
-  uint32_t dl[32], dr[32];
-  tmem_ld32(a + 64, dl);
-  tmem_ld32(a + 96, dr);
-  tmem_wait_ld();
+// Read D_left, D_right of this thread's lane (columns 2K.. of the group) and
+// return their sum (round to nearest) as 2^R amplitudes, 16 at a time.
+template <int R>
+__device__ __forceinline__ void load_row_sum(uint32_t a, float2 (&v)[1 << R]) {
+  constexpr uint32_t K = tc_k(R);
 #pragma unroll
-  for (int j = 0; j < 16; j++)
-    v[j] = __fadd2_rn(make_float2(__uint_as_float(dl[2 * j]), __uint_as_float(dl[2 * j + 1])),
-                      make_float2(__uint_as_float(dr[2 * j]), __uint_as_float(dr[2 * j + 1])));
+  for (uint32_t hh = 0; hh < K / 32; hh++) {
+    uint32_t dl[32], dr[32];
+    tmem_ld32(a + 2 * K + 32 * hh, dl);
+    tmem_ld32(a + 3 * K + 32 * hh, dr);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 16; j++)
+      v[16 * hh + j] = __fadd2_rn(make_float2(__uint_as_float(dl[2 * j]), __uint_as_float(dl[2 * j + 1])),
+                                  make_float2(__uint_as_float(dr[2 * j]), __uint_as_float(dr[2 * j + 1])));
+  }
 }
 
 }  // namespace svgb

@@ -6,8 +6,8 @@
 #include <random>
 // device-side helpers the planner links against; not used by fuse_pass
 namespace svgb {
-bool tc_pass_fits(uint32_t, uint32_t, uint32_t, uint32_t) { return false; }
-void tc_b_image(const double *, uint8_t *) {}
+bool tc_pass_fits(uint32_t, uint32_t, uint32_t, uint32_t, uint32_t) { return false; }
+void tc_b_image(int, const double *, uint8_t *) {}
 bool reg_pass_fits(uint32_t, uint32_t, uint32_t, uint32_t, uint32_t) { return true; }
 }
 using namespace svgb;

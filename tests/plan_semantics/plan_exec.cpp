@@ -18,26 +18,29 @@
 #include <random>
 
 // Device-side helpers the planner links against.  The stage image here holds
-// B as float pairs (hi = float(B), lo = float(B - hi)), [hi 32 x 32 | lo 32 x 32]
-// row-major in n: the interpreter checks what the planner computes and packs
-// (stages, their matrices, offsets), not the tensor cores' operand layout,
-// which the GPU self-test of the stage product covers.
+// B (K x K, K = 2^(R+1)) as float pairs (hi = float(B), lo = float(B - hi)),
+// [hi K x K | lo K x K] row-major in n: the interpreter checks what the planner
+// computes and packs (stages, their matrices, offsets), not the tensor cores'
+// operand layout, which the GPU self-test of the stage product covers.
 namespace svgb {
-bool tc_pass_fits(uint32_t T, uint32_t c, uint32_t n_stages, uint32_t data_bytes) {
-  // the kernel's limits: 11 <= T <= 13, shared memory = load + exchange buffers
-  // (8 B an amplitude each), the per-thread stage tables, the pass's records
-  if (T < 11 || T > 13 || T < c + 4 || c < 1 || n_stages < 1 || n_stages > 64 || data_bytes > 160u * 1024u)
+bool tc_pass_fits(uint32_t T, uint32_t c, uint32_t n_stages, uint32_t data_bytes, uint32_t R) {
+  // the kernel's limits: R = 4 with 11 <= T <= 13, R = 5 with 12 <= T <= 13;
+  // shared memory = load + exchange buffers (8 B an amplitude each), the
+  // per-thread stage tables, the pass's records
+  if ((R != 4 && R != 5) || T < R + 7 || T > R + (R == 4 ? 9 : 8) || T < c + R || c < 1 || n_stages < 1 ||
+      n_stages > 64 || data_bytes > 160u * 1024u)
     return false;
-  const size_t L = size_t(1) << T, NT = L >> 4;
+  const size_t L = size_t(1) << T, NT = L >> R;
   size_t o = 16 * L + size_t(n_stages) * NT * 4;
   o = (o + 15) & ~size_t(15);
   return o + data_bytes + 1024 <= 232448;
 }
-void tc_b_image(const double *B, uint8_t *img) {
+void tc_b_image(int R, const double *B, uint8_t *img) {
+  const int K = 2 << R;
   float *f = reinterpret_cast<float *>(img);
-  for (int i = 0; i < 32 * 32; i++) {
+  for (int i = 0; i < K * K; i++) {
     f[i] = float(B[i]);
-    f[1024 + i] = float(B[i] - double(f[i]));
+    f[K * K + i] = float(B[i] - double(f[i]));
   }
 }
 bool reg_pass_fits(uint32_t, uint32_t, uint32_t, uint32_t, uint32_t) { return true; }
@@ -145,20 +148,21 @@ static int exec_reg_pass(std::vector<cdd> &amp, const Plan &plan, size_t p) {
         }
       }
       if (hp.kind == KIND_TC && (st.flags & 4u)) {  // the stage product, before its phase ops
-        if (NR != 16) return 3;
+        if (NR != 16 && NR != 32) return 3;
+        const uint32_t K = 2 * NR;
         const float *bf = reinterpret_cast<const float *>(base_ptr + st.b_off);
         for (uint32_t tid = 0; tid < NT; tid++) {
-          double A[32], D[32];
-          for (uint32_t j = 0; j < 16; j++) {
+          double A[64], D[64];
+          for (uint32_t j = 0; j < NR; j++) {
             A[2 * j] = v[tid][j].real();
             A[2 * j + 1] = v[tid][j].imag();
           }
-          for (uint32_t nn = 0; nn < 32; nn++) {
+          for (uint32_t nn = 0; nn < K; nn++) {
             double acc = 0;
-            for (uint32_t k = 0; k < 32; k++) acc += A[k] * (double(bf[nn * 32 + k]) + double(bf[1024 + nn * 32 + k]));
+            for (uint32_t k = 0; k < K; k++) acc += A[k] * (double(bf[nn * K + k]) + double(bf[K * K + nn * K + k]));
             D[nn] = acc;
           }
-          for (uint32_t j = 0; j < 16; j++) v[tid][j] = cdd(D[2 * j], D[2 * j + 1]);
+          for (uint32_t j = 0; j < NR; j++) v[tid][j] = cdd(D[2 * j], D[2 * j + 1]);
         }
       }
       for (uint32_t o = st.op_begin; o < st.op_end; o++) {
@@ -286,6 +290,8 @@ int main(int argc, char **argv) {
   int n, ng;
   if (scanf("%d %d", &n, &ng) != 2) return 1;
   std::vector<sv_gate> ir(static_cast<size_t>(ng));
+  std::vector<std::vector<double>> mats;  // UNITARY gates: the matrices after their parameters
+  mats.reserve(static_cast<size_t>(ng));
   for (int i = 0; i < ng; i++) {
     sv_gate g{};
     int kind, nq;
@@ -295,6 +301,12 @@ int main(int argc, char **argv) {
     for (int x = 0; x < nq; x++)
       if (scanf("%d", &g.q[x]) != 1) return 1;
     if (scanf("%lf %lf %lf", &g.p[0], &g.p[1], &g.p[2]) != 3) return 1;
+    if (kind == SV_GATE_UNITARY) {
+      mats.emplace_back(size_t(2) << (2 * nq));
+      for (double &x : mats.back())
+        if (scanf("%lf", &x) != 1) return 1;
+      g.mat = mats.back().data();
+    }
     ir[size_t(i)] = g;
   }
   sv_opts o{};

@@ -174,3 +174,50 @@ def test_tc_norm_tracking_keeps_input_norm(sv):
     ref = oracle.run(n, circ, psi0.astype(np.complex128))
     err = float(np.max(np.abs(g - ref)))
     assert err <= AMP_TOL, err
+
+
+def test_tc_product_r5_matches_fp64(sv):
+    # the 5-qubit stage product: 128 x 64 times 64 x 64 (16 MMAs of N = 128 and 64)
+    rng = np.random.default_rng(3)
+    for scale in (1.0, 1e-3):
+        a = (rng.standard_normal((128, 64)) * scale).astype(np.float32)
+        b = rng.standard_normal((64, 64))
+        d = sv.capi.sv_tc_selftest_r(5, a, b)
+        want = a.astype(np.float64) @ b.T
+        bound = np.abs(a.astype(np.float64)) @ np.abs(b).T
+        err = np.abs(d - want)
+        assert np.all(err <= 2e-6 * bound + 1e-30), float(np.max(err / bound))
+    # r = 4 through the same entry point equals sv_tc_selftest
+    a4 = rng.standard_normal((128, 32)).astype(np.float32)
+    b4 = rng.standard_normal((32, 32))
+    assert np.array_equal(sv.capi.sv_tc_selftest_r(4, a4, b4), sv.capi.sv_tc_selftest(a4, b4))
+
+
+@pytest.mark.parametrize("T", [12, 13])
+def test_tc_five_qubit_stages(sv, T):
+    # kernel variant 2: blocks fused up to 5 qubits and 5-qubit stages (32 x 32
+    # complex products) on every tensor-core pass that fits
+    n = 16
+    circ = W.random_layered(n, 12, 23)
+    info = sv.capi.sv_plan_stats(n, circ, sv.capi.make_opts(5, T, 5, 1, 2))
+    assert info["tc_stages"] > 0 and info["hist_k"][5] > 0
+    _compare(_run(sv, n, circ, k_max=5, tile_qubits=T, kernel_variant=2), oracle.run(n, circ), f"R=5 T={T}")
+
+
+@pytest.mark.parametrize("depth", [1, 2])
+def test_tc_five_qubit_unitaries(sv, depth):
+    # 5-qubit UNITARY gates: a pass holding such a block takes 5-qubit
+    # tensor-core stages when its records fit (at most four 32 KB stage
+    # images), else the shared-memory kernel; depth 1 plans both passes as
+    # 5-qubit tensor-core passes, depth 2 one of each
+    n = 14
+    rng = np.random.default_rng(8)
+    circ = W.random_layered(n, depth, 41)
+    for _ in range(2):
+        qs = tuple(int(x) for x in rng.choice(n, 5, replace=False))
+        z = rng.standard_normal((32, 32)) + 1j * rng.standard_normal((32, 32))
+        u, _ = np.linalg.qr(z)
+        circ.insert(int(rng.integers(0, len(circ) + 1)), ("unitary", qs, (u,)))
+    info = sv.capi.sv_plan_stats(n, circ, sv.capi.make_opts(4, 12, 5, 1))
+    assert info["tc_stages"] > 0 and info["hist_k"][5] == 2
+    _compare(_run(sv, n, circ, k_max=4, tile_qubits=12), oracle.run(n, circ), "5-qubit unitaries")

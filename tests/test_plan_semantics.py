@@ -9,14 +9,15 @@ terms, relabeling, blocks kept open past queued diagonal gates) and the
 shared-memory pass's fusion, at fusion widths 2 and 5.
 
 tests/plan_semantics/plan_exec.cpp goes further: it plans with build_plan and
-executes the packed register-stage passes the way the register kernel reads
-their records (load rows, stage thread bits and swizzled exchange offsets,
-register-position matrices, phase classes, the store's qubit map), so the
-packing is checked on the host too."""
+executes the packed register-stage and tensor-core passes the way the kernels
+read their records (load rows, stage thread bits and swizzled exchange offsets,
+register-position matrices or stage products, phase classes, the store's qubit
+map), so the packing is checked on the host too."""
 import os
 import shutil
 import subprocess
 
+import numpy as np
 import pytest
 
 import workloads as W
@@ -59,9 +60,17 @@ def executor(tmp_path_factory):
 
 
 def _encode(n, circuit):
+    """kind nq qubits p0 p1 p2 per gate; a UNITARY gate's parameter is its
+    matrix, written after three zeros as row-major (re, im) pairs."""
     from paper_2512_04216_gb300 import capi  # gate kind numbers only (no library call)
     lines = [f"{n} {len(circuit)}"]
     for name, qs, ps in circuit:
+        if name == "unitary":
+            m = np.asarray(ps[0], dtype=np.complex128).reshape(-1)
+            flat = np.stack([m.real, m.imag], axis=1).reshape(-1)
+            lines.append(" ".join(map(str, [capi.GATE_KIND[name], len(qs), *qs, 0.0, 0.0, 0.0]))
+                         + " " + " ".join(repr(float(x)) for x in flat))
+            continue
         ps = list(ps) + [0.0] * (3 - len(ps))
         lines.append(" ".join(map(str, [capi.GATE_KIND[name], len(qs), *qs, *ps[:3]])))
     return "\n".join(lines) + "\n"
@@ -103,10 +112,24 @@ def test_fused_pass_equals_gates(checker, pairs, kmax):
     assert not bad, bad
 
 
+def _wide_unitary_circuit(n, seed):
+    """Random layers with 5-qubit UNITARY gates among them (a pass holding such
+    a block takes 5-qubit tensor-core stages)."""
+    rng = np.random.default_rng(seed)
+    circ = W.random_layered(n, 4, seed)
+    for _ in range(3):
+        qs = tuple(int(x) for x in rng.choice(n, 5, replace=False))
+        z = rng.standard_normal((32, 32)) + 1j * rng.standard_normal((32, 32))
+        u, _ = np.linalg.qr(z)
+        circ.insert(int(rng.integers(0, len(circ) + 1)), ("unitary", qs, (u,)))
+    return circ
+
+
 EXEC_CASES = ([("qft", 13, W.qft(13)), ("qft", 14, W.qft(14)), ("ghz", 14, W.ghz(14)),
                ("random_layered", 14, W.random_layered(14, 12, 3)), ("random_layered", 12, W.random_layered(12, 8, 4))]
               + [("gate_soup", 13, W.random_gate_soup(13, 160, s)) for s in range(4)]
               + [("interleaved", 12, _interleaved(12, s)) for s in range(3)])
+WIDE_CASES = [("wide_unitary", 13, _wide_unitary_circuit(13, s)) for s in range(2)]
 
 
 @pytest.mark.parametrize("k_max,T,c,variant", [(2, 12, 5, 0), (5, 12, 5, 0), (4, 11, 5, 2), (2, 10, 5, 0),
@@ -123,15 +146,17 @@ def test_packed_passes_equal_gates(executor, k_max, T, c, variant):
     assert not bad, bad
 
 
-@pytest.mark.parametrize("k_max,T,c", [(4, 12, 5), (4, 11, 5), (2, 13, 5), (5, 12, 4), (4, 11, 3)])
-def test_packed_tensor_core_passes_equal_gates(executor, k_max, T, c):
+@pytest.mark.parametrize("k_max,T,c,variant", [(4, 12, 5, 0), (4, 11, 5, 0), (2, 13, 5, 0), (5, 12, 4, 0),
+                                               (4, 11, 3, 0), (5, 12, 5, 2), (5, 13, 5, 2), (3, 12, 4, 2)])
+def test_packed_tensor_core_passes_equal_gates(executor, k_max, T, c, variant):
     """Tensor-core passes: each stage's dense blocks folded into one 16x16
-    product (the real embedding B), phase ops after it, no store-only stage
-    (the last stage stores whatever bits it holds), executed from the packed
-    records against gate-by-gate application."""
+    product (32x32 with 5-qubit stages: variant 2, or a pass holding a
+    5-qubit block), the real embedding B, phase ops after it, no store-only
+    stage (the last stage stores whatever bits it holds), executed from the
+    packed records against gate-by-gate application."""
     bad, n_tc = [], 0
-    for name, n, circ in EXEC_CASES:
-        r = subprocess.run([executor, str(k_max), str(T), str(c), "0", "0", "1"], input=_encode(n, circ),
+    for name, n, circ in EXEC_CASES + WIDE_CASES:
+        r = subprocess.run([executor, str(k_max), str(T), str(c), str(variant), "0", "1"], input=_encode(n, circ),
                            capture_output=True, text=True)
         if r.returncode != 0:
             bad.append(f"{name} n={n}: rc={r.returncode} {r.stdout.strip()}")
