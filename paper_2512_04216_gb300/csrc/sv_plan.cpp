@@ -527,14 +527,14 @@ struct HStage {
 // Greedy, in op order: a stage takes every op whose earlier unplaced ops do not
 // share a bit with it and whose bits fit the stage's Rb register bits.  Phase
 // ops need no register bits.  The first stage avoids the c low bits (it loads
-// with the low bits on the lanes), and for register passes a store stage is
-// appended when the last stage holds a low bit.  With `tc` the dense ops of a
-// stage become one product applied before the stage's phase ops, so a dense op
-// that touches a bit of an accepted phase op waits for a later stage; and the
-// last stage stores whatever bits it holds (no store stage: an appended stage
-// costs a whole-tile exchange through shared memory, more than the partly
-// filled 32-byte sectors of a store whose lanes skip some low bits, which L2
-// merges before they reach DRAM).
+// with the low bits on the lanes).  The last stage stores whatever bits it
+// holds: no store-only stage is appended (it would cost a whole-tile exchange
+// through shared memory, more than the partly filled 32-byte sectors of a store
+// whose lanes skip some low bits, which L2 merges before they reach DRAM),
+// except for a single-stage pass whose SWAPs relabel the store's low qubits.
+// With `tc` the dense ops of a stage become one product applied before the
+// stage's phase ops, so a dense op that touches a bit of an accepted phase op
+// waits for a later stage.
 // `store_low` (default: the c low bits) is the set of local bits that the store
 // puts on the lanes; it differs from the load's low bits when SWAPs relabel qubits
 // (`store_natural` false: the store lanes are not local bits 0..c-1 in order, so a
@@ -578,11 +578,11 @@ static void assign_stages(const std::vector<HostOp> &ops, const std::vector<uint
     first = false;
   }
   if (st.empty()) st.push_back(HStage{});
-  if (!tc && ((st.back().R & store_low) || (st.size() == 1 && !store_natural))) st.push_back(HStage{});
+  (void)store_low;
+  if (st.size() == 1 && !store_natural && !tc) st.push_back(HStage{});
   for (size_t i = 0; i < st.size(); i++) {
     uint32_t allowed = all;
     if (i == 0) allowed &= ~low;
-    if (i + 1 == st.size() && !tc) allowed &= ~store_low;
     for (int b = T - 1; b >= 0 && popc(uint64_t(st[i].R)) < Rb; b--)
       if (((allowed >> b) & 1u) && !((st[i].R >> b) & 1u)) st[i].R |= 1u << b;
   }
@@ -600,7 +600,10 @@ static StageRec make_stage(const HStage &hs, int T, int c, int Rb, bool load, bo
   for (int b = 0; b < T; b++)
     if (!((hs.R >> b) & 1u)) rest.push_back(b);
   std::vector<int> tb;
-  if (store && !load && store_lanes) {
+  bool lanes_free = store_lanes != nullptr;  // no store lane held in registers
+  if (store_lanes)
+    for (int b : *store_lanes) lanes_free &= !((hs.R >> b) & 1u);
+  if (store && !load && lanes_free) {
     tb = *store_lanes;  // output qubits 0..c-1 on the lanes, then the rest ascending
     for (int b : rest)
       if (std::find(tb.begin(), tb.end(), b) == tb.end()) tb.push_back(b);
