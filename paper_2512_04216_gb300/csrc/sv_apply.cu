@@ -173,13 +173,14 @@ bool reg_pass_fits(uint32_t T, uint32_t c, uint32_t R, uint32_t n_stages, uint32
 
 
 // ---------------------------------------------------------------------------
-// tensor-core stages (KIND_TC): the register-stage skeleton with 16 amplitudes
-// per thread (R = 4) and each stage's dense blocks applied as one 3xTF32
-// tcgen05 product (sv_tc.cu).  Per stage and 128-row group, the threads split
-// their rows into A_hi / A_lo in tensor memory, one thread of the group issues
-// the stage's 8 MMAs and commits them to the group's mbarrier, and the group
-// reads D back.  Between stages the tile moves through one swizzled exchange
-// buffer with one CTA barrier per exchange: a thread writes its amplitudes back
+// tensor-core stages (KIND_TC): the register-stage skeleton with 2^R amplitudes
+// per thread (R = 4; R = 5 for 5-qubit stages) and each stage's dense blocks
+// applied as one 3xTF32 tcgen05 product (sv_tc.cu).  Per stage and 128-row
+// group, the threads split their rows into A_hi / A_lo in tensor memory, one
+// thread of the group issues the stage's MMAs (8 for R = 4, 16 for R = 5) and
+// commits them to the group's mbarrier, and the group reads D back.  Between
+// stages the tile moves through one swizzled exchange buffer with one plain
+// CTA barrier per exchange: a thread writes its amplitudes back
 // to exactly the positions it read them from at the previous stage, which no
 // other thread reads, so no barrier is needed before the writes.  The next tile
 // is prefetched (16-byte cp.async, natural order) into a separate load buffer as
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(NT, R == 5 ? 1 : (NT <= 128 ? 3 : (NT <= 256 ?
   }
   fence_proxy_async_smem();  // stage images are read by the tensor cores
   if (warp == 0) {
-    tmem_alloc(&tbase_s, NG * kCols);  // 4K columns per row group
+    tmem_alloc(&tbase_s, NG * kCols);  // 4 x 2^(R+1) columns per row group
     tmem_relinquish();
   }
   if (tid < NG) mbar_init(&bar[tid], 1);
