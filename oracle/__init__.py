@@ -76,6 +76,8 @@ class Oracle:
         L.orc_sample.argtypes = [P, u64, P, u64, ctypes.c_double, P, P]
         L.orc_sample.restype = u64
         L.orc_expect_z.argtypes = [P, u64, u64]
+        L.orc_expect_pauli.argtypes = [P, ctypes.c_int, u64, u64, P, P]
+        L.orc_expect_pauli.restype = ctypes.c_int
         L.orc_measure.argtypes = [P, u64, ctypes.c_int, ctypes.c_double, P]
         L.orc_measure.restype = ctypes.c_int
         L.orc_reset_qubit.argtypes = [P, u64, ctypes.c_int, ctypes.c_double]
@@ -161,6 +163,16 @@ class Oracle:
         return float(self.L.orc_expect_z(psi.ctypes.data, psi.shape[0], int(zmask)))
 
 
+    def expect_pauli(self, psi, x_mask: int, z_mask: int) -> complex:
+        """<psi|P|psi>/<psi|psi> for P = X^x Z^z with Y on qubits in both masks."""
+        psi = np.ascontiguousarray(psi, dtype=np.complex128)
+        n = int(psi.shape[0]).bit_length() - 1
+        re, im = ctypes.c_double(), ctypes.c_double()
+        if self.L.orc_expect_pauli(psi.ctypes.data, n, int(x_mask), int(z_mask), ctypes.byref(re),
+                                   ctypes.byref(im)) != 0:
+            raise MemoryError("oracle: no memory for the Pauli copy")
+        return complex(re.value, im.value)
+
     def measure(self, psi, q: int, u: float):
         """Mid-circuit measurement of qubit q: returns (outcome, prob, collapsed copy)."""
         psi = np.array(psi, dtype=np.complex128, copy=True)
@@ -243,6 +255,7 @@ def cdf(psi): return default().cdf(psi)
 def sample(psi, uniforms, eps=1e-9): return default().sample(psi, uniforms, eps)
 def sample_cdf(C, uniforms, eps=1e-9): return default().sample_cdf(C, uniforms, eps)
 def expect_z(psi, zmask): return default().expect_z(psi, zmask)
+def expect_pauli(psi, x_mask, z_mask): return default().expect_pauli(psi, x_mask, z_mask)
 def measure(psi, q, u): return default().measure(psi, q, u)
 def reset_qubit(psi, q, u): return default().reset_qubit(psi, q, u)
 def kron(a, b): return default().kron(a, b)

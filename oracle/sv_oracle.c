@@ -303,6 +303,42 @@ double orc_expect_z(const cplx *psi, uint64_t N, uint64_t zmask) {
   return num / den;
 }
 
+/* Expectation of a Pauli string (cached-state expectation values, §III-B):
+ * qubit q carries I, X, Z or Y when (bit q of x_mask, bit q of z_mask) is
+ * (0,0), (1,0), (0,1) or (1,1).  The definition written out: phi = P psi by
+ * applying each qubit's 2x2 Pauli matrix (X = [[0,1],[1,0]], Y = [[0,-i],[i,0]],
+ * Z = [[1,0],[0,-1]]) with orc_apply_matrix, then <P> = <psi|phi> / <psi|psi>,
+ * both sums sequential in complex128.  *out_re, *out_im receive <P> (the
+ * imaginary part is 0 up to rounding: P is Hermitian).  Returns 0, or -1 when
+ * the copy cannot be allocated. */
+int orc_expect_pauli(const cplx *psi, int n, uint64_t x_mask, uint64_t z_mask, double *out_re,
+                     double *out_im) {
+  const uint64_t N = 1ull << n;
+  cplx *phi = (cplx *)malloc(N * sizeof(cplx));
+  if (!phi) return -1;
+  memcpy(phi, psi, N * sizeof(cplx));
+  const cplx X[4] = {0, 1, 1, 0};
+  const cplx Y[4] = {0, -I, I, 0};
+  const cplx Z[4] = {1, 0, 0, -1};
+  for (int q = 0; q < n; q++) {
+    const int xb = (int)((x_mask >> q) & 1u), zb = (int)((z_mask >> q) & 1u);
+    const int32_t t = q;
+    if (xb && zb) orc_apply_matrix(phi, n, 1, &t, Y);
+    else if (xb) orc_apply_matrix(phi, n, 1, &t, X);
+    else if (zb) orc_apply_matrix(phi, n, 1, &t, Z);
+  }
+  cplx num = 0;
+  double den = 0.0;
+  for (uint64_t i = 0; i < N; i++) {
+    num += conj(psi[i]) * phi[i];
+    den += creal(psi[i]) * creal(psi[i]) + cimag(psi[i]) * cimag(psi[i]);
+  }
+  free(phi);
+  *out_re = creal(num) / den;
+  *out_im = cimag(num) / den;
+  return 0;
+}
+
 /* Mid-circuit measurement of qubit q with uniform u: collapses psi in place and
  * returns the outcome; *prob = m_outcome / (m_0 + m_1). */
 int orc_measure(cplx *psi, uint64_t N, int q, double u, double *prob) {

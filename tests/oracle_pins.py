@@ -347,6 +347,50 @@ def pin_expectation(o):
         assert abs(o.expect_z(v, m) - want) < 1e-12, f"kron <Z_{m}>"
 
 
+def pin_expect_pauli(o):
+    """<X^x Z^z> (Y where both masks hold the qubit) against eigenstates, Bell
+    and GHZ closed forms, the Z-only routine, and Kronecker-built Pauli
+    matrices with textbook X, Y, Z on random states."""
+    s2 = 1 / math.sqrt(2)
+    plus = np.array([s2, s2], dtype=np.complex128)
+    minus = np.array([s2, -s2], dtype=np.complex128)
+    plus_i = np.array([s2, 1j * s2], dtype=np.complex128)
+    minus_i = np.array([s2, -1j * s2], dtype=np.complex128)
+    for psi, x, z, want in ((plus, 1, 0, 1), (minus, 1, 0, -1), (plus_i, 1, 1, 1), (minus_i, 1, 1, -1),
+                            (plus, 1, 1, 0), (plus_i, 1, 0, 0), (np.array([1, 0], np.complex128), 0, 1, 1),
+                            (np.array([0, 1], np.complex128), 0, 1, -1), (np.array([1, 0], np.complex128), 1, 0, 0)):
+        got = o.expect_pauli(psi, x, z)
+        assert abs(got - want) < 1e-12, ("eigenstate", x, z, got)
+    bell = o.run(2, [("h", (0,), ()), ("cx", (0, 1), ())])
+    for x, z, want in ((3, 0, 1), (3, 3, -1), (0, 3, 1), (1, 0, 0), (3, 1, 0)):
+        got = o.expect_pauli(bell, x, z)
+        assert abs(got - want) < 1e-12, ("bell XX / YY / ZZ", x, z, got)
+    n = 6
+    g = o.run(n, W.ghz(n))
+    assert abs(o.expect_pauli(g, (1 << n) - 1, 0) - 1) < 1e-12, "GHZ <X...X> = 1"
+    # GHZ: <Y^{⊗2} X^{⊗(n-2)}> = -1 (two Y's: i^2 from Y = iXZ on the |1..1> branch)
+    assert abs(o.expect_pauli(g, (1 << n) - 1, 3) + 1) < 1e-12, "GHZ <YYXXXX> = -1"
+    rng = np.random.default_rng(12)
+    X = np.array([[0, 1], [1, 0]], dtype=np.complex128)
+    Y = np.array([[0, -1j], [1j, 0]], dtype=np.complex128)
+    Z = np.diag([1.0, -1.0]).astype(np.complex128)
+    for n in (1, 3, 5):
+        v = random_state(n, rng) * 0.7
+        for _ in range(12):
+            x, z = int(rng.integers(0, 1 << n)), int(rng.integers(0, 1 << n))
+            mats = []
+            for q in range(n - 1, -1, -1):  # qubit 0 is the last Kronecker factor
+                xb, zb = (x >> q) & 1, (z >> q) & 1
+                mats.append(Y if (xb and zb) else X if xb else Z if zb else np.eye(2))
+            Pm = _kron_all(mats)
+            want = np.vdot(v, Pm @ v) / np.vdot(v, v)
+            got = o.expect_pauli(v, x, z)
+            assert abs(got - want) < 1e-12, ("kron", n, x, z, got, want)
+            if x == 0:
+                assert abs(got.real - o.expect_z(v, z)) < 1e-12, "Z-only routine"
+            assert abs(got.imag) < 1e-12, "Hermitian: real expectation"
+
+
 def pin_validate(o):
     assert o.validate(3, [("cx", (0, 2), ())])
     assert not o.validate(3, [("cx", (0, 3), ())]), "qubit out of range accepted"
@@ -547,5 +591,5 @@ def pin_alias(o):
 
 
 ALL_PINS = [pin_gate_identities, pin_kron_bruteforce, pin_apply_matrix_k5, pin_ghz, pin_qft,
-            pin_norm_and_mirror, pin_norm_sum, pin_sampler, pin_expectation, pin_validate,
-            pin_measure, pin_pblock, pin_alias]
+            pin_norm_and_mirror, pin_norm_sum, pin_sampler, pin_expectation, pin_expect_pauli,
+            pin_validate, pin_measure, pin_pblock, pin_alias]

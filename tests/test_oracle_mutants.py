@@ -47,6 +47,10 @@ MUTANTS = {
                            "(f * 2147483648.0 < (double)own[i]) ? alias[i] : i"),
     "alias_converted_keeps_full": ("own[heavy[j]] = (uint32_t)r;", "own[heavy[j]] = (uint32_t)C;"),
     "alias_plain_running_sum": ("  W += comp;", "  (void)comp;"),
+    "pauli_y_sign": ("const cplx Y[4] = {0, -I, I, 0};", "const cplx Y[4] = {0, I, -I, 0};"),
+    "pauli_x_as_z": ("else if (xb) orc_apply_matrix(phi, n, 1, &t, X);", "else if (xb) orc_apply_matrix(phi, n, 1, &t, Z);"),
+    "pauli_no_conjugate": ("num += conj(psi[i]) * phi[i];", "num += psi[i] * phi[i];"),
+    "pauli_unnormalised": ("*out_re = creal(num) / den;", "*out_re = creal(num);"),
 }
 
 
