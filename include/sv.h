@@ -3,7 +3,7 @@
  *
  * The library keeps a 2^n complex amplitude vector resident in GPU memory,
  * applies a circuit given as a flat gate IR, and returns amplitudes,
- * probabilities, measurement samples or Z-string expectation values.  This is
+ * probabilities, measurement samples or Pauli-string expectation values.  This is
  * the "circuit IR in; samples, expectations or amplitudes out" interface of
  * the paper's state-vector backend (§III-A common IR, §II state-vector method,
  * §III-B end-of-circuit sampling and cached-state expectation values).
@@ -259,9 +259,15 @@ int sv_alias_table(sv_state *s, uint64_t *out, uint64_t offset, uint64_t count, 
 int sv_alias_release(sv_state *s);
 
 /*
- * Expectation of the Pauli string X^x_mask Z^z_mask (cached-state expectation
- * values, §III-B): <Z_mask> = sum_i |a_i|^2 (-1)^popcount(i & z_mask) / ||psi||^2.
- * x_mask != 0 returns SV_ERR_UNSUPPORTED.
+ * Expectation of a Pauli string (cached-state expectation values, §III-B):
+ * qubit q carries I, X, Z or Y when (bit q of x_mask, bit q of z_mask) is (0,0),
+ * (1,0), (0,1) or (1,1); *out = <psi|P|psi> / ||psi||^2 (real: P is Hermitian).
+ * With x_mask = 0, <Z_mask> = sum_i |a_i|^2 (-1)^popcount(i & z_mask) / ||psi||^2;
+ * otherwise P = i^k X^x_mask Z^z_mask (k = popcount(x_mask & z_mask)) is summed
+ * over index pairs (i, i ^ x_mask).  One read of the state, products split
+ * error-free and summed in compensated float32 per thread and double across
+ * threads.  Masks with bits at or above n_qubits: SV_ERR_ARG; a zero norm:
+ * SV_ERR_ARG.  Synchronises the state's stream.
  */
 int sv_expect_pauli(sv_state *s, uint64_t x_mask, uint64_t z_mask, double *out);
 

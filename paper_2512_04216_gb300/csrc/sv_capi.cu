@@ -510,19 +510,25 @@ int sv_expect_pauli(sv_state *s, uint64_t x_mask, uint64_t z_mask, double *out) 
   CHECK_STATE(s);
   if (!out) return fail(SV_ERR_ARG, "out is null");
   if ((x_mask | z_mask) >> s->n) return fail(SV_ERR_ARG, "mask has bits beyond n_qubits");
-  if (x_mask) return fail(SV_ERR_UNSUPPORTED, "X/Y Pauli components are not supported");
   DeviceGuard g(s->device);
   int rc = ensure_reduce(s);
   if (rc) return rc;
-  CK(s, timed(s, "reduce", double(size_t(8) << s->n), [&] {
-       return launch_reduce_pz(s->amp, s->n, z_mask, s->ms.part, s->ms.n_part, s->dscal, s->stream);
-     }));
+  if (x_mask) {
+    CK(s, timed(s, "reduce", double(size_t(8) << s->n), [&] {
+         return launch_reduce_pauli(s->amp, s->n, x_mask, z_mask, s->ms.part, s->ms.n_part, s->dscal,
+                                    s->stream);
+       }));
+  } else {
+    CK(s, timed(s, "reduce", double(size_t(8) << s->n), [&] {
+         return launch_reduce_pz(s->amp, s->n, z_mask, s->ms.part, s->ms.n_part, s->dscal, s->stream);
+       }));
+  }
   CK(s, cudaMemcpyAsync(s->hscal, s->dscal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   CK(s, cudaStreamSynchronize(s->stream));
   rc = check_device_error(s);
   if (rc) return rc;
   if (!(s->hscal[0] > 0.0)) return fail(SV_ERR_ARG, "state has zero norm");
-  *out = s->hscal[1] / s->hscal[0];
+  *out = (x_mask ? 2.0 * s->hscal[1] : s->hscal[1]) / s->hscal[0];
   return SV_OK;
 }
 

@@ -196,6 +196,10 @@ constexpr int kBlockBits = 12;  // 4096 amplitudes = 64 chunks
 
 cudaError_t launch_reduce_pz(const float2 *amp, int n, uint64_t zmask, double *part,
                              size_t n_part, double *out2, cudaStream_t st);
+// <X^x Z^z> with x_mask != 0 (Y on qubits in both masks), one read of the state:
+// out2[0] = sum |psi|^2, out2[1] = half of <psi|P|psi> (see sv_measure.cu).
+cudaError_t launch_reduce_pauli(const float2 *amp, int n, uint64_t x_mask, uint64_t z_mask, double *part,
+                                size_t n_part, double *out2, cudaStream_t st);
 // Builds the CDF; with ztotal_dev, the same read also writes
 // sum p_i * (-1)^popcount(i & zmask) to ztotal_dev[0].
 cudaError_t launch_build_cdf(const float2 *amp, int n, MeasureScratch &ms, double *total_dev,

@@ -223,7 +223,93 @@ cudaError_t launch_reduce_pz(const float2 *amp, int n, uint64_t zmask, double *p
   return cudaGetLastError();
 }
 
-// ---- norm restoration --------------------------------------------------------
+// ---- Pauli-string expectation (x_mask != 0) ----------------------------------
+// P = i^k X^x Z^z (Y = iXZ on the qubits in both masks, k = popcount(x & z)), so
+// (P psi)_i = i^k (-1)^popcount((i^x) & z) psi_(i^x).  Over a pair (i, j = i ^ x),
+// i with x's lowest set bit b clear, the two terms of <psi|P psi> add to
+//   2 s_i Re(w) i^k (k even)  or  2i s_i Im(w) i^k (k odd),
+// w = conj(psi_i) psi_j, s_i = (-1)^popcount(j & z): a real number.  Each
+// amplitude is read once; the products are split error-free (fma) and summed
+// with the compensated float32 accumulators, per CTA in double.
+// part[2*c] = sum |psi|^2, part[2*c+1] = sum over the CTA's pairs of the real
+// factor times Re(w) or Im(w); <P> = 2 part_sum[1] / part_sum[0].
+constexpr int kPauliPairs = 8;  // pairs per thread
+
+__global__ void __launch_bounds__(kRT) k_reduce_pauli(const float2 *__restrict__ amp, int n, uint64_t x,
+                                                      uint64_t z, int b, int k, double *__restrict__ part) {
+  __shared__ double red[2][kRT / 32];
+  const uint64_t half = (uint64_t(1) << n) >> 1;  // pairs
+  const uint64_t m0 = uint64_t(blockIdx.x) * (kRT * kPauliPairs);
+  const uint64_t lowb = (uint64_t(1) << b) - 1u;
+  float2 ai[kPauliPairs], aj[kPauliPairs];
+  uint64_t jj[kPauliPairs];
+#pragma unroll
+  for (int r = 0; r < kPauliPairs; r++) {
+    const uint64_t m = m0 + uint64_t(r) * kRT + threadIdx.x;
+    const uint64_t i = ((m & ~lowb) << 1) | (m & lowb);
+    jj[r] = i ^ x;
+    if (m < half) {
+      ai[r] = amp[i];
+      aj[r] = amp[jj[r]];
+    } else {
+      ai[r] = aj[r] = make_float2(0.f, 0.f);
+    }
+  }
+  // the real factor: (-1)^(k/2) on Re(w) for even k, -(-1)^((k-1)/2) on Im(w) for odd k
+  const bool odd = k & 1;
+  const bool neg = odd ? !(((k - 1) >> 1) & 1) : (((k >> 1) & 1) != 0);
+  float ps = 0.f, pc = 0.f, qs = 0.f, qc = 0.f;
+#pragma unroll
+  for (int r = 0; r < kPauliPairs; r++) {
+    acc_sq(ps, pc, ai[r].x);
+    acc_sq(ps, pc, ai[r].y);
+    acc_sq(ps, pc, aj[r].x);
+    acc_sq(ps, pc, aj[r].y);
+    // Re(w) = ai.x aj.x + ai.y aj.y ; Im(w) = ai.x aj.y - ai.y aj.x
+    const float u1 = ai[r].x, v1 = odd ? aj[r].y : aj[r].x;
+    const float u2 = ai[r].y, v2 = odd ? -aj[r].x : aj[r].y;
+    const float h1 = __fmul_rn(u1, v1), l1 = fmaf(u1, v1, -h1);
+    const float h2 = __fmul_rn(u2, v2), l2 = fmaf(u2, v2, -h2);
+    const bool flip = neg != ((__popcll(jj[r] & z) & 1) != 0);
+    two_sum_acc(qs, qc, flip ? -h1 : h1);
+    two_sum_acc(qs, qc, flip ? -h2 : h2);
+    const float l = __fadd_rn(l1, l2);
+    qc = __fadd_rn(qc, flip ? -l : l);
+  }
+  warp_acc_pair(ps, pc);
+  warp_acc_pair(qs, qc);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][w] = cs_to_double(ps, pc);
+    red[1][w] = cs_to_double(qs, qc);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, c = 0.0;
+    for (int i = 0; i < kRT / 32; i++) {
+      a += red[0][i];
+      c += red[1][i];
+    }
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = c;
+  }
+}
+
+cudaError_t launch_reduce_pauli(const float2 *amp, int n, uint64_t x_mask, uint64_t z_mask, double *part,
+                                size_t n_part, double *out2, cudaStream_t st) {
+  if (x_mask == 0 || n < 1) return cudaErrorInvalidValue;
+  const uint64_t pairs = (uint64_t(1) << n) >> 1;
+  const uint64_t per = uint64_t(kRT) * kPauliPairs;
+  const size_t ctas = size_t((pairs + per - 1) / per);
+  if (ctas > n_part) return cudaErrorInvalidValue;
+  const int b = __builtin_ctzll(x_mask);
+  const int k = __builtin_popcountll(x_mask & z_mask);
+  k_reduce_pauli<<<unsigned(ctas), kRT, 0, st>>>(amp, n, x_mask, z_mask, b, k, part);
+  k_sum_pairs<<<1, 1024, 0, st>>>(part, ctas, out2);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
 // ---- CDF --------------------------------------------------------------------
 // Chunk sums (64 amplitudes; four threads each) and 4096-amplitude block sums;
 // with zblock, also the block's sum of p * (-1)^popcount(i & zmask), from the

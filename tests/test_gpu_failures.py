@@ -46,7 +46,7 @@ def test_bad_arguments_are_rejected(P):
     capi = P.capi
     s = P.StateVector(6)
     for fn in (lambda: capi.sv_reset(s.h, 1 << 6),
-               lambda: capi.sv_expect_pauli(s.h, 1, 0),
+               lambda: capi.sv_expect_pauli(s.h, 1 << 6, 0),
                lambda: capi.sv_probabilities(s.h, np.empty(4), 62, 4, False),
                lambda: capi.sv_create(0),
                lambda: capi.sv_create(8, capi.SV_C128)):
