@@ -253,11 +253,11 @@ struct NormAcc {
   }
 };
 
-// R = 4: 16 amplitudes a thread, T = 11, 12, 13 with 128, 256, 512 threads (3, 2,
-// 1 CTAs per SM); R = 5: 32 amplitudes a thread (5-qubit stages), T = 12, 13 with
-// 128, 256 threads.
+// R = 4: 16 amplitudes a thread, T = 11, 12, 13 with 128, 256, 512 threads (4, 2,
+// 1 CTAs per SM: at most 128 registers a thread); R = 5: 32 amplitudes a thread
+// (5-qubit stages), T = 12, 13 with 128, 256 threads.
 template <int NT, int R>
-__global__ void __launch_bounds__(NT, R == 5 ? 1 : (NT <= 128 ? 3 : (NT <= 256 ? 2 : 1)))
+__global__ void __launch_bounds__(NT, R == 5 ? 1 : (NT <= 128 ? 4 : (NT <= 256 ? 2 : 1)))
     k_pass_tc(float2 *__restrict__ amp, const uint8_t *__restrict__ plan, uint32_t pass_off,
               const __grid_constant__ RegPassParams prm, int *__restrict__ err, const TcNorm nrm) {
   constexpr int NR = 1 << R;  // amplitudes per thread
@@ -312,7 +312,9 @@ __global__ void __launch_bounds__(NT, R == 5 ? 1 : (NT <= 128 ? 3 : (NT <= 256 ?
   const uint32_t tbase = tbase_s;
   const uint32_t gcols = tbase + g * kCols;
   const uint32_t tq = gcols + (((warp & 3u) * 32u) << 16);  // this thread's lane
-  const uint32_t t_ldx = (tt[tid] & 0xffffu) * 8u;
+  // the load buffer is swizzled (swzl): the first stage reads local index l at
+  // swzl(l) = swzl(thread part) ^ swzl(register part); 16-byte chunk q lands at swzl(2q)
+  const uint32_t t_ldx = swzl(tt[tid] & 0xffffu) * 8u;
   uint64_t t_st = 0;
   {
     const uint32_t LB = tt[(ns - 1) * NT + tid] & 0xffffu;
@@ -320,12 +322,14 @@ __global__ void __launch_bounds__(NT, R == 5 ? 1 : (NT <= 128 ? 3 : (NT <= 256 ?
       if ((LB >> x) & 1u) t_st |= uint64_t(1) << prm.oq[x];
   }
   const uint64_t t_cp = pdep_u64(tid >> cs, hm) + (uint64_t(tid & cmask) << 1);
+  const uint32_t t_sd = swzl(2u * tid) * 8u;  // chunks tid + k * NT: swzl(2 k NT) xor-ed in per k
 
   uint64_t tile = blockIdx.x;
   uint64_t base = tile < n_tiles ? pdep_u64(tile, outer_mask) : 0;
   if (tile < n_tiles) {
 #pragma unroll
-    for (int k = 0; k < NK; k++) cp_async16_s(sin + (tid + k * NT) * 16u, amp + base + t_cp + prm.ko[k]);
+    for (int k = 0; k < NK; k++)
+      cp_async16_s(sin + (t_sd ^ (swzl(2u * uint32_t(k) * NT) * 8u)), amp + base + t_cp + prm.ko[k]);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
   uint32_t parity = 0;
@@ -349,7 +353,7 @@ __global__ void __launch_bounds__(NT, R == 5 ? 1 : (NT <= 128 ? 3 : (NT <= 256 ?
       break;
     }
 #pragma unroll
-    for (int j = 0; j < NR; j++) v[j] = lds64(sin + t_ldx + prm.lo[j]);
+    for (int j = 0; j < NR; j++) v[j] = lds64(sin + (t_ldx ^ prm.lo[j]));
     if (nrm.in_sum) acc_in.add_row(v);
     if (delta != 0.f) {
       const float2 d2 = make_float2(delta, delta);
@@ -363,7 +367,8 @@ __global__ void __launch_bounds__(NT, R == 5 ? 1 : (NT <= 128 ? 3 : (NT <= 256 ?
       }
       if (next < n_tiles) {
 #pragma unroll
-        for (int k = 0; k < NK; k++) cp_async16_s(sin + (tid + k * NT) * 16u, amp + base_next + t_cp + prm.ko[k]);
+        for (int k = 0; k < NK; k++)
+          cp_async16_s(sin + (t_sd ^ (swzl(2u * uint32_t(k) * NT) * 8u)), amp + base_next + t_cp + prm.ko[k]);
         asm volatile("cp.async.commit_group;\n" ::: "memory");
       }
     }
@@ -389,7 +394,7 @@ __global__ void __launch_bounds__(NT, R == 5 ? 1 : (NT <= 128 ? 3 : (NT <= 256 ?
         if (s == 1 && next < n_tiles) {  // every thread has read the load buffer at stage 0
 #pragma unroll
           for (int k = 0; k < NK; k++)
-            cp_async16_s(sin + (tid + k * NT) * 16u, amp + base_next + t_cp + prm.ko[k]);
+            cp_async16_s(sin + (t_sd ^ (swzl(2u * uint32_t(k) * NT) * 8u)), amp + base_next + t_cp + prm.ko[k]);
           asm volatile("cp.async.commit_group;\n" ::: "memory");
         }
         q = reinterpret_cast<const uint4 *>(st.xo);

@@ -105,6 +105,23 @@ __host__ __device__ inline uint32_t swz(uint32_t l) {
   return x;
 }
 
+// Load-buffer swizzle of tensor-core passes, at 16-byte granularity: local bit
+// 0 stays in place (a 16-byte cp.async chunk holds local indices 2q and 2q + 1),
+// bits 1..3 map to themselves, and a bit b >= 4 also flips bits 1..3 by
+// swzl_col(b) (a nonzero 3-bit pattern, 3 bits per b in kSwzL), so a first stage
+// whose registers hold low tile bits still reads the load buffer conflict-free:
+// the planner gives its half-warp lanes bits with independent images.
+constexpr uint64_t kSwzL = 0xae23f5711ull;  // b = 4..15: 1, 2, 4, 3, 5, 6, 7, 1, 2, 4, 3, 5
+__host__ __device__ constexpr uint32_t swzl_col(int b) {
+  return b < 4 ? (1u << b) : uint32_t(((kSwzL >> (3 * (b - 4))) & 7u) << 1);
+}
+__host__ __device__ constexpr uint32_t swzl(uint32_t l) {
+  uint32_t x = l;
+  for (int b = 4; b < 16; b++)
+    if ((l >> b) & 1u) x ^= swzl_col(b);
+  return x;
+}
+
 struct alignas(16) OpRec {
   uint8_t type;
   uint8_t k;

@@ -526,8 +526,9 @@ struct HStage {
 
 // Greedy, in op order: a stage takes every op whose earlier unplaced ops do not
 // share a bit with it and whose bits fit the stage's Rb register bits.  Phase
-// ops need no register bits.  The first stage avoids the c low bits (it loads
-// with the low bits on the lanes).  The last stage stores whatever bits it
+// ops need no register bits.  The first stage of a register pass avoids the c
+// low bits (it loads with the low bits on the lanes); that of a tensor-core pass
+// may hold any (its load buffer is swizzled, see swzl).  The last stage stores whatever bits it
 // holds: no store-only stage is appended (it would cost a whole-tile exchange
 // through shared memory, more than the partly filled 32-byte sectors of a store
 // whose lanes skip some low bits, which L2 merges before they reach DRAM),
@@ -548,7 +549,7 @@ static void assign_stages(const std::vector<HostOp> &ops, const std::vector<uint
   for (size_t i = 0; i < ops.size(); i++) rem[i] = int(i);
   bool first = true;
   while (!rem.empty()) {
-    const uint32_t allowed = first ? (all & ~low) : all;
+    const uint32_t allowed = (first && !tc) ? (all & ~low) : all;
     HStage s;
     uint32_t blocked = 0;
     uint32_t phase_bits = 0;  // tc: bits of accepted phase ops (applied after the stage's product)
@@ -582,7 +583,7 @@ static void assign_stages(const std::vector<HostOp> &ops, const std::vector<uint
   if (st.size() == 1 && !store_natural && !tc) st.push_back(HStage{});
   for (size_t i = 0; i < st.size(); i++) {
     uint32_t allowed = all;
-    if (i == 0) allowed &= ~low;
+    if (i == 0 && !tc) allowed &= ~low;
     for (int b = T - 1; b >= 0 && popc(uint64_t(st[i].R)) < Rb; b--)
       if (((allowed >> b) & 1u) && !((st[i].R >> b) & 1u)) st[i].R |= 1u << b;
   }
@@ -591,7 +592,7 @@ static void assign_stages(const std::vector<HostOp> &ops, const std::vector<uint
 // `store_lanes` (store stages of relabeled passes): the local bits that hold
 // output qubits 0..c-1, in that order, to be put on the lanes.
 static StageRec make_stage(const HStage &hs, int T, int c, int Rb, bool load, bool store,
-                           const std::vector<int> *store_lanes = nullptr) {
+                           const std::vector<int> *store_lanes = nullptr, bool tc = false) {
   StageRec sr{};
   int nr = 0;
   for (int b = 0; b < T; b++)
@@ -607,6 +608,28 @@ static StageRec make_stage(const HStage &hs, int T, int c, int Rb, bool load, bo
     tb = *store_lanes;  // output qubits 0..c-1 on the lanes, then the rest ascending
     for (int b : rest)
       if (std::find(tb.begin(), tb.end(), b) == tb.end()) tb.push_back(b);
+  } else if (load && tc) {
+    // tensor-core passes read their first stage from the swizzled load buffer:
+    // four half-warp lane bits with independent images under swzl, lowest first
+    uint32_t basis[4] = {0, 0, 0, 0};
+    std::vector<int> lanes, others;
+    for (int b : rest) {
+      uint32_t v = swzl_col(b);
+      for (int i = 3; i >= 0; i--)
+        if ((v >> i) & 1u) {
+          if (basis[i]) {
+            v ^= basis[i];
+          } else {
+            basis[i] = v;
+            break;
+          }
+        }
+      if (v && lanes.size() < 4) lanes.push_back(b);
+      else others.push_back(b);
+    }
+    tb = lanes;
+    std::sort(others.begin(), others.end());
+    tb.insert(tb.end(), others.begin(), others.end());
   } else if (load) {
     tb = rest;  // ascending: the low tile bits sit on the lanes
   } else if (store) {
@@ -739,7 +762,7 @@ static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint3
   uint32_t nterms = 0;
   for (size_t si = 0; si < stages.size(); si++) {
     const HStage &st = stages[si];
-    StageRec sr = make_stage(st, T, c, Rb, si == 0, si + 1 == stages.size());
+    StageRec sr = make_stage(st, T, c, Rb, si == 0, si + 1 == stages.size(), nullptr, true);
     sr.op_begin = uint32_t(recs.size());
     std::vector<cd> U(size_t(NU) * NU, 0.0);
     for (int d = 0; d < NU; d++) U[size_t(d) * (NU + 1)] = 1.0;
@@ -832,7 +855,9 @@ static RegPassParams reg_params(const PlanPass &hp, const StageRec &first, const
   const uint32_t NT = 1u << (hp.T - hp.R);
   for (uint32_t x = 0; x < hp.T; x++) p.oq[x] = uint8_t(outq[x]);
   for (int j = 0; j < (1 << hp.R); j++) {
-    p.lo[j] = uint32_t(first.la[j]) * 8u;
+    // tensor-core passes: the load buffer is swizzled (swzl); the kernel xors
+    // the thread's part in
+    p.lo[j] = (hp.kind == KIND_TC ? swzl(first.la[j]) : uint32_t(first.la[j])) * 8u;
     const uint32_t l = last.la[j];
     uint64_t g = 0;
     for (uint32_t x = 0; x < hp.T; x++)

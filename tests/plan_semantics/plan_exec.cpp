@@ -115,20 +115,27 @@ static int exec_reg_pass(std::vector<cdd> &amp, const Plan &plan, size_t p) {
   std::vector<std::vector<cdd>> v(NT, std::vector<cdd>(NR));
   for (uint64_t tile = 0; tile < hp.n_tiles; tile++) {
     const uint64_t base = pdep_host(tile, hp.outer_mask);
-    // load: 16-byte chunk rows into the natural-order tile
+    // load: 16-byte chunk rows into the natural-order tile (tensor-core passes:
+    // chunk q at position swzl(2q), stage-0 reads at swzl(LB0) ^ lo[j] / 8)
+    const bool tcp = hp.kind == KIND_TC;
     for (uint32_t tid = 0; tid < NT; tid++) {
       const uint64_t t_cp = pdep_host(tid >> cs, hp.high_mask) + (uint64_t(tid & cmask) << 1);
       for (uint32_t k = 0; k < NR / 2; k++) {
         const uint64_t g = base + t_cp + prm.ko[k];
         const uint32_t q = tid + k * NT;
-        if (g + 1 >= amp.size() || 2 * q + 1 >= L) return 4;
-        buf[2 * q] = amp[g];
-        buf[2 * q + 1] = amp[g + 1];
+        const uint32_t pos = tcp ? swzl(2 * q) : 2 * q;
+        if (g + 1 >= amp.size() || pos + 1 >= L) return 4;
+        buf[pos] = amp[g];
+        buf[pos + 1] = amp[g + 1];
       }
     }
     for (uint32_t tid = 0; tid < NT; tid++) {
       const uint32_t LB0 = tt[tid] & 0xffffu;
-      for (uint32_t j = 0; j < NR; j++) v[tid][j] = buf[LB0 + prm.lo[j] / 8];
+      for (uint32_t j = 0; j < NR; j++) {
+        const uint32_t pos = tcp ? (swzl(LB0) ^ (prm.lo[j] / 8)) : (LB0 + prm.lo[j] / 8);
+        if (pos >= L) return 4;
+        v[tid][j] = buf[pos];
+      }
     }
     for (uint32_t s = 0; s < ns; s++) {
       const StageRec &st = stages[s];
