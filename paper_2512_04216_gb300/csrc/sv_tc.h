@@ -17,8 +17,6 @@ __host__ __device__ constexpr uint32_t tc_b_image_bytes(int R) { return 2u * tc_
 __host__ __device__ constexpr uint32_t tc_b_kstep(int R) { return 2u * tc_k(R) * 32u; }
 // TMEM columns per 128-row group: A_hi (K), A_lo (K), D (2K: D_left, D_right).
 __host__ __device__ constexpr uint32_t tc_cols_per_group(int R) { return 4u * tc_k(R); }
-constexpr uint32_t kTcBImage = tc_b_image_bytes(4);
-constexpr uint32_t kTcBKStep = tc_b_kstep(4);
 
 // Byte offset of B'[n][k] (n < 2K, k < K) inside a stage image of width R.
 size_t tc_b_offset(int R, int n, int k);
