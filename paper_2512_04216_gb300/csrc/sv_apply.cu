@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(NTMAX, R == 5 ? (NTMAX <= 128 ? 4 : 2) : (NTMA
   const uint64_t outer_mask = P->outer_mask, n_tiles = P->n_tiles;
   // the launch's shared memory was sized from the host's copy of these fields
   if (T != prm.chk[0] || ns != prm.chk[1] || data_bytes != prm.chk[2] || data_off != prm.chk[3] ||
-      P->R != uint32_t(R) || ns == 0 || ns > uint32_t(kMaxStages)) {
+      P->R != uint32_t(R) || ns == 0 || ns > uint32_t(kMaxStages) || !w_table_ok(P)) {
     if (threadIdx.x == 0) atomicOr(err, kPlanMismatch);
     return;
   }
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(NT, R == 5 ? 1 : (NT <= 128 ? 4 : (NT <= 256 ?
   const uint64_t outer_mask = P->outer_mask, n_tiles = P->n_tiles;
   // the launch's shared memory was sized from the host's copy of these fields
   if (T != kT || T != prm.chk[0] || ns != prm.chk[1] || data_bytes != prm.chk[2] || data_off != prm.chk[3] ||
-      P->R != uint32_t(R) || P->kind != KIND_TC || ns == 0 || ns > uint32_t(kMaxStages)) {
+      P->R != uint32_t(R) || P->kind != KIND_TC || ns == 0 || ns > uint32_t(kMaxStages) || !w_table_ok(P)) {
     if (threadIdx.x == 0) atomicOr(err, kPlanMismatch);
     return;
   }
@@ -298,6 +298,11 @@ __global__ void __launch_bounds__(NT, R == 5 ? 1 : (NT <= 128 ? 4 : (NT <= 256 ?
   tc_fence_after();
   const StageRec *stages = reinterpret_cast<const StageRec *>(data + (P->stages_off - data_off));
   const OpRec *ops = reinterpret_cast<const OpRec *>(data);
+  // outer-term slots of the phase ops, their per-tile sums in alternate halves
+  const uint32_t n_w = P->n_w;
+  const uint8_t *wrec = data + (n_w ? P->w_off - data_off : 0u);
+  uint32_t *wsum = reinterpret_cast<uint32_t *>(data + (n_w ? P->w_off - data_off + rphase_w_sums(n_w) : 0u));
+  uint32_t wpar = 0;
   // per-thread stage tables (own entries only): low 16 bits local index part, high 16 swizzled
   for (uint32_t s = 0; s < ns; s++) {
     uint32_t LB = 0;
@@ -347,6 +352,7 @@ __global__ void __launch_bounds__(NT, R == 5 ? 1 : (NT <= 128 ? 4 : (NT <= 256 ?
   while (tile < n_tiles) {
     const uint64_t next = tile + gridDim.x;
     const uint64_t base_next = next < n_tiles ? pdep_u64(next, outer_mask) : 0;
+    if (n_w) rphase_tile_sums(wrec, n_w, data_bytes - (P->w_off - data_off), base, wsum + wpar * n_w);
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     if (__syncthreads_or(bad)) {  // the tile has landed; the previous tile is done
       aborted = true;
@@ -375,7 +381,6 @@ __global__ void __launch_bounds__(NT, R == 5 ? 1 : (NT <= 128 ? 4 : (NT <= 256 ?
     for (uint32_t s = 0; s < ns; s++) {
       const StageRec &st = stages[s];
       const uint32_t w = tt[s * NT + tid];
-      const uint32_t LB = w & 0xffffu;
       if (s > 0) {
         const uint32_t PBp = (tt[(s - 1) * NT + tid] >> 16) * 8u, PB = (w >> 16) * 8u;
         uint32_t xo[NR];
@@ -427,7 +432,7 @@ __global__ void __launch_bounds__(NT, R == 5 ? 1 : (NT <= 128 ? 4 : (NT <= 256 ?
       const uint32_t oe = st.op_end;
       for (uint32_t o = st.op_begin; o < oe; o++) {
         const OpRec op = ops[o];
-        reg_rphase<R>(v, data + (op.data_off - data_off), base, LB);
+        reg_rphase<R>(v, data + (op.data_off - data_off), wsum + wpar * n_w, tid);
       }
     }
     if (aborted) break;
@@ -439,6 +444,7 @@ __global__ void __launch_bounds__(NT, R == 5 ? 1 : (NT <= 128 ? 4 : (NT <= 256 ?
     }
     tile = next;
     base = base_next;
+    wpar ^= 1u;
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   tc_fence_before();

@@ -181,7 +181,8 @@ __device__ __forceinline__ bool batch_plan_ok(const uint8_t *plans, uint64_t pla
     const PlanPass P = reinterpret_cast<const PlanPass *>(plan)[p];
     if (P.kind == KIND_REG) {  // arena register pass: the checks k_pass_reg makes, and the budget
       if (C.n <= uint32_t(kBatchSmemQubits) || P.T != uint32_t(kBatchRegT) || P.R != 4u || P.c < 1 ||
-          P.c + 4 > P.T || P.n_tiles != (uint64_t(1) << (C.n - P.T)) || !batch_reg_fits(P.c, P.n_stages, P.data_bytes))
+          P.c + 4 > P.T || P.n_tiles != (uint64_t(1) << (C.n - P.T)) || !batch_reg_fits(P.c, P.n_stages, P.data_bytes) ||
+          !w_table_ok(&P))
         return false;
       if (C.plan_off + P.aux_off + sizeof(RegPassParams) > plans_size ||
           C.plan_off + P.ops_off + uint64_t(P.data_bytes) > plans_size || (P.aux_off & 15u) || (P.ops_off & 15u))

@@ -14,7 +14,9 @@
 //             32-bit fractions of a turn so sums wrap exactly modulo 2*pi;
 //   OP_RPHASE the register-stage form of a diagonal product (KIND_REG and
 //             KIND_TC passes): terms may touch two tile qubits, and are
-//             pre-classified by the stage's register bits (RegPhaseHdr).
+//             pre-classified by the stage's register bits (RegPhaseHdr); the
+//             terms on tile qubits only are pre-summed per thread, those on
+//             outer qubits are summed once per tile (RegPhaseSlot).
 #pragma once
 
 #include <atomic>
@@ -51,10 +53,11 @@ struct alignas(16) PlanPass {
   uint32_t n_stages;
   uint32_t stages_off;  // byte offset of StageRec[n_stages]
   uint32_t data_bytes;  // bytes from ops_off to the end of this pass's records
-  uint32_t pad0_;
+  uint32_t w_off;       // KIND_REG / KIND_TC: byte offset of the pass's outer-term slot
+                        // table (RegPhaseSlot), 0 when no phase op has outer terms
   uint32_t aux_off;     // batched plans, KIND_REG passes: byte offset of the pass's
                         // RegPassParams from the circuit's plan base (0 otherwise)
-  uint32_t pad_;
+  uint32_t n_w;         // slots in the table at w_off
   int8_t lq[32];        // local bit -> physical qubit
 };
 
@@ -130,7 +133,7 @@ struct alignas(16) OpRec {
                         // ascending register order)
   uint32_t data_off;    // DENSE: byte offset of the row-major matrix: float2 (re, im) per
                         // element, or in KIND_REG passes float4 (re, re, -im, im);
-                        // PHASE: of PhaseTerm[]; RPHASE: of RegPhaseHdr + terms
+                        // PHASE: of PhaseTerm[]; RPHASE: of RegPhaseHdr + tables
   uint32_t count;       // PHASE: number of terms
 };
 
@@ -141,34 +144,63 @@ struct alignas(16) PhaseTerm {
 };
 
 // OP_RPHASE record, relative to the stage holding it (register bits rb[0..R-1],
-// thread-local bits the rest).  The phase of register amplitude j of a thread
-// whose thread-local index bits are LB is
-//     2*pi/2^32 * ( P + sum_{i: bit i of j} alpha_i ) + arg D[j]
-// where P sums the class-0 terms and alpha_i the class-(1+i) terms that apply
-// (outer qubits outer_mask all 1 in this tile, thread-local bits tmask all 1 in
-// LB), and D[j] collects the terms that depend on register bits only.  Terms
-// are stored by class: class c occupies [end[c-1], end[c]).
+// thread bits tb[0..ntb-1], ntb = T - R).  The phase of register amplitude j of
+// thread t is
+//     2*pi/2^32 * ( a_0 + sum_{i: bit i of j} a_{1+i} ) + arg D[j]
+// where class 0 holds the terms on no register bit and class 1+i those on
+// register bit i (a term touches at most two qubits, so at most one register
+// bit once the terms on register bits only are folded into D[j]), and a_k is
+// the sum of the turns of class k's terms that apply to this thread in this
+// tile (their outer qubits all 1 in the tile, their thread-local bits all 1 in
+// t's local index):
+//   * terms on tile qubits only: summed per thread by the planner, a table of
+//     nt turns per class with such terms (bit k of pre_mask), after the header
+//     in ascending k;
+//   * terms on outer qubits: summed once per tile (the sum depends on the tile
+//     only) into the pass's slots w_slot.. (RegPhaseSlot): slot 0 takes class
+//     0's terms without a thread bit, slot 1 + i those on thread bit i (added
+//     by the threads whose bit i is 1), slot 1 + ntb + r class 1+r's terms;
+//     bit 0 of w_used marks slot 0 used, bit 1 any of slots 1..ntb, bit 2 + r
+//     slot 1 + ntb + r.
+// Sums are of 32-bit turn fractions modulo 2^32, so their order does not
+// matter: every grouping gives the same a_k.
 struct alignas(16) RegPhaseHdr {
-  uint32_t end[6];      // cumulative term counts of classes 0..R (R <= 5)
+  uint32_t pre_mask;    // classes with a per-thread table
+  uint32_t w_used;      // outer-term slots in use (see above)
+  uint32_t w_slot;      // first of this op's 1 + ntb + R slots
   uint32_t has_d;       // D differs from the identity
-  uint32_t pad_;
+  uint32_t ntb;         // thread bits of the stage (T - R)
+  uint32_t nt;          // threads of the stage (2^ntb): the tables' length
+  uint32_t pad_[2];
   float2 d[32];         // register-only diagonal (2^R entries used)
 };
-struct alignas(16) RegPhaseTerm {
-  uint64_t outer_mask;  // outer qubits that must all be 1
-  uint32_t tmask;       // thread-local bits (as a tile-local index mask) that must all be 1
-  uint32_t turn;        // fraction of 2*pi, scaled by 2^32
+
+// A pass's phase terms on outer qubits (KIND_REG and KIND_TC passes), at
+// PlanPass.w_off: RegPhaseSlot[n_w] (each a range of the term array), then
+// 2 x n_w uint32 of per-tile sums (a scratch area: the kernels write it in
+// their shared-memory copy of the records, alternating halves tile by tile),
+// then the terms.  rphase_w_sums / rphase_w_terms give the byte offsets of the
+// last two from w_off.
+struct alignas(8) RegPhaseSlot {
+  uint32_t begin, end;  // term indices [begin, end)
 };
+struct alignas(16) RegPhaseOuter {
+  uint64_t outer_mask;  // outer qubits that must all be 1 in the tile
+  uint32_t turn;        // fraction of 2*pi, scaled by 2^32
+  uint32_t pad_;
+};
+__host__ __device__ constexpr uint32_t rphase_w_sums(uint32_t n_w) { return (8u * n_w + 15u) & ~15u; }
+__host__ __device__ constexpr uint32_t rphase_w_terms(uint32_t n_w) {
+  return rphase_w_sums(n_w) + ((8u * n_w + 15u) & ~15u);
+}
 
 static_assert(sizeof(RegPhaseHdr) == 288, "RegPhaseHdr layout");
-static_assert(sizeof(RegPhaseTerm) == 16, "RegPhaseTerm layout");
+static_assert(sizeof(RegPhaseOuter) == 16, "RegPhaseOuter layout");
+static_assert(sizeof(RegPhaseSlot) == 8, "RegPhaseSlot layout");
 static_assert(sizeof(PlanPass) == 112, "PlanPass layout");
 static_assert(sizeof(StageRec) == 288, "StageRec layout");
 static_assert(sizeof(OpRec) == 16, "OpRec layout");
 static_assert(sizeof(PhaseTerm) == 16, "PhaseTerm layout");
-
-// ||psi||^2 restoration after a unitary circuit: amp *= sqrt(before[0] / after[0])
-// (both device doubles; nothing changes if either is not positive).
 
 // Norm tracking across the tensor-core passes of one unitary circuit.  The
 // tensor cores' float32 accumulation rounds toward zero, so every stage product

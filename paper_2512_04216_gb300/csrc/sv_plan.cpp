@@ -44,6 +44,7 @@ namespace svgb {
 using cd = std::complex<double>;
 
 static inline int popc(uint64_t x) { return __builtin_popcountll(x); }
+static inline int ctz(uint64_t x) { return __builtin_ctzll(x); }
 
 // ---------------------------------------------------------------------------
 // gate matrices (OpenQASM 2 definitions, see include/sv.h)
@@ -469,14 +470,45 @@ static void align16(std::vector<uint8_t> &buf) {
 // non-low tile bits.
 static bool T_reg_ok(int T, int c, int Rb) { return T - Rb >= 5 && T <= kMaxTile && T - c >= Rb; }
 
+// The outer-term slots of one register or tensor-core pass (RegPhaseSlot):
+// slot s collects the terms whose sum the kernels form once per tile.
+struct WSlots {
+  std::vector<std::vector<RegPhaseOuter>> slot;
+  size_t terms = 0;
+};
+
+// Bytes a phase op adds to a pass's records at most: its record, its per-thread
+// tables and its slots (entry, two sums, terms), with alignment.
+static size_t rphase_bytes_max(const std::vector<HostTerm> &terms, int T, int Rb) {
+  const size_t nt = size_t(1) << (T - Rb), nslot = size_t(1 + (T - Rb) + Rb);
+  return sizeof(RegPhaseHdr) + size_t(Rb + 1) * nt * 4 + nslot * 16 + terms.size() * sizeof(RegPhaseOuter) + 64;
+}
+
 // Appends the OP_RPHASE record of a phase op placed in a register stage whose
-// register bits are R (register index i <-> i-th lowest bit of R); returns the
-// number of stored terms.  Terms on register bits only fold into D.
-static uint32_t put_rphase(const std::vector<HostTerm> &terms, uint32_t R, std::vector<uint8_t> &buf) {
+// register bits are R (register index i <-> i-th lowest bit of R) and whose
+// thread bit i is local bit tb[i] (i < ntb); its outer terms go to new slots
+// of `ws`.  Returns the number of terms.  Terms on register bits only fold into
+// D; a term touches at most two qubits (diagonal gates have one or two), so a
+// term on an outer qubit has at most one more bit, a register or a thread bit.
+static uint32_t put_rphase(const std::vector<HostTerm> &terms, uint32_t R, const uint8_t *tb, int ntb,
+                           WSlots &ws, std::vector<uint8_t> &buf) {
   RegPhaseHdr h{};
   const int Rb = popc(uint64_t(R));
+  const uint32_t nt = 1u << ntb;
+  h.ntb = uint32_t(ntb);
+  h.nt = nt;
+  int tbi[32];
+  for (int b = 0; b < 32; b++) tbi[b] = -1;
+  for (int i = 0; i < ntb; i++) tbi[tb[i]] = i;
+  // LB(t): the local index bits of thread t
+  std::vector<uint32_t> LB(nt, 0);
+  for (uint32_t t = 0; t < nt; t++)
+    for (int i = 0; i < ntb; i++)
+      if ((t >> i) & 1u) LB[t] |= 1u << tb[i];
   uint32_t dturn[32] = {0};
-  std::vector<RegPhaseTerm> cls[6];
+  std::vector<uint32_t> pre[6];
+  const uint32_t nslot = uint32_t(1 + ntb + Rb);
+  std::vector<std::vector<RegPhaseOuter>> sl(nslot);
   for (const HostTerm &t : terms) {
     uint32_t tmask = 0, jm = 0;
     int nreg = 0, reg0 = -1;
@@ -494,15 +526,32 @@ static uint32_t put_rphase(const std::vector<HostTerm> &terms, uint32_t R, std::
     if (tmask == 0 && t.outer == 0) {
       for (int j = 0; j < (1 << Rb); j++)
         if ((uint32_t(j) & jm) == jm) dturn[j] += t.turn;
+      continue;
+    }
+    const int k = nreg ? 1 + reg0 : 0;
+    if (t.outer == 0) {
+      if (pre[k].empty()) pre[k].assign(nt, 0u);
+      for (uint32_t x = 0; x < nt; x++)
+        if ((LB[x] & tmask) == tmask) pre[k][x] += t.turn;
     } else {
-      // a term has at most two qubits, so here it has at most one register bit
-      cls[nreg ? 1 + reg0 : 0].push_back(RegPhaseTerm{t.outer, tmask, t.turn});
+      const uint32_t s = k ? uint32_t(1 + ntb + (k - 1)) : (tmask ? uint32_t(1 + tbi[ctz(uint64_t(tmask))]) : 0u);
+      sl[s].push_back(RegPhaseOuter{t.outer, t.turn, 0});
     }
   }
-  uint32_t n = 0;
-  for (int k = 0; k < 6; k++) {
-    n += uint32_t(cls[k].size());
-    h.end[k] = n;
+  for (int k = 0; k <= Rb; k++)
+    if (!pre[k].empty()) h.pre_mask |= 1u << k;
+  bool any = false;
+  for (uint32_t s = 0; s < nslot; s++) {
+    if (sl[s].empty()) continue;
+    any = true;
+    h.w_used |= s == 0 ? 1u : (s <= uint32_t(ntb) ? 2u : 1u << (2 + (s - 1 - ntb)));
+  }
+  if (any) {
+    h.w_slot = uint32_t(ws.slot.size());
+    for (auto &v : sl) {
+      ws.terms += v.size();
+      ws.slot.push_back(std::move(v));
+    }
   }
   for (int j = 0; j < 32; j++) {
     if (dturn[j]) h.has_d = 1;
@@ -510,9 +559,31 @@ static uint32_t put_rphase(const std::vector<HostTerm> &terms, uint32_t R, std::
     h.d[j] = make_float2(float(std::cos(a)), float(std::sin(a)));
   }
   put_bytes(buf, &h, sizeof(h));
-  for (int k = 0; k < 6; k++)
-    if (!cls[k].empty()) put_bytes(buf, cls[k].data(), cls[k].size() * sizeof(RegPhaseTerm));
-  return n;
+  for (int k = 0; k <= Rb; k++)
+    if (!pre[k].empty()) put_bytes(buf, pre[k].data(), pre[k].size() * 4);
+  return uint32_t(terms.size());
+}
+
+// Appends a pass's slot table (RegPhaseSlot[n], the per-tile sums' scratch,
+// the terms) and records it in the pass header; nothing when no slot is used.
+static void put_wslots(const WSlots &ws, PlanPass &hp, std::vector<uint8_t> &buf) {
+  if (ws.slot.empty()) return;
+  align16(buf);
+  const uint32_t n = uint32_t(ws.slot.size());
+  const size_t at = buf.size();
+  hp.w_off = uint32_t(at);
+  hp.n_w = n;
+  std::vector<RegPhaseSlot> tab(n);
+  uint32_t b = 0;
+  for (uint32_t s = 0; s < n; s++) {
+    tab[s].begin = b;
+    b += uint32_t(ws.slot[s].size());
+    tab[s].end = b;
+  }
+  buf.resize(at + rphase_w_terms(n), 0);
+  std::memcpy(buf.data() + at, tab.data(), n * sizeof(RegPhaseSlot));
+  for (const auto &v : ws.slot)
+    if (!v.empty()) put_bytes(buf, v.data(), v.size() * sizeof(RegPhaseOuter));
 }
 
 // ---------------------------------------------------------------------------
@@ -739,7 +810,7 @@ static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint3
     for (int o : st.ops) {
       if (ops[o].type == OP_PHASE) {
         nphase++;
-        terms_bytes += ops[o].terms.size() * sizeof(RegPhaseTerm) + sizeof(RegPhaseHdr);
+        terms_bytes += rphase_bytes_max(ops[o].terms, T, Rb);
       } else {
         mma = true;
       }
@@ -760,6 +831,7 @@ static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint3
   std::vector<StageRec> srecs;
   std::vector<std::vector<double>> bmats;  // per MMA stage: B[n][k], K x K
   uint32_t nterms = 0;
+  WSlots ws;
   for (size_t si = 0; si < stages.size(); si++) {
     const HStage &st = stages[si];
     StageRec sr = make_stage(st, T, c, Rb, si == 0, si + 1 == stages.size(), nullptr, true);
@@ -774,7 +846,7 @@ static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint3
         r.type = OP_RPHASE;
         align16(buf);
         r.data_off = uint32_t(buf.size());
-        r.count = put_rphase(op.terms, st.R, buf);
+        r.count = put_rphase(op.terms, st.R, sr.tb, T - Rb, ws, buf);
         nterms += r.count;
         info.n_phase++;
         recs.push_back(r);
@@ -820,6 +892,7 @@ static bool pack_tc_pass(const std::vector<HostOp> &ops, const std::vector<uint3
     }
   }
   std::memcpy(buf.data() + stage_at, srecs.data(), srecs.size() * sizeof(StageRec));
+  put_wslots(ws, hp, buf);
   align16(buf);
   hp.data_bytes = uint32_t(buf.size() - hp.ops_off);
   hp.n_ops = uint32_t(recs.size());
@@ -1224,7 +1297,7 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
       size_t est = nops * sizeof(OpRec) + stages.size() * sizeof(StageRec) + 16;
       for (auto &op : ph.ops)
         est += op.type == OP_DENSE ? ((size_t(16) << (2 * op.blk.k())) + 15) / 16 * 16
-                                   : op.terms.size() * sizeof(RegPhaseTerm) + sizeof(RegPhaseHdr) + 16;
+                                   : rphase_bytes_max(op.terms, T_, Rb);
       if (!reg_pass_fits(uint32_t(T_), uint32_t(c), uint32_t(Rb), uint32_t(stages.size()), uint32_t(est))) {
         reg = false;
         stages.clear();
@@ -1248,6 +1321,11 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
     std::vector<int> stage_of(nops, -1);
     for (size_t si = 0; si < stages.size(); si++)
       for (int o : stages[si].ops) stage_of[o] = int(si);
+    std::vector<StageRec> srecs;
+    for (size_t si = 0; si < stages.size(); si++)
+      srecs.push_back(make_stage(stages[si], T_, c, Rb, si == 0, si + 1 == stages.size(),
+                                 store_natural ? nullptr : &store_lanes));
+    WSlots ws;
 
     align16(buf);
     hp.ops_off = uint32_t(buf.size());
@@ -1301,7 +1379,8 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
         plan.info.flops += uint64_t(amps * 8.0 * K);
       } else if (reg) {
         r.type = OP_RPHASE;
-        r.count = put_rphase(op.terms, stages[stage_of[order[oi]]].R, buf);
+        const int si = stage_of[order[oi]];
+        r.count = put_rphase(op.terms, stages[si].R, srecs[si].tb, T_ - Rb, ws, buf);
         nterms += r.count;
         plan.info.n_phase++;
       } else {
@@ -1330,8 +1409,7 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
       uint32_t ob = 0;
       StageRec first{}, last{};
       for (size_t si = 0; si < stages.size(); si++) {
-        StageRec sr = make_stage(stages[si], T_, c, Rb, si == 0, si + 1 == stages.size(),
-                                 store_natural ? nullptr : &store_lanes);
+        StageRec sr = srecs[si];
         sr.op_begin = ob;
         ob += uint32_t(stages[si].ops.size());
         sr.op_end = ob;
@@ -1341,6 +1419,7 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
       }
       plan.rparams[p] = reg_params(hp, first, last, outq);
       plan.info.n_stages += stages.size();
+      put_wslots(ws, hp, buf);
     }
     align16(buf);
     hp.data_bytes = uint32_t(buf.size() - hp.ops_off);

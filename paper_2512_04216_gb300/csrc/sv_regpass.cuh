@@ -164,18 +164,44 @@ __device__ __forceinline__ void reg_dense_dispatch(float2 (&v)[1 << R], uint32_t
 }
 #undef SV_CASE
 
-// exp(2*pi*i * sum of the turns of terms [i0, i1) that apply to this thread)
-__device__ __forceinline__ float2 rphase_exp(const RegPhaseTerm *__restrict__ t, uint32_t i0, uint32_t i1,
-                                             uint64_t base, uint32_t LB) {
-  uint32_t a = 0;
-  for (uint32_t i = i0; i < i1; i++) {
-    const RegPhaseTerm x = t[i];
-    if ((base & x.outer_mask) == x.outer_mask && (LB & x.tmask) == x.tmask) a += x.turn;
-  }
+// exp(2*pi*i * a / 2^32)
+__device__ __forceinline__ float2 turn_exp(uint32_t a) {
   if (a == 0) return make_float2(1.f, 0.f);
   float sn, cs;
   sincospif(static_cast<float>(static_cast<int32_t>(a)) * 4.656612873077393e-10f, &sn, &cs);
   return make_float2(cs, sn);
+}
+
+// Whether a pass's outer-term slot table lies inside its records (its scratch
+// and terms included: the kernels keep term indices below the records' end).
+__device__ __forceinline__ bool w_table_ok(const PlanPass *P) {
+  const uint32_t n = P->n_w, o = P->w_off - P->ops_off;
+  return n == 0 || (P->w_off >= P->ops_off && (o & 15u) == 0 && n <= 4096u && o + rphase_w_terms(n) <= P->data_bytes);
+}
+
+// The per-tile sums of a pass's outer-term slots (RegPhaseSlot) for the tile
+// at `base`, into `sums` (n_w words): warp w takes slots w, w + nwarps, ...,
+// its lanes the slot's terms; sums wrap modulo 2^32.  `w` is the table in the
+// records' copy, `w_bytes` the bytes from it to the records' end (term indices
+// beyond them are not read).  Called by every thread of the CTA before the
+// barrier that precedes the tile's first stage.
+__device__ __forceinline__ void rphase_tile_sums(const uint8_t *__restrict__ w, uint32_t n_w, uint32_t w_bytes,
+                                                 uint64_t base, uint32_t *sums) {
+  const RegPhaseSlot *sl = reinterpret_cast<const RegPhaseSlot *>(w);
+  const RegPhaseOuter *t = reinterpret_cast<const RegPhaseOuter *>(w + rphase_w_terms(n_w));
+  const uint32_t lim = (w_bytes - rphase_w_terms(n_w)) / uint32_t(sizeof(RegPhaseOuter));
+  const uint32_t lane = threadIdx.x & 31u, nw = blockDim.x >> 5;
+  for (uint32_t s = threadIdx.x >> 5; s < n_w; s += nw) {
+    const RegPhaseSlot r = sl[s];
+    const uint32_t e = r.end < lim ? r.end : lim;
+    uint32_t a = 0;
+    for (uint32_t i = r.begin + lane; i < e; i += 32) {
+      const RegPhaseOuter x = t[i];
+      if ((base & x.outer_mask) == x.outer_mask) a += x.turn;
+    }
+    a = __reduce_add_sync(0xffffffffu, a);
+    if (lane == 0) sums[s] = a;
+  }
 }
 
 template <int J>
@@ -196,22 +222,33 @@ __device__ __forceinline__ void phase_tree(float2 (&f)[1 << R], const float2 (&e
   }
 }
 
-// OP_RPHASE on the 2^R register amplitudes of one thread (record layout in
-// RegPhaseHdr).  The thread sums the turns of the terms that apply to it into
-// P and alpha_i (exact modulo 2^32), takes the 1 + R exponentials, and forms
+// OP_RPHASE on the 2^R register amplitudes of thread `tid` (record layout in
+// RegPhaseHdr).  The thread adds its pre-summed turns of each class (terms on
+// tile qubits) to the tile's sums of the terms on outer qubits (`sums`, this
+// tile's half of the pass's scratch), takes the 1 + R exponentials, and forms
 // the 2^R amplitude phases as products along a binary tree (at most R complex
 // products deep), times D[j].
 template <int R>
-__device__ __forceinline__ void reg_rphase(float2 (&v)[1 << R], const uint8_t *__restrict__ rec, uint64_t base,
-                                           uint32_t LB) {
+__device__ __forceinline__ void reg_rphase(float2 (&v)[1 << R], const uint8_t *__restrict__ rec,
+                                           const uint32_t *__restrict__ sums, uint32_t tid) {
   const RegPhaseHdr *h = reinterpret_cast<const RegPhaseHdr *>(rec);
-  const RegPhaseTerm *t = reinterpret_cast<const RegPhaseTerm *>(rec + sizeof(RegPhaseHdr));
+  const uint32_t *pre = reinterpret_cast<const uint32_t *>(rec + sizeof(RegPhaseHdr));
+  const uint32_t pm = h->pre_mask, wu = h->w_used, nt = h->nt, ntb = h->ntb;
+  const uint32_t *w = sums + h->w_slot;
+  uint32_t a[R + 1];
+#pragma unroll
+  for (int k = 0; k <= R; k++)
+    a[k] = ((pm >> k) & 1u) ? pre[uint32_t(__popc(pm & ((1u << k) - 1u))) * nt + tid] : 0u;
+  if (wu & 1u) a[0] += w[0];
+  if (wu & 2u)
+    for (uint32_t i = 0; i < ntb; i++)
+      if ((tid >> i) & 1u) a[0] += w[1 + i];
+#pragma unroll
+  for (int r = 0; r < R; r++)
+    if ((wu >> (2 + r)) & 1u) a[1 + r] += w[1 + ntb + r];
   float2 e[R + 1];
 #pragma unroll
-  for (int k = 0; k <= R; k++) {
-    const uint32_t i0 = k ? h->end[k - 1] : 0u, i1 = h->end[k];
-    e[k] = rphase_exp(t, i0, i1, base, LB);
-  }
+  for (int k = 0; k <= R; k++) e[k] = turn_exp(a[k]);
   const bool has_d = h->has_d != 0;
   // f[j] = e[0] * prod_{bit i of j} e[1 + i], built from f[j without its lowest bit]
   float2 f[1 << R];
@@ -300,6 +337,13 @@ __device__ __forceinline__ void reg_pass_tiles(float2 *__restrict__ amp, const u
   __syncthreads();
   const StageRec *stages = reinterpret_cast<const StageRec *>(data + (P->stages_off - data_off));
   const OpRec *ops = reinterpret_cast<const OpRec *>(data);
+  // outer-term slots of the phase ops and their per-tile sums (two halves, used
+  // by alternate tiles: a tile's sums are written before the barrier that starts
+  // it, when every thread has finished the tile before the previous one)
+  const uint32_t n_w = P->n_w;
+  const uint8_t *wrec = data + (n_w ? P->w_off - data_off : 0u);
+  uint32_t *wsum = reinterpret_cast<uint32_t *>(data + (n_w ? P->w_off - data_off + rphase_w_sums(n_w) : 0u));
+  uint32_t wpar = 0;
   // per-thread stage tables: low 16 bits = local index part, high 16 = swizzled
   for (uint32_t s = 0; s < ns; s++) {
     uint32_t LB = 0;
@@ -338,6 +382,7 @@ __device__ __forceinline__ void reg_pass_tiles(float2 *__restrict__ amp, const u
   while (tile < n_tiles) {
     const uint64_t next = tile + tile_step;
     const uint64_t base_next = next < n_tiles ? pdep_u64(next, outer_mask) : 0;
+    if (n_w) rphase_tile_sums(wrec, n_w, data_bytes - (P->w_off - data_off), base, wsum + wpar * n_w);
     if constexpr (kShared) {
       asm volatile("cp.async.wait_all;\n" ::: "memory");
       __syncthreads();
@@ -358,7 +403,6 @@ __device__ __forceinline__ void reg_pass_tiles(float2 *__restrict__ amp, const u
     for (uint32_t s = 0; s < ns; s++) {
       const StageRec &st = stages[s];
       const uint32_t w = tt[s * NT + tid];
-      const uint32_t LB = w & 0xffffu;
       if (s > 0) {
         const StageRec &pv = stages[s - 1];
         const uint32_t PBp = (tt[(s - 1) * NT + tid] >> 16) * 8u, PB = (w >> 16) * 8u;
@@ -400,7 +444,7 @@ __device__ __forceinline__ void reg_pass_tiles(float2 *__restrict__ amp, const u
         if (op.type == OP_DENSE) {
           reg_dense_dispatch<R>(v, op.rmask, reinterpret_cast<const float4 *>(data + (op.data_off - data_off)));
         } else {
-          reg_rphase<R>(v, data + (op.data_off - data_off), base, LB);
+          reg_rphase<R>(v, data + (op.data_off - data_off), wsum + wpar * n_w, tid);
         }
       }
     }
@@ -411,6 +455,7 @@ __device__ __forceinline__ void reg_pass_tiles(float2 *__restrict__ amp, const u
     }
     tile = next;
     base = base_next;
+    wpar ^= 1u;
   }
 }
 

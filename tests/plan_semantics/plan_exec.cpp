@@ -113,8 +113,23 @@ static int exec_reg_pass(std::vector<cdd> &amp, const Plan &plan, size_t p) {
   const uint32_t L = 1u << T;
   std::vector<cdd> buf(L), xbuf(L);
   std::vector<std::vector<cdd>> v(NT, std::vector<cdd>(NR));
+  // the outer-term slots (RegPhaseSlot) of the pass's phase ops
+  const uint32_t n_w = hp.n_w;
+  std::vector<uint32_t> wsum(n_w);
+  if (n_w && (hp.w_off < hp.ops_off || hp.w_off + rphase_w_terms(n_w) > hp.ops_off + hp.data_bytes)) return 6;
+  const RegPhaseSlot *wsl = reinterpret_cast<const RegPhaseSlot *>(base_ptr + hp.w_off);
+  const RegPhaseOuter *wt = reinterpret_cast<const RegPhaseOuter *>(base_ptr + hp.w_off + rphase_w_terms(n_w));
   for (uint64_t tile = 0; tile < hp.n_tiles; tile++) {
     const uint64_t base = pdep_host(tile, hp.outer_mask);
+    // this tile's sums of each slot's terms whose outer qubits are all 1
+    for (uint32_t sl = 0; sl < n_w; sl++) {
+      uint32_t a = 0;
+      for (uint32_t i = wsl[sl].begin; i < wsl[sl].end; i++) {
+        if (hp.w_off + rphase_w_terms(n_w) + (i + 1) * sizeof(RegPhaseOuter) > hp.ops_off + hp.data_bytes) return 6;
+        if ((base & wt[i].outer_mask) == wt[i].outer_mask) a += wt[i].turn;
+      }
+      wsum[sl] = a;
+    }
     // load: 16-byte chunk rows into the natural-order tile (tensor-core passes:
     // chunk q at position swzl(2q), stage-0 reads at swzl(LB0) ^ lo[j] / 8)
     const bool tcp = hp.kind == KIND_TC;
@@ -195,16 +210,25 @@ static int exec_reg_pass(std::vector<cdd> &amp, const Plan &plan, size_t p) {
               for (uint32_t r = 0; r < K; r++) x[g | dep_bits(r, M)] = out[r];
             }
           } else {
+            // per-thread tables of the terms on tile qubits, plus the tile's
+            // sums of the terms on outer qubits (slot w_slot + 0: no thread
+            // bit, + 1 + i: thread bit i, + 1 + ntb + r: register bit r)
             const RegPhaseHdr *h = reinterpret_cast<const RegPhaseHdr *>(d);
-            const RegPhaseTerm *t = reinterpret_cast<const RegPhaseTerm *>(d + sizeof(RegPhaseHdr));
-            const uint32_t LB = tt[s * NT + tid] & 0xffffu;
+            const uint32_t *pre = reinterpret_cast<const uint32_t *>(d + sizeof(RegPhaseHdr));
+            if (h->nt != NT || h->ntb != T - R) return 6;
+            if (h->w_used && h->w_slot + 1 + h->ntb + R > n_w) return 6;
+            uint32_t a[6] = {0, 0, 0, 0, 0, 0};
+            for (uint32_t k = 0; k <= R; k++)
+              if ((h->pre_mask >> k) & 1u) a[k] = pre[uint32_t(__builtin_popcount(h->pre_mask & ((1u << k) - 1u))) * NT + tid];
+            const uint32_t *w = wsum.data() + h->w_slot;
+            if (h->w_used & 1u) a[0] += w[0];
+            if (h->w_used & 2u)
+              for (uint32_t i = 0; i < h->ntb; i++)
+                if ((tid >> i) & 1u) a[0] += w[1 + i];
+            for (uint32_t r = 0; r < R; r++)
+              if ((h->w_used >> (2 + r)) & 1u) a[1 + r] += w[1 + h->ntb + r];
             cdd e[6];
-            for (uint32_t k = 0; k <= R; k++) {
-              uint32_t turn = 0;
-              for (uint32_t i = k ? h->end[k - 1] : 0u; i < h->end[k]; i++)
-                if ((base & t[i].outer_mask) == t[i].outer_mask && (LB & t[i].tmask) == t[i].tmask) turn += t[i].turn;
-              e[k] = turn_exp(turn);
-            }
+            for (uint32_t k = 0; k <= R; k++) e[k] = turn_exp(a[k]);
             for (uint32_t j = 0; j < NR; j++) {
               cdd f = e[0];
               for (uint32_t i = 0; i < R; i++)
@@ -366,7 +390,7 @@ int main(int argc, char **argv) {
       n_tc += plan.passes[p].kind == KIND_TC;
       const int rc = plan.passes[p].kind == KIND_SMEM ? exec_smem_pass(b, plan, p) : exec_reg_pass(b, plan, p);
       if (rc) {
-        printf("pass %zu: %s\n", total, rc == 3 ? "unsupported pass" : rc == 5 ? "unknown op" : "index out of range");
+        printf("pass %zu: %s\n", total, rc == 3 ? "unsupported pass" : rc == 5 ? "unknown op" : rc == 6 ? "bad phase record" : "index out of range");
         return rc;
       }
     }
