@@ -82,17 +82,24 @@ typedef struct sv_opts {
                           k_max qubits (1..5; default 2).  Per pass, blocks wider
                           than 2 qubits are formed only when their estimated cost
                           is lower (the register kernels run 1-2-qubit blocks
-                          fastest); with precision 1, up to min(k_max, 4).  A gate
+                          fastest); with precision 1 or 2, up to min(k_max, 4).  A gate
                           wider than the width keeps a block of its own. */
   int32_t tile_qubits; /* T: qubits held by one CTA tile in shared memory per HBM
                           pass (5..13; default 12; clamped to n) */
   int32_t low_qubits;  /* c: low qubits every tile contains, so each global access
                           is a run of 2^c contiguous amplitudes (1..T; default 5) */
   int32_t precision;   /* 0 = FP32 CUDA cores for every block;
-                          1 = 3xTF32 tensor cores (tcgen05): all dense blocks of a
-                          register stage as one 16x16 complex product (tiles of
-                          11..13 qubits; smaller states use the CUDA-core kernels);
-                          when every gate is unitary the passes track ||psi||^2
+                          2 = 3xTF32 tensor cores (tcgen05) on every pass that fits:
+                          all dense blocks of a register stage as one 16x16 complex
+                          product (tiles of 11..13 qubits; smaller states use the
+                          CUDA-core kernels);
+                          1 = as 2, except that with kernel_variant 0 a pass runs on
+                          the FP32 CUDA-core register kernel when the planner
+                          estimates that faster: light passes (blocks of at most 2
+                          qubits, no phase ops, few stages), from a per-pass model
+                          of both kernels' measured times;
+                          with 1 and 2, when every gate is unitary the tensor-core
+                          passes track ||psi||^2
                           (the tensor cores' float32 accumulation rounds toward
                           zero, ~1e-7 of the norm per stage): the first tensor-core
                           pass sums it on load, each pass on store, and each later
@@ -105,11 +112,11 @@ typedef struct sv_opts {
                           qubits and T <= 12, else 16;
                           1 = every op sweeps the shared-memory tile;
                           2 = register stages with 16 amplitudes per thread; with
-                          precision 1: blocks fused up to min(k_max, 5) qubits and
+                          precision 1 or 2: blocks fused up to min(k_max, 5) qubits and
                           5-qubit stages (32 x 32 complex products, 32 amplitudes
                           per thread, T = 12 or 13) on every tensor-core pass whose
                           records fit (at most four 32 KB stage images).  Without
-                          it, precision 1 uses 4-qubit stages, and 5-qubit stages
+                          it, precisions 1 and 2 use 4-qubit stages, and 5-qubit stages
                           only for a pass holding a 5-qubit block (a 5-qubit
                           UNITARY gate) */
 } sv_opts;
@@ -125,7 +132,7 @@ typedef struct sv_plan_info {
   uint64_t bytes;      /* algorithmic HBM bytes: n_passes * 2 * 2^n * 8 */
   uint64_t upload_bytes; /* size of the packed plan copied host -> device per apply */
   uint64_t n_stages;   /* register stages over all register-stage passes */
-  uint64_t tc_stages;  /* stages applied as one 3xTF32 tensor-core product (precision 1) */
+  uint64_t tc_stages;  /* stages applied as one 3xTF32 tensor-core product (precision 1, 2) */
   uint64_t passes_by_kind[3]; /* passes run by the shared-memory sweep kernel, the
                                  register-stage kernel and the tensor-core kernel */
 } sv_plan_info;

@@ -447,7 +447,7 @@ int sv_apply_circuit(sv_state *s, const sv_gate *ir, size_t n_gates, const sv_op
   // the norm (TcNorm): dscal[4] takes the first tensor-core pass's input sum,
   // dscal[5..7] the output sums of successive tensor-core passes in rotation, and
   // each later pass rescales what it loads by sqrt(dscal[4] / previous sum).
-  const bool track = opts && opts->precision == 1 && builder.unitary() && s->n >= 11;
+  const bool track = opts && opts->precision >= 1 && builder.unitary() && s->n >= 11;
   if (track) CK(s, cudaMemsetAsync(s->dscal + 4, 0, 2 * sizeof(double), s->stream));
   size_t n_tc = 0;
   size_t chunk = 2;

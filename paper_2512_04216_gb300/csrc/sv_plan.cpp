@@ -1029,14 +1029,14 @@ bool PlanBuilder::init(int n, const sv_gate *ir, size_t ng, const sv_opts *opts_
     err = "tile_qubits must be in [1," + std::to_string(kMaxTile) + "]";
     return false;
   }
-  if (o.precision != 0 && o.precision != 1) {
-    err = "precision must be 0 or 1";
+  if (o.precision < 0 || o.precision > 2) {
+    err = "precision must be 0, 1 or 2";
     return false;
   }
   // kernel_variant: 0 = register stages where possible (32 amplitudes per
   // thread when the pass's blocks have at most 2 qubits and T <= 12, else 16),
   // 1 = shared-memory sweeps, 2 = register stages with 16 amplitudes per thread;
-  // with precision 1, variant 2 fuses up to 5 qubits and gives every
+  // with precision 1 or 2, variant 2 fuses up to 5 qubits and gives every
   // tensor-core pass 5-qubit stages (32 amplitudes a thread)
   const bool o_smem = (o.kernel_variant == 1);
   if (o.kernel_variant < 0 || o.kernel_variant > 2) {
@@ -1097,6 +1097,12 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
     int kfuse;                  // fusion width used
     bool relabeled;             // SWAPs folded into the store mapping
     int rho[64];                // qubit q's data ends at the loaded position of rho[q]
+    // precision 1: the same gates fused for the CUDA-core register kernel (blocks
+    // of <= 2 qubits, SWAPs folded into the store), for the per-pass choice
+    bool has_alt = false;
+    std::vector<HostOp> alt_ops;
+    bool alt_pairs = false;
+    int alt_rho[64];
   };
   std::vector<PassH> passes;
 
@@ -1182,13 +1188,19 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
       }
       return w * (kx <= 2 ? 1.0 : (kx <= 4 ? 1.3 : 4.0));
     };
-    int kf = (o.precision == 1) ? std::min(kmax, o.kernel_variant == 2 ? 5 : 4) : std::min(kmax, 2);
+    int kf = (o.precision >= 1) ? std::min(kmax, o.kernel_variant == 2 ? 5 : 4) : std::min(kmax, 2);
     // SWAPs of tile qubits become a relabeling of the store (register passes only)
     ph.relabeled = !o_smem && o.precision == 0;
     for (int q = 0; q < 64; q++) ph.rho[q] = q;
     ph.pairs = pairs_ok(kf);
     fuse_pass(gates, acc, Q, lpos, kf, ph.pairs, ph.ops, ph.relabeled ? ph.rho : nullptr);
-    if (o.precision != 1 && kmax > kf) {
+    if (o.precision == 1 && o_r5) {
+      ph.has_alt = true;
+      for (int q = 0; q < 64; q++) ph.alt_rho[q] = q;
+      ph.alt_pairs = pairs_ok(std::min(kmax, 2));
+      fuse_pass(gates, acc, Q, lpos, std::min(kmax, 2), ph.alt_pairs, ph.alt_ops, ph.alt_rho);
+    }
+    if (o.precision == 0 && kmax > kf) {
       std::vector<HostOp> wide;
       const bool pw = pairs_ok(kmax);
       int rho2[64];
@@ -1256,23 +1268,73 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
     // store mapping: local bit x is written to physical qubit outq[x]; SWAPs folded
     // into the pass leave qubit q's data at local bit lpos[rho[q]]
     int outq[32];
-    for (int x = 0; x < 32; x++) outq[x] = x < T_ ? ph.lq[x] : -1;
-    if (ph.relabeled)
-      for (int x = 0; x < T_; x++) outq[lpos[ph.rho[ph.lq[x]]]] = ph.lq[x];
     std::vector<int> store_lanes(size_t(c), 0);
     uint32_t store_low = 0;
-    for (int x = 0; x < T_; x++)
-      if (outq[x] < c) {
-        store_lanes[size_t(outq[x])] = x;
-        store_low |= 1u << x;
-      }
     bool store_natural = true;
-    for (int q = 0; q < c; q++) store_natural &= store_lanes[size_t(q)] == q;
+    auto store_map = [&]() {
+      for (int x = 0; x < 32; x++) outq[x] = x < T_ ? ph.lq[x] : -1;
+      if (ph.relabeled)
+        for (int x = 0; x < T_; x++) outq[lpos[ph.rho[ph.lq[x]]]] = ph.lq[x];
+      store_lanes.assign(size_t(c), 0);
+      store_low = 0;
+      for (int x = 0; x < T_; x++)
+        if (outq[x] < c) {
+          store_lanes[size_t(outq[x])] = x;
+          store_low |= 1u << x;
+        }
+      store_natural = true;
+      for (int q = 0; q < c; q++) store_natural &= store_lanes[size_t(q)] == q;
+    };
+    store_map();
+    // Precision 1: a pass runs on the tensor cores unless the CUDA-core register
+    // kernel (32 amplitudes a thread, blocks of <= 2 qubits, no phase ops) is
+    // estimated faster.  Times in units of one HBM pass, fitted to both kernels'
+    // measured passes on a 34-qubit state: tensor cores 0.66 + 0.47 per stage +
+    // 0.36 per phase op; CUDA cores max(1.05, 0.30 + 0.10 per stage + 0.0075 per
+    // block flop per amplitude).  Light passes (few stages of one- and two-qubit
+    // blocks, SWAPs folded into the store) go to the CUDA cores.
+    if (ph.has_alt && kmx <= 4 && T_reg_ok(T_, c, 5)) {
+      std::vector<HStage> st;
+      assign_stages(ph.ops, omask, T_, c, 4, st, true);
+      size_t nph = 0;
+      for (auto &op : ph.ops) nph += op.type == OP_PHASE;
+      const double t_tc = 0.66 + 0.47 * double(st.size()) + 0.36 * double(nph);
+      std::swap(ph.ops, ph.alt_ops);
+      std::swap(ph.pairs, ph.alt_pairs);
+      std::swap(ph.rho, ph.alt_rho);
+      ph.relabeled = true;
+      op_masks();
+      store_map();
+      bool light = kmx <= 2;
+      double flop = 0.0;
+      for (auto &op : ph.ops) {
+        if (op.type == OP_PHASE) light = false;
+        else flop += 8.0 * double(1 << op.blk.k());
+      }
+      bool use_cc = false;
+      if (light) {
+        st.clear();
+        assign_stages(ph.ops, omask, T_, c, 5, st, false, store_low, store_natural);
+        const double t_cc = std::max(1.05, 0.30 + 0.10 * double(st.size()) + 0.0075 * flop);
+        use_cc = t_cc < t_tc - 0.05;
+      }
+      if (!use_cc) {
+        std::swap(ph.ops, ph.alt_ops);
+        std::swap(ph.pairs, ph.alt_pairs);
+        std::swap(ph.rho, ph.alt_rho);
+        ph.relabeled = false;
+        op_masks();
+        store_map();
+      } else {
+        ph.kfuse = std::min(kmax, 2);
+      }
+      hp.n_ops = uint32_t(nops);
+    }
     // tensor-core stages (precision 1) when the pass fits the TC kernel: 4-qubit
     // stages, or 5-qubit stages for a pass holding a 5-qubit block (or all
     // passes with kernel variant 2), else 4-qubit ones if those fit
     const int Rtc = (kmx == 5 || o.kernel_variant == 2) ? 5 : 4;
-    if (o.precision == 1 && kmx <= 5 && !ph.relabeled &&
+    if (o.precision >= 1 && kmx <= 5 && !ph.relabeled &&
         (pack_tc_pass(ph.ops, omask, lpos, int(hp.T), c, outq, hp, buf, plan.rparams[p], plan.info, Rtc) ||
          (Rtc == 5 && kmx <= 4 &&
           pack_tc_pass(ph.ops, omask, lpos, int(hp.T), c, outq, hp, buf, plan.rparams[p], plan.info, 4)))) {

@@ -396,6 +396,9 @@ int main(int argc, char **argv) {
     }
   double e = 0;
   for (size_t i = 0; i < a.size(); i++) e = std::max(e, std::abs(a[i] - b[i]));
-  printf("plans %zu passes %zu tensor-core %zu maxerr %.3e\n", plans.size(), total, n_tc, e);
+  printf("plans %zu passes %zu tensor-core %zu maxerr %.3e kinds:", plans.size(), total, n_tc, e);
+  for (const Plan &plan : plans)
+    for (const PlanPass &hp : plan.passes) printf(" %u", hp.kind);
+  printf("\n");
   return e <= 1e-5 ? 0 : 2;
 }

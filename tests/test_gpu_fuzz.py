@@ -32,7 +32,7 @@ def _case(seed):
     T = int(rng.integers(min(n, 7), min(n, 13) + 1))
     opts = dict(tile_qubits=T, low_qubits=int(rng.integers(1, min(T, 5) + 1)),
                 k_max=int(rng.integers(1, 6)), kernel_variant=int(rng.integers(0, 3)),
-                precision=int(rng.random() < 0.3))
+                precision=(1 + seed % 2) if rng.random() < 0.3 else 0)
     return n, circ, opts
 
 

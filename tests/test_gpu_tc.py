@@ -1,5 +1,7 @@
 """Tensor-core (tcgen05, 3xTF32) path: the stage product against an FP64
-product, and whole circuits with precision=1 against the complex128 oracle.
+product, and whole circuits with precision=2 (every pass that fits on the
+tensor cores) and precision=1 (the planner's per-pass choice between the
+tensor-core and the CUDA-core register kernel) against the complex128 oracle.
 
 Tolerances: the split-TF32 product keeps about float32 accuracy -- per element
 |d - d_fp64| <= 2e-6 * (sum_k |a_mk| |b_nk|), versus ~1e-3 for one plain TF32
@@ -63,11 +65,11 @@ def test_tc_product_unitary_embedding(sv):
     assert np.max(np.abs(out - want)) < 1e-5
 
 
-def _run(P, n, circ, psi0=None, **opts):
+def _run(P, n, circ, psi0=None, precision=2, **opts):
     s = P.StateVector(n)
     if psi0 is not None:
         s.set_amplitudes(psi0)
-    s.apply(circ, precision=1, **opts)
+    s.apply(circ, precision=precision, **opts)
     g = s.amplitudes().astype(np.complex128)
     s.close()
     return g
@@ -85,7 +87,7 @@ def _compare(g, ref, what):
 def test_tc_random_layered(sv, T, k_max):
     n = 16
     circ = W.random_layered(n, 14, 21)
-    info = sv.capi.sv_plan_stats(n, circ, sv.capi.make_opts(k_max, T, 5, 1))
+    info = sv.capi.sv_plan_stats(n, circ, sv.capi.make_opts(k_max, T, 5, 2))
     assert info["tc_stages"] > 0
     _compare(_run(sv, n, circ, k_max=k_max, tile_qubits=T), oracle.run(n, circ), f"T={T} k={k_max}")
 
@@ -115,7 +117,7 @@ def test_tc_qft_closed_form(sv):
     for n in (14, 18):
         x = W.basis_index(n, 5)
         s = sv.StateVector(n, basis_index=x)
-        s.apply(W.qft(n), precision=1, k_max=4)
+        s.apply(W.qft(n), precision=2, k_max=4)
         g = s.amplitudes().astype(np.complex128)
         s.close()
         y = np.arange(1 << n)
@@ -126,7 +128,7 @@ def test_tc_mirror_28(sv):
     n = 28
     c = W.random_layered(n, 40, 2)
     s = sv.StateVector(n)
-    s.apply(c + W.inverse(c), precision=1, k_max=4)
+    s.apply(c + W.inverse(c), precision=2, k_max=4)
     a0 = s.amplitudes(0, 1)[0]
     norm2 = s.norm2()
     # fidelity with |0...0>: |a_0|^2 / ||psi||^2
@@ -166,7 +168,7 @@ def test_tc_norm_tracking_keeps_input_norm(sv):
     psi0 = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
     psi0 = (0.8 * psi0 / np.linalg.norm(psi0)).astype(np.complex64)
     circ = W.random_layered(n, 40, 17)
-    info = sv.capi.sv_plan_stats(n, circ, sv.capi.make_opts(4, 11, 5, 1))
+    info = sv.capi.sv_plan_stats(n, circ, sv.capi.make_opts(4, 11, 5, 2))
     assert info["passes_by_kind"][2] >= 20
     g = _run(sv, n, circ, psi0=psi0, k_max=4, tile_qubits=11)
     n0 = oracle.norm2(psi0.astype(np.complex128))
@@ -199,7 +201,7 @@ def test_tc_five_qubit_stages(sv, T):
     # complex products) on every tensor-core pass that fits
     n = 16
     circ = W.random_layered(n, 12, 23)
-    info = sv.capi.sv_plan_stats(n, circ, sv.capi.make_opts(5, T, 5, 1, 2))
+    info = sv.capi.sv_plan_stats(n, circ, sv.capi.make_opts(5, T, 5, 2, 2))
     assert info["tc_stages"] > 0 and info["hist_k"][5] > 0
     _compare(_run(sv, n, circ, k_max=5, tile_qubits=T, kernel_variant=2), oracle.run(n, circ), f"R=5 T={T}")
 
@@ -218,6 +220,19 @@ def test_tc_five_qubit_unitaries(sv, depth):
         z = rng.standard_normal((32, 32)) + 1j * rng.standard_normal((32, 32))
         u, _ = np.linalg.qr(z)
         circ.insert(int(rng.integers(0, len(circ) + 1)), ("unitary", qs, (u,)))
-    info = sv.capi.sv_plan_stats(n, circ, sv.capi.make_opts(4, 12, 5, 1))
+    info = sv.capi.sv_plan_stats(n, circ, sv.capi.make_opts(4, 12, 5, 2))
     assert info["tc_stages"] > 0 and info["hist_k"][5] == 2
     _compare(_run(sv, n, circ, k_max=4, tile_qubits=12), oracle.run(n, circ), "5-qubit unitaries")
+
+
+def test_mixed_precision_plan(sv):
+    # precision 1: the planner puts light passes (one- and two-qubit blocks, no
+    # phase ops) on the CUDA-core register kernel and the rest on the tensor
+    # cores; the mixed plan tracks the norm across its tensor-core passes only
+    n = 20
+    circ = W.random_layered(n, 40, 3) + W.qft(n)
+    info = sv.capi.sv_plan_stats(n, circ, sv.capi.make_opts(5, 12, 5, 1))
+    assert info["passes_by_kind"][1] > 0 and info["passes_by_kind"][2] > 0, info["passes_by_kind"]
+    g = _run(sv, n, circ, precision=1, k_max=5, tile_qubits=12)
+    _compare(g, oracle.run(n, circ), "mixed n=20")
+    assert abs(oracle.norm2(g) - 1) < 1e-5

@@ -156,7 +156,7 @@ def test_packed_tensor_core_passes_equal_gates(executor, k_max, T, c, variant):
     packed records against gate-by-gate application."""
     bad, n_tc = [], 0
     for name, n, circ in EXEC_CASES + WIDE_CASES:
-        r = subprocess.run([executor, str(k_max), str(T), str(c), str(variant), "0", "1"], input=_encode(n, circ),
+        r = subprocess.run([executor, str(k_max), str(T), str(c), str(variant), "0", "2"], input=_encode(n, circ),
                            capture_output=True, text=True)
         if r.returncode != 0:
             bad.append(f"{name} n={n}: rc={r.returncode} {r.stdout.strip()}")
@@ -164,6 +164,26 @@ def test_packed_tensor_core_passes_equal_gates(executor, k_max, T, c, variant):
             n_tc += int(r.stdout.split(" tensor-core ")[1].split()[0])
     assert not bad, bad
     assert n_tc > 0
+
+
+def test_mixed_precision_passes_equal_gates(executor):
+    """Precision 1: the planner's per-pass choice puts light passes on the
+    CUDA-core register kernel (SWAPs folded into the store) and the rest on
+    the tensor cores; the mixed plans, streamed in chunks or whole, still equal
+    gate-by-gate application, and both kinds occur."""
+    bad, kinds = [], set()
+    circs = [("qft", 16, W.qft(16)), ("random_layered", 18, W.random_layered(18, 12, 5)),
+             ("qft_after_layers", 16, W.random_layered(16, 6, 6) + W.qft(16))]
+    for name, n, circ in circs:
+        for chunk in ("0", "2"):
+            r = subprocess.run([executor, "5", "12", "5", "0", chunk, "1"], input=_encode(n, circ),
+                               capture_output=True, text=True)
+            if r.returncode != 0:
+                bad.append(f"{name} n={n} chunk={chunk}: rc={r.returncode} {r.stdout.strip()}")
+            if "kinds:" in r.stdout:
+                kinds.update(r.stdout.split("kinds:")[1].split())
+    assert not bad, bad
+    assert {"1", "2"} <= kinds, kinds
 
 
 @pytest.mark.parametrize("chunk", [1, 2, 3])
