@@ -457,6 +457,79 @@ static void fuse_pass(const std::vector<GateM> &gates, const std::vector<uint32_
   flush_phase();
 }
 
+// Tensor-core passes whose gates are all non-diagonal and at most kmax wide:
+// every stage is one product over at most kmax qubits, so the ops are built
+// stage by stage.  A stage's qubit set S starts as the first remaining gate's
+// qubits and grows one qubit at a time, each time by the qubit that lets the
+// most remaining gates into the stage (two-qubit and wider gates weigh 4, one-
+// qubit gates 1): a scan in program order admits a gate when its qubits lie in
+// S and no earlier gate left out touches them, so the stage's gates may move
+// ahead of the ones left out only where they share no qubit.  The admitted
+// gates are multiplied into one block over S.  False (ops untouched) when the
+// pass has a diagonal or a wider gate.
+static bool fuse_stages(const std::vector<GateM> &gates, const std::vector<uint32_t> &acc, int kmax,
+                        std::vector<HostOp> &ops) {
+  for (uint32_t gi : acc)
+    if (gates[gi].diag || gates[gi].k > kmax) return false;
+  std::vector<uint32_t> rem = acc, in, out;
+  auto scan = [&](uint64_t S, std::vector<uint32_t> *a, std::vector<uint32_t> *r) {
+    uint64_t blocked = 0;
+    int score = 0;
+    for (uint32_t gi : rem) {
+      const GateM &g = gates[gi];
+      if (!(g.mask & blocked) && (g.mask & ~S) == 0) {
+        score += g.k >= 2 ? 4 : 1;
+        if (a) a->push_back(gi);
+      } else {
+        blocked |= g.mask;
+        if (r) r->push_back(gi);
+      }
+    }
+    return score;
+  };
+  std::vector<HostOp> built;
+  while (!rem.empty()) {
+    uint64_t S = gates[rem[0]].mask;
+    while (popc(S) < kmax) {
+      uint64_t cand = 0;
+      for (uint32_t gi : rem) cand |= gates[gi].mask;
+      cand &= ~S;
+      if (!cand) break;
+      int best = -1;
+      uint64_t bq = 0;
+      for (uint64_t cq = cand; cq; cq &= cq - 1) {
+        const uint64_t q = cq & (~cq + 1);
+        const int sc = scan(S | q, nullptr, nullptr);
+        if (sc > best) {
+          best = sc;
+          bq = q;
+        }
+      }
+      S |= bq;
+    }
+    in.clear();
+    out.clear();
+    scan(S, &in, &out);
+    Block b = identity_block();
+    for (uint64_t cq = S; cq; cq &= cq - 1) {
+      Block one;
+      const int q = ctz(cq);
+      one.mask = uint64_t(1) << q;
+      one.qs = {q};
+      one.M = {cd(1.0), cd(0.0), cd(0.0), cd(1.0)};
+      b = kron_blocks(b, one);
+    }
+    for (uint32_t gi : in) apply_to_block(b, gates[gi]);
+    HostOp op;
+    op.type = OP_DENSE;
+    op.blk = std::move(b);
+    built.push_back(std::move(op));
+    rem.swap(out);
+  }
+  ops.swap(built);
+  return true;
+}
+
 static void put_bytes(std::vector<uint8_t> &buf, const void *p, size_t n) {
   const uint8_t *b = static_cast<const uint8_t *>(p);
   buf.insert(buf.end(), b, b + n);
@@ -1194,6 +1267,27 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
     for (int q = 0; q < 64; q++) ph.rho[q] = q;
     ph.pairs = pairs_ok(kf);
     fuse_pass(gates, acc, Q, lpos, kf, ph.pairs, ph.ops, ph.relabeled ? ph.rho : nullptr);
+    if (o.precision >= 1 && kf == 4 && !o_smem) {
+      // tensor-core stages: the look-ahead stage former when it needs fewer stages
+      auto n_stages = [&](const std::vector<HostOp> &ops) {
+        std::vector<uint32_t> om(ops.size(), 0);
+        for (size_t i = 0; i < ops.size(); i++) {
+          if (ops[i].type == OP_DENSE) {
+            for (int q : ops[i].blk.qs) om[i] |= 1u << lpos[q];
+          } else {
+            for (auto &t : ops[i].terms) {
+              if (t.la >= 0) om[i] |= 1u << t.la;
+              if (t.lb >= 0) om[i] |= 1u << t.lb;
+            }
+          }
+        }
+        std::vector<HStage> st;
+        assign_stages(ops, om, popc(Q), c, 4, st, true);
+        return st.size();
+      };
+      std::vector<HostOp> staged;
+      if (fuse_stages(gates, acc, 4, staged) && n_stages(staged) < n_stages(ph.ops)) ph.ops.swap(staged);
+    }
     if (o.precision == 1 && o_r5) {
       ph.has_alt = true;
       for (int q = 0; q < 64; q++) ph.alt_rho[q] = q;
