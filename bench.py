@@ -57,8 +57,8 @@ def workload_name():
     return (f"random layered n={N_QUBITS} depth={DEPTH} + QFT-{N_QUBITS} on a seeded basis state; "
             f"FP64 norm, CDF and {SHOTS} shots; <Z> expectation")
 # DRAM bytes (read + write) of one pass-kernel launch from an ncu capture of the
-# current kernel, keyed by (n, tile qubits, precision, kernel variant); see profiles/.
-PASS_TRAFFIC_BYTES = {(28, 12, 0, 0): 4238000000, (28, 12, 1, 0): 4235000000, (28, 12, 2, 0): 4235000000}
+# current kernel, keyed by (n, tile qubits, low qubits, precision, kernel variant); see profiles/.
+PASS_TRAFFIC_BYTES = {(28, 12, 5, 0, 0): 4238000000, (28, 12, 5, 1, 0): 4235000000, (28, 12, 5, 2, 0): 4235000000}
 
 
 def peaks():
@@ -268,7 +268,7 @@ def run_ours(args, rank, world, local_rank):
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": peak_kind}
     roof.update({"kernel": "pass kernels (k_pass_tc and k_pass_reg launches together; one HBM pass over the state each)",
-                 "traffic": PASS_TRAFFIC_BYTES.get((n, OPTS["tile_qubits"], OPTS["precision"],
+                 "traffic": PASS_TRAFFIC_BYTES.get((n, OPTS["tile_qubits"], OPTS["low_qubits"], OPTS["precision"],
                                                     OPTS.get("kernel_variant", 0))),
                  "algorithmic_bytes_per_launch": 16 * (1 << n),
                  "algorithmic_flops_per_step": flops_pass_step,
@@ -400,7 +400,7 @@ def config_dict(world: int) -> dict:
     n = N_QUBITS
     return {"workload": workload_name(), "n_qubits": n, "depth": DEPTH,
             "gates": len(W.random_layered(n, DEPTH, SEED)) + len(W.qft(n)),
-            "shots": SHOTS, "fusion_k_max": OPTS["k_max"], "tile_qubits": OPTS["tile_qubits"],
+            "shots": SHOTS, "fusion_k_max": OPTS["k_max"], "tile_qubits": OPTS["tile_qubits"], "low_qubits": OPTS["low_qubits"],
             "kernel_variant": OPTS.get("kernel_variant", 0), "precision": OPTS["precision"],
             "passes_per_step": DEFAULT_PLAN["passes_per_step"],
             "l2": f"inputs larger than L2 ({(8 << n) / 2**30:.3g} GiB state vs 129 MB L2)",
@@ -781,6 +781,8 @@ def main():
                     help="smaller states for profiling captures (the bench line uses 28)")
     ap.add_argument("--depth", type=int, default=DEPTH)
     ap.add_argument("--tile-qubits", type=int, default=OPTS["tile_qubits"])
+    ap.add_argument("--low-qubits", type=int, default=OPTS["low_qubits"],
+                    help="qubits every tile holds (HBM runs of 2^c amplitudes)")
     ap.add_argument("--k-max", type=int, default=OPTS["k_max"])
     ap.add_argument("--kernel-variant", type=int, default=0)
     ap.add_argument("--precision", type=int, default=OPTS["precision"],
@@ -804,7 +806,8 @@ def main():
     if args.workload == "large":
         N_QUBITS, DEPTH, SHOTS = 34, 30, 1_000_000
         args.no_cpu_baseline = True  # the complex128 oracle would need 256 GiB of host memory
-    OPTS.update(tile_qubits=args.tile_qubits, k_max=args.k_max, kernel_variant=args.kernel_variant,
+    OPTS.update(tile_qubits=args.tile_qubits, low_qubits=args.low_qubits, k_max=args.k_max,
+                kernel_variant=args.kernel_variant,
                 precision=args.precision)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
