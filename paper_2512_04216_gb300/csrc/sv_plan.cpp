@@ -191,15 +191,19 @@ bool convert_ir(int n, const sv_gate *ir, size_t ng, std::vector<GateM> &gates, 
 // fusion helpers
 // ---------------------------------------------------------------------------
 
+// A fused block.  A block without a matrix (M empty) is a shape only: the
+// planner fuses the candidate forms of a pass as shapes (qubits and order, all
+// that its choices read) and multiplies out the matrices of the form it keeps.
 struct Block {
   uint64_t mask = 0;
   std::vector<int> qs;   // matrix bit m <-> physical qubit qs[m]
-  std::vector<cd> M;     // 2^k x 2^k row-major
+  std::vector<cd> M;     // 2^k x 2^k row-major (empty: a shape only)
   int k() const { return int(qs.size()); }
 };
 
-// M <- G (on block bits pos[0..kg-1]) * M, column by column.
+// M <- G (on block bits pos[0..kg-1]) * M, column by column (nothing for a shape).
 static void apply_to_block(Block &b, const GateM &g) {
+  if (b.M.empty()) return;
   const int k = b.k();
   const int K = 1 << k, KG = 1 << g.k;
   int pos[5];
@@ -231,12 +235,14 @@ static void apply_to_block(Block &b, const GateM &g) {
   }
 }
 
-// Tensor product of disjoint blocks: qs = a.qs ++ b.qs (a on the low matrix bits).
+// Tensor product of disjoint blocks: qs = a.qs ++ b.qs (a on the low matrix bits);
+// a shape if either is one.
 static Block kron_blocks(const Block &a, const Block &b) {
   Block c;
   c.mask = a.mask | b.mask;
   c.qs = a.qs;
   c.qs.insert(c.qs.end(), b.qs.begin(), b.qs.end());
+  if (a.M.empty() || b.M.empty()) return c;
   const int KA = 1 << a.k(), KB = 1 << b.k(), K = KA * KB;
   c.M.assign(size_t(K) * K, 0.0);
   for (int rb = 0; rb < KB; rb++)
@@ -247,10 +253,19 @@ static Block kron_blocks(const Block &a, const Block &b) {
   return c;
 }
 
-static Block identity_block() {
+static Block identity_block(bool shape = false) {
   Block b;
-  b.M = {cd(1.0)};
+  if (!shape) b.M = {cd(1.0)};
   return b;
+}
+
+// The one-qubit identity block on qubit q (a shape when `shape`).
+static Block qubit_block(int q, bool shape) {
+  Block one;
+  one.mask = uint64_t(1) << q;
+  one.qs = {q};
+  if (!shape) one.M = {cd(1.0), cd(0.0), cd(0.0), cd(1.0)};
+  return one;
 }
 
 static uint32_t to_turn(double phi) {
@@ -327,7 +342,7 @@ static void merge_terms(std::vector<HostTerm> &terms) {
 // lpos[rho[q]].  Without it, SWAPs are ordinary 4x4 blocks.
 static void fuse_pass(const std::vector<GateM> &gates, const std::vector<uint32_t> &acc,
                       uint64_t Q, const int *lpos, int kmax, bool pairs, std::vector<HostOp> &ops,
-                      int *rho = nullptr) {
+                      int *rho = nullptr, bool shape = false) {
   std::vector<Block> open;
   std::vector<HostTerm> pending;
   uint64_t pending_local = 0;
@@ -426,7 +441,7 @@ static void fuse_pass(const std::vector<GateM> &gates, const std::vector<uint32_
       if (b.mask & g.mask) U |= b.mask;
     Block nb;
     if (popc(U) <= kmax) {
-      nb = identity_block();
+      nb = identity_block(shape);
       for (size_t i = 0; i < open.size();) {
         if (open[i].mask & g.mask) {
           nb = kron_blocks(nb, open[i]);
@@ -437,17 +452,11 @@ static void fuse_pass(const std::vector<GateM> &gates, const std::vector<uint32_
       }
     } else {
       close_touching(g.mask);
-      nb = identity_block();
+      nb = identity_block(shape);
     }
     // append the gate's new qubits, then multiply the gate in
     for (int x = 0; x < g.k; x++) {
-      if (!(nb.mask >> g.q[x] & 1)) {
-        Block one;
-        one.mask = uint64_t(1) << g.q[x];
-        one.qs = {g.q[x]};
-        one.M = {cd(1.0), cd(0.0), cd(0.0), cd(1.0)};
-        nb = kron_blocks(nb, one);
-      }
+      if (!(nb.mask >> g.q[x] & 1)) nb = kron_blocks(nb, qubit_block(g.q[x], shape));
     }
     apply_to_block(nb, g);
     open.push_back(std::move(nb));
@@ -468,7 +477,7 @@ static void fuse_pass(const std::vector<GateM> &gates, const std::vector<uint32_
 // gates are multiplied into one block over S.  False (ops untouched) when the
 // pass has a diagonal or a wider gate.
 static bool fuse_stages(const std::vector<GateM> &gates, const std::vector<uint32_t> &acc, int kmax,
-                        std::vector<HostOp> &ops) {
+                        std::vector<HostOp> &ops, bool shape = false) {
   for (uint32_t gi : acc)
     if (gates[gi].diag || gates[gi].k > kmax) return false;
   std::vector<uint32_t> rem = acc, in, out;
@@ -510,15 +519,8 @@ static bool fuse_stages(const std::vector<GateM> &gates, const std::vector<uint3
     in.clear();
     out.clear();
     scan(S, &in, &out);
-    Block b = identity_block();
-    for (uint64_t cq = S; cq; cq &= cq - 1) {
-      Block one;
-      const int q = ctz(cq);
-      one.mask = uint64_t(1) << q;
-      one.qs = {q};
-      one.M = {cd(1.0), cd(0.0), cd(0.0), cd(1.0)};
-      b = kron_blocks(b, one);
-    }
+    Block b = identity_block(shape);
+    for (uint64_t cq = S; cq; cq &= cq - 1) b = kron_blocks(b, qubit_block(ctz(cq), shape));
     for (uint32_t gi : in) apply_to_block(b, gates[gi]);
     HostOp op;
     op.type = OP_DENSE;
@@ -1290,7 +1292,9 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
     ph.relabeled = !o_smem && o.precision == 0;
     for (int q = 0; q < 64; q++) ph.rho[q] = q;
     ph.pairs = pairs_ok(kf);
-    fuse_pass(gates, acc, Q, lpos, kf, ph.pairs, ph.ops, ph.relabeled ? ph.rho : nullptr);
+    // The candidate forms are compared as shapes (qubits only); only the kept
+    // form's matrices are multiplied out.
+    bool staged_form = false;
     if (o.precision >= 1 && kf == 4 && !o_smem) {
       // tensor-core stages: the look-ahead stage former when it needs fewer stages
       auto n_stages = [&](const std::vector<HostOp> &ops) {
@@ -1309,27 +1313,33 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
         assign_stages(ops, om, popc(Q), c, 4, st, true);
         return st.size();
       };
-      std::vector<HostOp> staged;
-      if (fuse_stages(gates, acc, 4, staged) && n_stages(staged) < n_stages(ph.ops)) ph.ops.swap(staged);
+      std::vector<HostOp> blocks, staged;
+      fuse_pass(gates, acc, Q, lpos, kf, ph.pairs, blocks, nullptr, true);
+      staged_form = fuse_stages(gates, acc, 4, staged, true) && n_stages(staged) < n_stages(blocks);
     }
+    if (o.precision == 0 && kmax > kf) {
+      // the wider fusion when its estimated cost is lower
+      std::vector<HostOp> narrow, wide;
+      const bool pw = pairs_ok(kmax);
+      int rho_n[64], rho_w[64];
+      for (int q = 0; q < 64; q++) rho_n[q] = rho_w[q] = q;
+      fuse_pass(gates, acc, Q, lpos, kf, ph.pairs, narrow, ph.relabeled ? rho_n : nullptr, true);
+      fuse_pass(gates, acc, Q, lpos, kmax, pw, wide, ph.relabeled ? rho_w : nullptr, true);
+      if (est(wide) < est(narrow)) {
+        ph.pairs = pw;
+        kf = kmax;
+      }
+    }
+    if (staged_form)
+      fuse_stages(gates, acc, 4, ph.ops);
+    else
+      fuse_pass(gates, acc, Q, lpos, kf, ph.pairs, ph.ops, ph.relabeled ? ph.rho : nullptr);
     if (o.precision == 1 && o_r5) {
+      // the CUDA-core form, as a shape: multiplied out if the pass goes there
       ph.has_alt = true;
       for (int q = 0; q < 64; q++) ph.alt_rho[q] = q;
       ph.alt_pairs = pairs_ok(std::min(kmax, 2));
-      fuse_pass(gates, acc, Q, lpos, std::min(kmax, 2), ph.alt_pairs, ph.alt_ops, ph.alt_rho);
-    }
-    if (o.precision == 0 && kmax > kf) {
-      std::vector<HostOp> wide;
-      const bool pw = pairs_ok(kmax);
-      int rho2[64];
-      for (int q = 0; q < 64; q++) rho2[q] = q;
-      fuse_pass(gates, acc, Q, lpos, kmax, pw, wide, ph.relabeled ? rho2 : nullptr);
-      if (est(wide) < est(ph.ops)) {
-        ph.ops.swap(wide);
-        ph.pairs = pw;
-        kf = kmax;
-        std::copy(rho2, rho2 + 64, ph.rho);
-      }
+      fuse_pass(gates, acc, Q, lpos, std::min(kmax, 2), ph.alt_pairs, ph.alt_ops, ph.alt_rho, true);
     }
     ph.kfuse = kf;
     ph.acc = std::move(acc);
@@ -1445,6 +1455,10 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
         store_map();
       } else {
         ph.kfuse = std::min(kmax, 2);
+        int rho[64];
+        for (int q = 0; q < 64; q++) rho[q] = q;
+        ph.ops.clear();
+        fuse_pass(gates, ph.acc, ph.Q, lpos, ph.kfuse, ph.pairs, ph.ops, rho);
       }
       hp.n_ops = uint32_t(nops);
     }
