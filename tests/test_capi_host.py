@@ -103,6 +103,35 @@ def test_plan_rejects_bad_options():
         capi.sv_plan_stats(12, W.ghz(12), capi.make_opts(tile_qubits=14))
 
 
+def test_precision_modes_plan_kinds():
+    # The planner's per-pass kernel choice, on the host: precision 2 puts every
+    # pass of a 28-qubit random circuit and QFT on the tensor cores, precision 1
+    # moves some light passes (blocks of <= 2 qubits, no phase ops) to the
+    # CUDA-core register kernel without changing the tile sets, precision 0
+    # uses no tensor cores; precision 3 is refused.
+    capi = _lib()
+    circ = W.random_layered(28, 40, 2) + W.qft(28)
+    info = {p: capi.sv_plan_stats(28, circ, capi.make_opts(k_max=5, tile_qubits=12, low_qubits=5, precision=p))
+            for p in (0, 1, 2)}
+    assert info[2]["passes_by_kind"][2] == info[2]["n_passes"] and info[2]["tc_stages"] == info[2]["n_stages"]
+    assert 0 < info[1]["passes_by_kind"][1] < info[1]["n_passes"] // 4
+    assert info[1]["passes_by_kind"][2] + info[1]["passes_by_kind"][1] == info[1]["n_passes"]
+    assert info[0]["tc_stages"] == 0 and info[0]["passes_by_kind"][2] == 0
+    assert info[0]["n_passes"] == info[1]["n_passes"] == info[2]["n_passes"]
+    with pytest.raises(capi.SvError):
+        capi.sv_plan_stats(12, W.ghz(12), capi.make_opts(precision=3))
+
+
+def test_beam_tile_choice_takes_fewer_passes_from_27_qubits():
+    # From 27 qubits the look-ahead tile choice keeps a beam of partial tile
+    # sets: the 28-qubit depth-40 random layered circuit plans in 59 passes
+    # (68 with the single greedy choice the planner keeps below 27 qubits).
+    capi = _lib()
+    opts = capi.make_opts(k_max=5, tile_qubits=12, low_qubits=5, precision=1)
+    p28 = capi.sv_plan_stats(28, W.random_layered(28, 40, 2), opts)["n_passes"]
+    assert p28 <= 60, p28
+
+
 def test_unknown_gate_kind_rejected():
     capi = _lib()
     import numpy as np
