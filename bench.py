@@ -313,7 +313,7 @@ def capi_get(capi, h, i):
 # Plan statistics of the default step (n=28 depth-40 random circuit + QFT-28 with
 # OPTS): the reference arm reports them without loading the library;
 # tests/test_bench_host.py checks them against the planner.
-DEFAULT_PLAN = {"passes_per_step": 66, "bytes_step": 289910292480.0}
+DEFAULT_PLAN = {"passes_per_step": 68, "bytes_step": 298500227072.0}
 
 
 def oracle_gate_time(threads: int, reps: int = 3):

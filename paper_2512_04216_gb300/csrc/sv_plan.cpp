@@ -1052,10 +1052,14 @@ static int count_fixed(const std::vector<GateM> &gates, const std::vector<uint32
 // Tile set grown by look-ahead: start from the low qubits and the first
 // unapplied gate, then add single qubits, or the two outside qubits of a gate
 // in the look-ahead window, scored by how many non-diagonal gates a scan of the
-// window then accepts per added qubit.  A beam of the `beam` best partial sets
-// is grown in step (one greedy choice often shuts out a better completion); of
-// the complete sets, the one whose scan of all remaining gates accepts the most
-// non-diagonal gates is taken.
+// window then accepts per added qubit.  With one set (beam_width 1) the set
+// whose scan of all remaining gates accepts the most non-diagonal gates is
+// taken.  With a beam of the beam_width best partial sets grown in step (one
+// greedy choice often shuts out a better completion), each complete set is
+// scored by those gates per unit of estimated pass time, 3 + the tensor-core
+// stages of the pass's gates fused as shapes (the constant gave the shortest
+// estimated step on random 28- to 34-qubit circuits): fewer stages can be worth
+// a pass more.
 static uint64_t lookahead_tile(const std::vector<GateM> &gates, const std::vector<uint32_t> &rem, int n,
                                int T, uint64_t lowmask, size_t beam_width) {
   constexpr size_t kWindow = 96;
@@ -1102,8 +1106,39 @@ static uint64_t lookahead_tile(const std::vector<GateM> &gates, const std::vecto
   }
   uint64_t best = Q0;
   int best_n = -1;
+  double best_r = -1.0;
   for (uint64_t Q : done) {
     const int k = count_fixed(gates, rem, rem.size(), Q);
+    if (beam_width > 1 && popc(Q) == T) {
+      std::vector<uint32_t> acc, rest;
+      scan_fixed(gates, rem, Q, acc, rest);
+      int lpos[64];
+      for (int q = 0; q < 64; q++) lpos[q] = -1;
+      int j = 0;
+      for (int q = 0; q < n; q++)
+        if (Q >> q & 1) lpos[q] = j++;
+      std::vector<HostOp> ops;
+      if (!fuse_stages(gates, acc, 4, ops, true)) fuse_pass(gates, acc, Q, lpos, 4, true, ops, nullptr, true);
+      std::vector<uint32_t> om(ops.size(), 0);
+      for (size_t i = 0; i < ops.size(); i++) {
+        if (ops[i].type == OP_DENSE) {
+          for (int q : ops[i].blk.qs) om[i] |= 1u << lpos[q];
+        } else {
+          for (auto &t : ops[i].terms) {
+            if (t.la >= 0) om[i] |= 1u << t.la;
+            if (t.lb >= 0) om[i] |= 1u << t.lb;
+          }
+        }
+      }
+      std::vector<HStage> st;
+      assign_stages(ops, om, T, ctz(~lowmask), 4, st, true);
+      const double r = double(k) / (3.0 + double(st.size()));
+      if (r > best_r) {
+        best_r = r;
+        best = Q;
+      }
+      continue;
+    }
     if (k > best_n) {
       best_n = k;
       best = Q;

@@ -124,12 +124,13 @@ def test_precision_modes_plan_kinds():
 
 def test_beam_tile_choice_takes_fewer_passes_from_27_qubits():
     # From 27 qubits the look-ahead tile choice keeps a beam of partial tile
-    # sets: the 28-qubit depth-40 random layered circuit plans in 59 passes
-    # (68 with the single greedy choice the planner keeps below 27 qubits).
+    # sets: the 28-qubit depth-40 random layered circuit plans in 61 passes
+    # (68 with the single greedy choice the planner keeps below 27 qubits; 59
+    # when the beam's sets are ranked by gates alone, with more stages).
     capi = _lib()
     opts = capi.make_opts(k_max=5, tile_qubits=12, low_qubits=5, precision=1)
     p28 = capi.sv_plan_stats(28, W.random_layered(28, 40, 2), opts)["n_passes"]
-    assert p28 <= 60, p28
+    assert p28 <= 62, p28
 
 
 def test_unknown_gate_kind_rejected():
