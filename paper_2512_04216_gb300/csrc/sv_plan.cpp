@@ -1054,14 +1054,14 @@ static int count_fixed(const std::vector<GateM> &gates, const std::vector<uint32
 // in the look-ahead window, scored by how many non-diagonal gates a scan of the
 // window then accepts per added qubit.  With one set (beam_width 1) the set
 // whose scan of all remaining gates accepts the most non-diagonal gates is
-// taken.  With a beam of the beam_width best partial sets grown in step (one
-// greedy choice often shuts out a better completion), each complete set is
-// scored by those gates per unit of estimated pass time, 3 + the tensor-core
-// stages of the pass's gates fused as shapes (the constant gave the shortest
-// estimated step on random 28- to 34-qubit circuits): fewer stages can be worth
-// a pass more.
+// taken, also from a beam of the beam_width best partial sets grown in step
+// (one greedy choice often shuts out a better completion).  For tensor-core
+// passes (stage_rank) the beam's complete sets are ranked instead by those
+// gates per unit of estimated pass time, 3 + the tensor-core stages of the
+// pass's gates fused as shapes (the constant gave the shortest estimated step
+// on random 28- to 34-qubit circuits): fewer stages can be worth a pass more.
 static uint64_t lookahead_tile(const std::vector<GateM> &gates, const std::vector<uint32_t> &rem, int n,
-                               int T, uint64_t lowmask, size_t beam_width) {
+                               int T, uint64_t lowmask, size_t beam_width, bool stage_rank) {
   constexpr size_t kWindow = 96;
   const size_t W = std::min(rem.size(), kWindow);
   uint64_t Q0 = lowmask;
@@ -1109,7 +1109,7 @@ static uint64_t lookahead_tile(const std::vector<GateM> &gates, const std::vecto
   double best_r = -1.0;
   for (uint64_t Q : done) {
     const int k = count_fixed(gates, rem, rem.size(), Q);
-    if (beam_width > 1 && popc(Q) == T) {
+    if (stage_rank) {
       std::vector<uint32_t> acc, rest;
       scan_fixed(gates, rem, Q, acc, rest);
       int lpos[64];
@@ -1280,7 +1280,7 @@ bool PlanBuilder::next(Plan &plan, size_t max_passes, std::string &err) {
       }
       // a beam of 8 partial tile sets from 27 qubits up: there a pass takes more
       // GPU time than planning it with the beam (~0.4 ms a pass on the host)
-      uint64_t Ql = lookahead_tile(gates, remaining, n, T, lowmask, n >= 27 ? 8 : 1);
+      uint64_t Ql = lookahead_tile(gates, remaining, n, T, lowmask, n >= 27 ? 8 : 1, n >= 27 && o.precision >= 1);
       for (int q = 0; q < n && popc(Ql) < T; q++) Ql |= uint64_t(1) << q;
       scan_fixed(gates, remaining, Ql, acc2, rest2);
       if (nondiag(acc2) > nondiag(acc)) {

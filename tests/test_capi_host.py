@@ -108,7 +108,8 @@ def test_precision_modes_plan_kinds():
     # pass of a 28-qubit random circuit and QFT on the tensor cores, precision 1
     # moves some light passes (blocks of <= 2 qubits, no phase ops) to the
     # CUDA-core register kernel without changing the tile sets, precision 0
-    # uses no tensor cores; precision 3 is refused.
+    # uses no tensor cores (and ranks tile sets by gates alone, not by
+    # estimated tensor-core stages); precision 3 is refused.
     capi = _lib()
     circ = W.random_layered(28, 40, 2) + W.qft(28)
     info = {p: capi.sv_plan_stats(28, circ, capi.make_opts(k_max=5, tile_qubits=12, low_qubits=5, precision=p))
@@ -117,7 +118,7 @@ def test_precision_modes_plan_kinds():
     assert 0 < info[1]["passes_by_kind"][1] < info[1]["n_passes"] // 4
     assert info[1]["passes_by_kind"][2] + info[1]["passes_by_kind"][1] == info[1]["n_passes"]
     assert info[0]["tc_stages"] == 0 and info[0]["passes_by_kind"][2] == 0
-    assert info[0]["n_passes"] == info[1]["n_passes"] == info[2]["n_passes"]
+    assert info[1]["n_passes"] == info[2]["n_passes"]
     with pytest.raises(capi.SvError):
         capi.sv_plan_stats(12, W.ghz(12), capi.make_opts(precision=3))
 
