@@ -1,6 +1,8 @@
 // Host-only check of the planner's fusion (fuse_pass): the fused ops of one pass
 // (dense blocks, phase terms, SWAP relabeling) applied to a random state must
-// equal the gates applied one by one.  Built and run by tests/test_plan_semantics.py.
+// equal the gates applied one by one, and the shape-only forms of fuse_pass and
+// fuse_stages (no matrices) must give the same ops.  Built and run by
+// tests/test_plan_semantics.py.
 #include "sv_plan.cpp"
 #include <cstdio>
 #include <random>
@@ -57,6 +59,34 @@ int main(int argc, char **argv) {
   int rho[64];
   for (int q = 0; q < 64; q++) rho[q] = q;
   fuse_pass(gates, acc, Q, lpos, kmax, pairs, ops, pairs ? rho : nullptr);
+  // The planner compares candidate fusions as shapes (no matrices) and builds
+  // only the kept one: a shape fusion must give the same ops, qubits in the
+  // same order, and the same phase terms.  Likewise the stage former.
+  {
+    std::vector<HostOp> shp;
+    int rho_s[64];
+    for (int q = 0; q < 64; q++) rho_s[q] = q;
+    fuse_pass(gates, acc, Q, lpos, kmax, pairs, shp, pairs ? rho_s : nullptr, true);
+    bool same = shp.size() == ops.size();
+    for (size_t i = 0; same && i < ops.size(); i++) {
+      same = shp[i].type == ops[i].type && shp[i].blk.qs == ops[i].blk.qs && shp[i].blk.mask == ops[i].blk.mask &&
+             shp[i].blk.M.empty() && shp[i].terms.size() == ops[i].terms.size();
+      for (size_t t = 0; same && t < ops[i].terms.size(); t++)
+        same = shp[i].terms[t].outer == ops[i].terms[t].outer && shp[i].terms[t].la == ops[i].terms[t].la &&
+               shp[i].terms[t].lb == ops[i].terms[t].lb && shp[i].terms[t].turn == ops[i].terms[t].turn;
+    }
+    for (int q = 0; same && q < 64; q++) same = !pairs || rho_s[q] == rho[q];
+    std::vector<HostOp> st_full, st_shape;
+    const bool f1 = fuse_stages(gates, acc, 4, st_full), f2 = fuse_stages(gates, acc, 4, st_shape, true);
+    same = same && f1 == f2 && st_full.size() == st_shape.size();
+    for (size_t i = 0; same && i < st_full.size(); i++)
+      same = st_full[i].blk.qs == st_shape[i].blk.qs && st_shape[i].blk.M.empty() &&
+             int(st_full[i].blk.M.size()) == (1 << (2 * st_full[i].blk.k()));
+    if (!same) {
+      printf("shape fusion differs from the full fusion\n");
+      return 3;
+    }
+  }
   std::mt19937_64 rng(7);
   std::normal_distribution<double> nd;
   std::vector<cd> a(1ull << n), b;
